@@ -1,0 +1,429 @@
+"""Benchmark: NFFT forward + adjoint nodes/s on one GB300 (or N replicas).
+
+A step is one pass of the whole path over one batch: Algorithm 1
+(deconv_pad -> cuFFT forward -> gather) and Algorithm 2 (scatter ->
+cuFFT inverse -> crop_deconv), every kernel launched through the C ABI, on
+device-resident inputs (nodes set once: the plan's precomputation, timed
+separately as set_nodes).  value = M / (mean step time) nodes/s, summed over
+ranks; each rank runs an independent replica of the same workload (a single
+transform does not shard: "replicas only", weak scaling).
+
+Default workload: 3D, N = 128^3, M = 2097152 uniform nodes, sigma = 2, m = 4,
+complex64 (FP32 arithmetic).  Between timed steps L2 is flushed by writing a
+256 MiB buffer.  e2e repeats the step through the same C-ABI calls with
+pinned HOST buffers (host<->device copies inside the timed region).
+
+--impl reference times the FP64 CPU oracle (plain numpy Algorithms 1/2) on a
+bounded node sample of the same workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NFFT fwd+adj nodes/s at 3D 128^3 (FP32, rel err <=1e-5) vs FP64 form; % HBM roofline"
+UNIT = "nodes/s"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+WORKLOADS = {
+    "3d": "3d",
+    "3d_lean": "3d_lean",
+    "2d_c64": "2d_c64",
+    "2d_c128": "2d_c128",
+    "1d": "1d",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=131072,
+                    help="nodes in the oracle's bounded sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_desc(wl):
+    N = "x".join(str(n) for n in wl["N"])
+    return "%s N=%s M=%d sigma=%g m=%d %s" % (wl["name"], N, wl["M"], wl["sigma"], wl["m"], wl["dtype"])
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2208_00049_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary for this kernel
+    and workload, or None if absent or taken on different kernel sources."""
+    path = os.path.join(PROFILE_DIR, "%s_%s.md" % (kernel, workload))
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not mh or not mt or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mt.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._thread = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                     "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5).stdout
+                for line in out.strip().splitlines():
+                    self.samples.append([x.strip() for x in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._thread.join(timeout=10)
+
+    def summary(self):
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                mx = float(s[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_throughput(wl, sample):
+    """Time the plain FP64 oracle (numpy, Algorithms 1/2) on the full grid with
+    a node sample; returns (full-workload nodes/s, details).  Grid steps
+    (deconvolution, two FFTs) run once at full size; node steps (gather,
+    scatter) scale linearly in the number of nodes, so the full-workload time
+    is t_grid + t_nodes * M / sample."""
+    import numpy as np
+    from oracle import nfft as onfft
+    Ms = min(int(sample), wl["M"])
+    k = wl["k"][:Ms]
+    w = wl["w"][:Ms]
+    p = onfft.Params(wl["N"], wl["sigma"], wl["m"])
+    t0 = time.perf_counter()
+    g = onfft.correction_pad(p, wl["f"])
+    t1 = time.perf_counter()
+    gh = onfft.fft_forward(g)
+    t2 = time.perf_counter()
+    onfft.resample(p, k, gh)
+    t3 = time.perf_counter()
+    ga = onfft.resample_adjoint(p, k, w)
+    t4 = time.perf_counter()
+    gg = onfft.fft_adjoint(ga)
+    t5 = time.perf_counter()
+    onfft.crop_correction(p, gg)
+    t6 = time.perf_counter()
+    t_grid = (t1 - t0) + (t2 - t1) + (t5 - t4) + (t6 - t5)
+    t_nodes = (t3 - t2) + (t4 - t3)
+    full = t_grid + t_nodes * wl["M"] / Ms
+    del np
+    return wl["M"] / full, {
+        "sample": "full %s grid, %d of %d nodes; node steps scaled by M/sample" % (
+            "x".join(str(n) for n in wl["N"]), Ms, wl["M"]),
+        "t_grid_s": round(t_grid, 3), "t_nodes_s": round(t_nodes, 3), "t_full_est_s": round(full, 3),
+        "wall_s": round(t6 - t0, 3)}
+
+
+def cpu_cores_used():
+    # numpy's FFT (pocketfft) and element-wise kernels run on one thread.
+    return 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2208_00049_gb300 import inputs
+    wl = inputs.workload(WORKLOADS[args.workload])
+    vals = []
+    det = None
+    for _ in range(max(1, args.warmup)):
+        oracle_throughput(wl, max(4096, args.cpu_sample // 8))
+    for _ in range(max(1, args.steps)):
+        v, det = oracle_throughput(wl, args.cpu_sample)
+        vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl["M"] / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded PCG64, uniform nodes)",
+        "config": {"workload": workload_desc(wl), "parallelism": "none (host cores)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": det["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_detail": det,
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(wl, kernel):
+    """Bytes a kernel must move at minimum (complex64 = 8 B, FP32 coordinate
+    = 4 B): the grid once, the nodes' coordinates once, fhat once."""
+    import numpy as np
+    grid = 8 * int(np.prod([2 * int(np.ceil(wl["sigma"] * n / 2.0 - 1e-12)) for n in wl["N"]]))
+    M, D = wl["M"], len(wl["N"])
+    nvals = 8 * int(np.prod(wl["N"]))
+    if kernel in ("gather", "scatter"):
+        return grid + M * (4 * D + 8)
+    if kernel == "deconv_pad":
+        return grid + nvals
+    if kernel == "crop_deconv":
+        return 2 * nvals
+    raise KeyError(kernel)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300 import inputs
+    from paper_2208_00049_gb300.nfft import Plan
+
+    wl = inputs.workload(WORKLOADS[args.workload])
+    dt = torch.complex64 if wl["dtype"] == "c64" else torch.complex128
+    stream = torch.cuda.current_stream()
+    plan = Plan(wl["N"], wl["M"], sigma=wl["sigma"], m=wl["m"], dtype=dt)
+    k_d = torch.from_numpy(wl["k"]).cuda()
+    f_d = torch.from_numpy(wl["f"]).to(dt).cuda()
+    w_d = torch.from_numpy(wl["w"]).to(dt).cuda()
+    fhat_d = torch.empty(wl["M"], dtype=dt, device="cuda")
+    y_d = torch.empty(wl["N"], dtype=dt, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # set_nodes (precomputation), timed separately
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    plan.set_nodes(k_d)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    plan.set_nodes(k_d)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    set_nodes_ms = ev[0].elapsed_time(ev[1])
+    info = plan.info()
+
+    h = plan.handle
+    names = ["deconv_pad", "fft_fwd", "gather", "scatter", "fft_inv", "crop_deconv"]
+
+    def step(evs):
+        evs[0].record(stream)
+        B.check(B.nfft_step_deconv_pad(h, f_d.data_ptr()))
+        evs[1].record(stream)
+        B.check(B.nfft_step_fft(h, -1))
+        evs[2].record(stream)
+        B.check(B.nfft_step_gather(h, fhat_d.data_ptr()))
+        evs[3].record(stream)
+        B.check(B.nfft_step_scatter(h, w_d.data_ptr()))
+        evs[4].record(stream)
+        B.check(B.nfft_step_fft(h, +1))
+        evs[5].record(stream)
+        B.check(B.nfft_step_crop_deconv(h, y_d.data_ptr()))
+        evs[6].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step([torch.cuda.Event(enable_timing=True) for _ in range(7)])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    all_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            step(all_ev[i])
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    B.check(B.nfft_plan_sync(h))
+
+    per = {n: [] for n in names}
+    steps_ms = []
+    for evs in all_ev:
+        steps_ms.append(evs[0].elapsed_time(evs[6]))
+        for j, n in enumerate(names):
+            per[n].append(evs[j].elapsed_time(evs[j + 1]))
+    total_ms = sum(steps_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * wl["M"] / (ms_per_step * 1e-3)
+    mean = {n: statistics.mean(v) for n, v in per.items()}
+    conv_ms = mean["deconv_pad"] + mean["gather"] + mean["scatter"] + mean["crop_deconv"]
+
+    # roofline of the dominant kernel
+    dom = "gather" if mean["gather"] >= mean["scatter"] else "scatter"
+    peak, peak_kind = measured_peak()
+    abytes = algorithmic_bytes(wl, dom)
+    achieved = abytes / (mean[dom] * 1e-3) / 1e9
+    traffic = profiled_traffic(dom, args.workload)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "algorithmic_bytes": abytes}
+    kernel_table = {}
+    for n in names:
+        entry = {"ms": round(mean[n], 4)}
+        if n in ("deconv_pad", "gather", "scatter", "crop_deconv"):
+            ab = algorithmic_bytes(wl, n)
+            entry["GBps"] = round(ab / (mean[n] * 1e-3) / 1e9, 1)
+            entry["hbm_frac"] = round(ab / (mean[n] * 1e-3) / 1e9 / peak, 4)
+        kernel_table[n] = entry
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        f_h = torch.from_numpy(wl["f"]).to(dt).pin_memory()
+        w_h = torch.from_numpy(wl["w"]).to(dt).pin_memory()
+        fh_h = torch.empty(wl["M"], dtype=dt).pin_memory()
+        y_h = torch.empty(wl["N"], dtype=dt).pin_memory()
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for _ in range(2):
+            plan.forward(f_h, out=fh_h)
+            plan.adjoint(w_h, out=y_h)
+        times = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            ee[0].record(stream)
+            plan.forward(f_h, out=fh_h)
+            plan.adjoint(w_h, out=y_h)
+            ee[1].record(stream)
+            torch.cuda.synchronize()
+            times.append(ee[0].elapsed_time(ee[1]))
+        e2e_ms = statistics.mean(times)
+        if world > 1:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        nb = f_h.numel() * f_h.element_size() + w_h.numel() * w_h.element_size()
+        ob = fh_h.numel() * fh_h.element_size() + y_h.numel() * y_h.element_size()
+        e2e = {"value": world * wl["M"] / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": ob, "ms_per_step": round(e2e_ms, 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, det = oracle_throughput(wl, args.cpu_sample)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": det["sample"], "detail": det}
+
+    launches_per_step = 4  # deconv_pad, gather, scatter, crop_deconv (cuFFT and memset not counted)
+    plan.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dt == torch.complex64 else "f64",
+            "data": "synthetic (seeded PCG64, uniform nodes)",
+            "config": {"workload": workload_desc(wl), "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "tile": list(info["tile"]), "work_items": info["n_items"]},
+            "nodes_per_s_excl_fft": world * wl["M"] / (conv_ms * 1e-3),
+            "set_nodes_ms": round(set_nodes_ms, 3),
+            "kernels": kernel_table,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    del np
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

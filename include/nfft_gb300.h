@@ -1,0 +1,175 @@
+/*
+ * nfft_gb300.h -- C ABI of the GB300 (sm_103a) NFFT window-convolution library.
+ *
+ * The library computes the nonequispaced fast Fourier transform of
+ * arXiv 2208.00049 (NFFT.jl), Sec. 2.2:
+ *
+ *   direct  (Algorithm 1):  fhat = B F D f      fhat_j ~ sum_{n in I_N} f_n e^{-2 pi i n.k_j}
+ *   adjoint (Algorithm 2):  y    = D^T F^H B^T fhat   y_n ~ sum_j fhat_j e^{+2 pi i n.k_j}
+ *
+ * with D the resampling correction (deconvolution) plus zero pad / crop,
+ * F the FFT on the sigma-oversampled grid (cuFFT), and B the sparse
+ * window-resampling matrix (Eq. Bmatrix) built from a Kaiser-Bessel window
+ * truncated to [-m, m) grid cells (2m points per dimension, Sec. 3.7.5).
+ *
+ * Conventions (all entry points):
+ *  - Arrays are row-major (C order).  f and y have shape (N_1, ..., N_D) with
+ *    array index i_d = n_d + floor(N_d/2) for n in I_N (Sec. 2.1).  Nodes k
+ *    have shape (M, D), k[j][d] in [-1/2, 1/2) (values outside are wrapped
+ *    periodically).  fhat has M entries in the caller's node order.
+ *  - Complex values are interleaved (re, im): complex64 (NFFT_C64) or
+ *    complex128 (NFFT_C128).  The plan's dtype fixes the real type of every
+ *    buffer except k, whose type is given to nfft_set_nodes.
+ *  - Buffers are owned by the caller and must be contiguous.  Pointers may be
+ *    device pointers (the call is then asynchronous on the plan's stream) or
+ *    host pointers (pageable or pinned); with a host pointer the library
+ *    stages the data through plan-owned device memory and the call returns
+ *    only once host outputs are written.
+ *  - The plan owns the oversampled grid, the sorted node records, the
+ *    deconvolution vectors, the cuFFT plan and all scratch memory.
+ *  - Every entry point returns an int status: NFFT_OK (0) or a negative
+ *    NFFT_ERR_* code.  No C++ exception crosses the ABI.  A failure inside a
+ *    CUDA or cuFFT call is latched in the plan (sticky) and returned by every
+ *    later call on that plan until it is destroyed.
+ */
+#ifndef NFFT_GB300_H
+#define NFFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define NFFT_OK                 0
+#define NFFT_ERR_INVALID_ARG   -1   /* argument out of range, null pointer, bad shape */
+#define NFFT_ERR_NO_NODES      -2   /* a transform was requested before nfft_set_nodes */
+#define NFFT_ERR_OOM           -3   /* device allocation failed */
+#define NFFT_ERR_CUFFT         -4   /* cuFFT returned an error */
+#define NFFT_ERR_CUDA          -5   /* CUDA runtime returned an error */
+#define NFFT_ERR_TIMEOUT       -6   /* a bounded device wait gave up */
+#define NFFT_ERR_DEVICE_CHECK  -7   /* a device-side range check failed */
+#define NFFT_ERR_UNSUPPORTED   -8   /* valid but not supported by this build */
+
+/* ---- dtypes and flags ------------------------------------------------ */
+#define NFFT_C64   0   /* complex64 data, FP32 resampling, FP32 accumulation */
+#define NFFT_C128  1   /* complex128 data, FP64 everywhere */
+
+/* Support [-m, m] instead of [-m, m): nodes exactly on a grid line get the
+   extra tap at u = +m, i.e. the (2m+1)^D footprint discussed in Sec. 3.7.5. */
+#define NFFT_FLAG_CLOSED_SUPPORT  0x1u
+/* FP32 scatter: each shared-memory tile sum also accumulates the rounding
+   error of every addition (TwoSum) and adds it back at the flush. */
+#define NFFT_FLAG_COMPENSATED     0x2u
+
+typedef struct nfft_plan nfft_plan;
+
+/* ---- plan ------------------------------------------------------------- */
+
+/* Create a plan (Sec. 3.1-3.2: the plan allocates every temporary and does
+ * the precomputation).
+ *   out    : receives the plan; *out is NULL on failure.
+ *   D      : dimension, 1..3.
+ *   N      : N[0..D-1], each >= 2 (even or odd).
+ *   M      : number of nodes, >= 0 (0 gives empty transforms).
+ *   sigma  : oversampling factor > 1; N~_d = sigma N_d rounded up to even.
+ *   m      : window half-width, 1..8, with 2m < N~_d.
+ *   dtype  : NFFT_C64 or NFFT_C128.
+ *   flags  : NFFT_FLAG_* bits.
+ *   stream : cudaStream_t on which every later call enqueues its work
+ *            (NULL = legacy default stream).
+ * Precomputation done here on the device, in FP64 (Sec. 3.5): the
+ * deconvolution vectors beta_d(n_d) = 1/I0(m sqrt(b^2 - (2 pi n_d/N~_d)^2)),
+ * b = pi (2 - N_d/N~_d).  The current CUDA device becomes the plan's device.
+ */
+int nfft_plan_create(nfft_plan **out, int D, const int64_t *N, int64_t M,
+                     double sigma, int m, int dtype, uint32_t flags,
+                     void *stream);
+
+/* Release everything the plan owns.  NULL is accepted. */
+int nfft_plan_destroy(nfft_plan *p);
+
+/* Set the nodes (Sec. 3.7.3: nodes are grouped by the grid block R_p they
+ * fall in).  k: (M, D) array, FP64 if k_is_fp64 != 0 else FP32 (for either
+ * plan dtype; FP32 nodes are promoted to FP64), host or device.  In FP64,
+ * x = N~_d k_{j,d} is split into the cell floor(x) mod N~_d and the fraction
+ * x - floor(x) (rounded to the plan's real type); nodes are bin-sorted by
+ * grid tile on the device.  The library copies what it needs: the caller
+ * may free k on return (device k: once the stream reaches this call). */
+int nfft_set_nodes(nfft_plan *p, const void *k, int k_is_fp64);
+
+/* Direct NFFT, Algorithm 1: fhat = B F D f.  f: N_1 x ... x N_D complex,
+ * fhat: M complex. */
+int nfft_forward(nfft_plan *p, const void *f, void *fhat);
+
+/* Adjoint NFFT, Algorithm 2: y = D^T F^H B^T fhat.  fhat: M complex,
+ * y: N_1 x ... x N_D complex. */
+int nfft_adjoint(nfft_plan *p, const void *fhat, void *y);
+
+/* Node gradient through the direct NFFT (the paper defines none; this is
+ * the derivative of Eq. SumOverNode with respect to k_{j,d}):
+ *   gk[j][d] = Re( conj(cot_j) * d fhat_j / d k_{j,d} ),
+ *   d fhat_j / d k_{j,d} = N~_d sum_l ghat_l psi'(u_d) prod_{e != d} psi(u_e),
+ * ghat = F D f.  cot: M complex (the upstream gradient of a real loss with
+ * respect to fhat, PyTorch convention); gk: (M, D) real of the plan's real
+ * type.  The same call gives the node gradient of y = A^H w for upstream Y
+ * with f := Y and cot := w. */
+int nfft_grad(nfft_plan *p, const void *f, const void *cot, void *gk);
+
+/* Block the host until all work enqueued by this plan has finished; returns
+ * the first error seen. */
+int nfft_plan_sync(nfft_plan *p);
+
+/* Static, human-readable text for a status code. */
+const char *nfft_strerror(int code);
+
+/* ---- introspection and the individual steps ---------------------------
+ * The transforms above are compositions of these steps; they are exported
+ * so that each step can be timed and checked on its own.  All take device
+ * pointers and run asynchronously on the plan's stream. */
+
+/* N~ (oversampled sizes), the tile shape in grid cells, and the number of
+ * work items of the current node set (0 before nfft_set_nodes; reading it
+ * synchronises the plan's stream). */
+int nfft_plan_info(nfft_plan *p, int64_t *Ntilde3, int64_t *tile3, int64_t *n_items);
+
+/* Device pointer to the plan's oversampled grid (N~_1 x ... x N~_D complex,
+ * natural FFT order: grid index l is stored at position l mod N~). */
+void *nfft_plan_grid(nfft_plan *p);
+
+/* Choose the tile shape (grid cells per tile per dimension) used by the
+ * resampling kernels; takes effect at the next nfft_set_nodes.  Used by the
+ * autotuner.  Tiles must satisfy 1 <= tile_d <= N~_d and fit the shared
+ * memory limit with their halo. */
+int nfft_plan_set_tile(nfft_plan *p, const int64_t *tile3);
+
+/* Algorithm 1 lines 1-3: resampling correction and zero pad of f into the
+ * plan grid (fftshift folded into the index map, Sec. 3.5). */
+int nfft_step_deconv_pad(nfft_plan *p, const void *f);
+
+/* Algorithm 1 lines 4-6 (sign = -1, cuFFT FORWARD) or Algorithm 2 lines 4-6
+ * (sign = +1, cuFFT INVERSE, unnormalised), in place on the plan grid. */
+int nfft_step_fft(nfft_plan *p, int sign);
+
+/* Algorithm 1 lines 7-9 / Algorithm 3: block-partitioned resampling
+ * (gather) from the plan grid to fhat (M complex, caller order). */
+int nfft_step_gather(nfft_plan *p, void *fhat);
+
+/* Algorithm 2 lines 1-3 / Algorithm 4: block-partitioned adjoint resampling
+ * (scatter) of fhat onto the plan grid; the grid is cleared first. */
+int nfft_step_scatter(nfft_plan *p, const void *fhat);
+
+/* Algorithm 2 lines 8-10: crop of the plan grid to I_N and resampling
+ * correction into y. */
+int nfft_step_crop_deconv(nfft_plan *p, void *y);
+
+/* Node-gradient resampling on the current plan grid (which must hold
+ * ghat = F D f): gk[j][d] = Re(conj(cot_j) d fhat_j / d k_{j,d}). */
+int nfft_step_grad_gather(nfft_plan *p, const void *cot, void *gk);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NFFT_GB300_H */

@@ -127,18 +127,15 @@ def resample_adjoint(p, k, fhat):
     ls, us = footprint(p, k)
     w = [psi(u, p.m, b, p.closed) for u, b in zip(us, p.b)]
     M = fhat.shape[0]
-    size = int(np.prod(p.Nt))
-    acc_re = np.zeros(size)
-    acc_im = np.zeros(size)
+    acc = np.zeros(int(np.prod(p.Nt)), dtype=np.complex128)
     for tap in itertools.product(range(p.taps()), repeat=p.D):
         idx = tuple(np.mod(ls[d][:, tap[d]], p.Nt[d]) for d in range(p.D))
         flat = np.ravel_multi_index(idx, p.Nt)
         wt = np.ones(M)
         for d in range(p.D):
             wt = wt * w[d][:, tap[d]]
-        acc_re += np.bincount(flat, weights=fhat.real * wt, minlength=size)
-        acc_im += np.bincount(flat, weights=fhat.imag * wt, minlength=size)
-    return (acc_re + 1j * acc_im).reshape(p.Nt)
+        np.add.at(acc, flat, fhat * wt)
+    return acc.reshape(p.Nt)
 
 
 def fft_forward(g):

@@ -1,0 +1,173 @@
+"""ctypes binding of libnfft_gb300.so: the C ABI of include/nfft_gb300.h under
+the same names, argument marshalling only.
+
+Every function takes plain integers (pointers as ints) and returns the C
+status code; ``check`` turns a non-zero status into ``NFFTError``.  Loading
+fails loudly if the library has not been built: there is no fallback path.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libnfft_gb300.so")
+
+NFFT_OK = 0
+NFFT_ERR_INVALID_ARG = -1
+NFFT_ERR_NO_NODES = -2
+NFFT_ERR_OOM = -3
+NFFT_ERR_CUFFT = -4
+NFFT_ERR_CUDA = -5
+NFFT_ERR_TIMEOUT = -6
+NFFT_ERR_DEVICE_CHECK = -7
+NFFT_ERR_UNSUPPORTED = -8
+
+NFFT_C64 = 0
+NFFT_C128 = 1
+NFFT_FLAG_CLOSED_SUPPORT = 0x1
+NFFT_FLAG_COMPENSATED = 0x2
+
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes), in header order
+SIGNATURES = {
+    "nfft_plan_create": (_i, [ctypes.POINTER(_p), _i, _i64p, ctypes.c_int64, ctypes.c_double, _i, _i,
+                              ctypes.c_uint32, _p]),
+    "nfft_plan_destroy": (_i, [_p]),
+    "nfft_set_nodes": (_i, [_p, _p, _i]),
+    "nfft_forward": (_i, [_p, _p, _p]),
+    "nfft_adjoint": (_i, [_p, _p, _p]),
+    "nfft_grad": (_i, [_p, _p, _p, _p]),
+    "nfft_plan_sync": (_i, [_p]),
+    "nfft_strerror": (ctypes.c_char_p, [_i]),
+    "nfft_plan_info": (_i, [_p, _i64p, _i64p, _i64p]),
+    "nfft_plan_grid": (_p, [_p]),
+    "nfft_plan_set_tile": (_i, [_p, _i64p]),
+    "nfft_step_deconv_pad": (_i, [_p, _p]),
+    "nfft_step_fft": (_i, [_p, _i]),
+    "nfft_step_gather": (_i, [_p, _p]),
+    "nfft_step_scatter": (_i, [_p, _p]),
+    "nfft_step_crop_deconv": (_i, [_p, _p]),
+    "nfft_step_grad_gather": (_i, [_p, _p, _p]),
+}
+
+_lib = None
+
+
+class NFFTError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (where or "nfft", strerror(code), code))
+
+
+def lib():
+    """Load the library once; raise if it is missing (no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libnfft_gb300.so is not built (expected at %s); run "
+                "paper_2208_00049_gb300.build.build() first" % LIB_PATH)
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def strerror(code):
+    return lib().nfft_strerror(int(code)).decode()
+
+
+def check(code, where=""):
+    if code != NFFT_OK:
+        raise NFFTError(code, where)
+    return code
+
+
+def _i64_array(vals, n=3):
+    arr = (ctypes.c_int64 * n)()
+    for i, v in enumerate(vals):
+        arr[i] = int(v)
+    return arr
+
+
+def nfft_plan_create(D, N, M, sigma, m, dtype, flags, stream):
+    """Returns (status, plan handle as int or None)."""
+    out = _p()
+    Narr = _i64_array(N, max(3, len(N)))
+    s = lib().nfft_plan_create(ctypes.byref(out), int(D), Narr, int(M), float(sigma), int(m),
+                               int(dtype), int(flags), _p(stream or None))
+    return s, out.value
+
+
+def nfft_plan_destroy(plan):
+    return lib().nfft_plan_destroy(_p(plan))
+
+
+def nfft_set_nodes(plan, k_ptr, k_is_fp64):
+    return lib().nfft_set_nodes(_p(plan), _p(k_ptr), int(k_is_fp64))
+
+
+def nfft_forward(plan, f_ptr, fhat_ptr):
+    return lib().nfft_forward(_p(plan), _p(f_ptr), _p(fhat_ptr))
+
+
+def nfft_adjoint(plan, fhat_ptr, y_ptr):
+    return lib().nfft_adjoint(_p(plan), _p(fhat_ptr), _p(y_ptr))
+
+
+def nfft_grad(plan, f_ptr, cot_ptr, gk_ptr):
+    return lib().nfft_grad(_p(plan), _p(f_ptr), _p(cot_ptr), _p(gk_ptr))
+
+
+def nfft_plan_sync(plan):
+    return lib().nfft_plan_sync(_p(plan))
+
+
+def nfft_strerror(code):
+    return strerror(code)
+
+
+def nfft_plan_info(plan):
+    """Returns (status, Ntilde3, tile3, n_items)."""
+    nt = (ctypes.c_int64 * 3)()
+    tl = (ctypes.c_int64 * 3)()
+    ni = ctypes.c_int64()
+    s = lib().nfft_plan_info(_p(plan), nt, tl, ctypes.byref(ni))
+    return s, tuple(nt), tuple(tl), ni.value
+
+
+def nfft_plan_grid(plan):
+    return lib().nfft_plan_grid(_p(plan))
+
+
+def nfft_plan_set_tile(plan, tile3):
+    return lib().nfft_plan_set_tile(_p(plan), _i64_array(list(tile3) + [1] * (3 - len(tile3))))
+
+
+def nfft_step_deconv_pad(plan, f_ptr):
+    return lib().nfft_step_deconv_pad(_p(plan), _p(f_ptr))
+
+
+def nfft_step_fft(plan, sign):
+    return lib().nfft_step_fft(_p(plan), int(sign))
+
+
+def nfft_step_gather(plan, fhat_ptr):
+    return lib().nfft_step_gather(_p(plan), _p(fhat_ptr))
+
+
+def nfft_step_scatter(plan, fhat_ptr):
+    return lib().nfft_step_scatter(_p(plan), _p(fhat_ptr))
+
+
+def nfft_step_crop_deconv(plan, y_ptr):
+    return lib().nfft_step_crop_deconv(_p(plan), _p(y_ptr))
+
+
+def nfft_step_grad_gather(plan, cot_ptr, gk_ptr):
+    return lib().nfft_step_grad_gather(_p(plan), _p(cot_ptr), _p(gk_ptr))

@@ -1,0 +1,130 @@
+// Internal declarations shared by the translation units of libnfft_gb300.
+//
+// Layout in HBM (see nfft_plan.cu for allocation):
+//   grid   : N~_0 x ... x N~_{D-1} complex, row-major, natural FFT order
+//            (grid index l lives at position l mod N~_d).
+//   cell   : D planes of M int32, the sorted nodes' cells floor(N~_d k) mod N~_d
+//   frac   : D planes of M reals, the sorted nodes' fractions N~_d k - floor(.)
+//   perm   : M int32, sorted position -> caller's node index
+//   items  : work items {tile, first sorted node, node count, 0}
+//   beta   : sum_d N_d reals, the scaled deconvolution vectors
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include "nfft_gb300.h"
+
+namespace nfftgb {
+
+constexpr int kMaxD = 3;
+constexpr int kResampleThreads = 128;
+constexpr int kMaxM = 8;
+
+// Everything a resampling kernel needs about the plan, passed by value.
+// Dimension d = D-1 is the contiguous one.
+struct Geometry {
+  int D;
+  int Nt[kMaxD];     // oversampled sizes
+  int T[kMaxD];      // tile extent in grid cells
+  int ntile[kMaxD];  // tiles per dimension
+  int L[kMaxD];      // shared-memory region extent = T + K - 1
+  int K;             // taps per dimension held by the kernel template
+  int off;           // footprint start relative to the cell: -m+1 (or -m closed)
+  int closed;        // support [-m, m] instead of [-m, m)
+  int M;             // number of nodes
+  double m;          // window half-width
+  double b[kMaxD];   // Kaiser-Bessel shape per dimension
+  double norm[kMaxD];  // m / sinh(b m): scales the window to 1 at u = 0
+};
+
+// Kaiser-Bessel window in grid units, scaled to 1 at u = 0:
+//   w(u) = [sinh(b s)/s] * m/sinh(b m),  s = sqrt(m^2 - u^2).
+// s^2 is formed as (m - u)(m + u) from the integer and fractional parts of
+// u so that it stays accurate near the support edges.  At s = 0 the value
+// is the limit b * m/sinh(b m).
+template <typename R>
+__device__ __forceinline__ R kb_window(R mm_u, R mp_u, R b, R norm) {
+  R s2 = mm_u * mp_u;
+  R s = sqrt(s2 > R(0) ? s2 : R(0));
+  R z = b * s;
+  R r = (z < R(1e-3)) ? b * (R(1) + z * z * R(1.0 / 6.0)) : sinh(z) / s;
+  return r * norm;
+}
+
+// Derivative of the scaled window with respect to u:
+//   w'(u) = -u (b s cosh(b s) - sinh(b s)) / s^3 * m/sinh(b m)
+// with the series b^3 (1/3 + z^2/30 + z^4/840 + z^6/45360) for small z = b s.
+template <typename R>
+__device__ __forceinline__ R kb_window_deriv(R u, R mm_u, R mp_u, R b, R norm, R zsmall) {
+  R s2 = mm_u * mp_u;
+  R s = sqrt(s2 > R(0) ? s2 : R(0));
+  R z = b * s;
+  R h;
+  if (z < zsmall) {
+    R z2 = z * z;
+    h = b * b * b * (R(1.0 / 3.0) + z2 * (R(1.0 / 30.0) + z2 * (R(1.0 / 840.0) + z2 * R(1.0 / 45360.0))));
+  } else {
+    h = (z * cosh(z) - sinh(z)) / (s * s * s);
+  }
+  return -u * h * norm;
+}
+
+// ---- launchers (one per translation unit) ------------------------------
+struct NodeArrays {
+  const int* cell;   // D planes of M
+  const void* frac;  // D planes of M reals
+  const int* perm;   // M
+  const int4* items;
+  const int* n_items;
+};
+
+template <typename R>
+cudaError_t launch_gather(const Geometry& g, const void* grid, const NodeArrays& na,
+                          void* fhat, int grid_ctas, cudaStream_t s);
+template <typename R>
+cudaError_t launch_scatter(const Geometry& g, void* grid, const NodeArrays& na,
+                           const void* fhat, int compensated, int grid_ctas, cudaStream_t s);
+template <typename R>
+cudaError_t launch_grad_gather(const Geometry& g, const void* grid, const NodeArrays& na,
+                               const void* cot, void* gk, int grid_ctas, cudaStream_t s);
+template <typename R>
+size_t resample_smem_bytes(const Geometry& g, int kind);  // kind 0 gather, 1 scatter, 2 scatter+comp
+template <typename R>
+int resample_ctas_per_sm(const Geometry& g, int kind);
+
+// deconvolution, tables, sorting (nfft_kernels.cu)
+struct DeconvArgs {
+  int D;
+  int N[kMaxD];
+  int Nt[kMaxD];
+  const void* beta[kMaxD];  // per-dimension beta vectors (plan real type)
+};
+template <typename R>
+cudaError_t launch_deconv_pad(const DeconvArgs& a, const void* f, void* grid, cudaStream_t s);
+template <typename R>
+cudaError_t launch_crop_deconv(const DeconvArgs& a, const void* grid, void* y, cudaStream_t s);
+
+cudaError_t launch_build_beta(int D, const int* N, const int* Nt, int m, const double* b,
+                              double* beta64, float* beta32, cudaStream_t s);
+
+struct SortArgs {
+  int D;
+  int M;
+  int Nt[kMaxD];
+  int T[kMaxD];
+  int ntile[kMaxD];
+  int n_tiles;
+  int cmax;
+  int max_items;
+};
+cudaError_t launch_node_count(const SortArgs& a, const void* k, int k_is_fp64, int* tile_count,
+                              int* key, int* rank, cudaStream_t s);
+cudaError_t launch_tile_scan(const SortArgs& a, const int* tile_count, int* tile_offset,
+                             int4* items, int* n_items, cudaStream_t s);
+cudaError_t launch_node_place(const SortArgs& a, const void* k, int k_is_fp64, const int* key,
+                              const int* rank, const int* tile_offset, int* cell, void* frac,
+                              int frac_is_fp64, int* perm, cudaStream_t s);
+
+}  // namespace nfftgb

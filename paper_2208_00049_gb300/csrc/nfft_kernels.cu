@@ -1,0 +1,377 @@
+// Deconvolution (resampling correction), plan-time tables and node bin-sort.
+//
+// arXiv 2208.00049:
+//  * Algorithm 1 lines 1-3 and Algorithm 2 lines 8-10: the resampling
+//    correction 1/(|I_N~| phi(n)) with zero pad (direct) or crop (adjoint);
+//    Sec. 3.5 folds the fftshift into the index map and factorises the
+//    correction into per-dimension vectors beta_d (O(sum N_d) memory).
+//  * Sec. 3.7.3: nodes are grouped by the grid block they fall in (the sets
+//    Gamma_p); here by a device counting sort over tiles, with tiles holding
+//    more than `cmax` nodes split into several work items (fixed number of
+//    points per block, Sec. 3.7.2).
+#include "nfft_internal.cuh"
+
+namespace nfftgb {
+
+template <typename R>
+struct Cplx;
+template <>
+struct Cplx<float> {
+  using type = float2;
+};
+template <>
+struct Cplx<double> {
+  using type = double2;
+};
+
+static int launch_blocks(int64_t work, int threads) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t want = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)sms * 16;
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
+// ---------------------------------------------------------------------------
+// beta_d(n_d) = W_d(0) / I0(m sqrt(b_d^2 - (2 pi n_d / N~_d)^2)), n_d in I_{N_d},
+// in FP64 on the device.  W_d(0) = sinh(b_d m)/(pi m) is the peak of the
+// window, which the resampling kernels divide out of their weights; the
+// product over d of these factors is 1/(|I_N~| phi(n)) times that peak.
+// ---------------------------------------------------------------------------
+struct BetaArgs {
+  int D;
+  int N[kMaxD];
+  int Nt[kMaxD];
+  int offset[kMaxD];
+  double b[kMaxD];
+  int m;
+};
+
+__global__ void build_beta_kernel(BetaArgs a, double* beta64, float* beta32) {
+  int total = a.offset[a.D - 1] + a.N[a.D - 1];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int d = 0;
+    while (d + 1 < a.D && idx >= a.offset[d + 1]) ++d;
+    int i = idx - a.offset[d];
+    double n = (double)(i - a.N[d] / 2);
+    double w = 2.0 * M_PI * n / (double)a.Nt[d];
+    double bb = a.b[d];
+    double arg = (double)a.m * sqrt(bb * bb - w * w);
+    double peak = sinh(bb * (double)a.m) / (M_PI * (double)a.m);
+    double v = peak / cyl_bessel_i0(arg);
+    beta64[idx] = v;
+    beta32[idx] = (float)v;
+  }
+}
+
+cudaError_t launch_build_beta(int D, const int* N, const int* Nt, int m, const double* b,
+                              double* beta64, float* beta32, cudaStream_t s) {
+  BetaArgs a{};
+  a.D = D;
+  a.m = m;
+  int off = 0;
+  for (int d = 0; d < D; ++d) {
+    a.N[d] = N[d];
+    a.Nt[d] = Nt[d];
+    a.b[d] = b[d];
+    a.offset[d] = off;
+    off += N[d];
+  }
+  build_beta_kernel<<<launch_blocks(off, 256), 256, 0, s>>>(a, beta64, beta32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 lines 1-3: g[p] = f_n * prod_d beta_d(n_d) where the grid
+// position p_d = n_d mod N~_d, zero at every other position.  One thread
+// writes two adjacent grid points (16 B for complex64) of the last dimension.
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void deconv_pad_kernel(DeconvArgs a, const typename Cplx<R>::type* __restrict__ f,
+                                  typename Cplx<R>::type* __restrict__ grid) {
+  using C = typename Cplx<R>::type;
+  const R* __restrict__ beta0 = (const R*)a.beta[0];
+  const R* __restrict__ beta1 = (const R*)a.beta[D > 1 ? 1 : 0];
+  const R* __restrict__ beta2 = (const R*)a.beta[D > 2 ? 2 : 0];
+  const int last = D - 1;
+  const int half_last = a.Nt[last] / 2;  // pairs per row
+  int64_t rows = 1;
+  for (int d = 0; d < last; ++d) rows *= a.Nt[d];
+  const int64_t total = rows * half_last;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int pair = (int)(t % half_last);
+    int64_t row = t / half_last;
+    // index into f of the outer dimensions; -1 if outside I_N
+    int64_t frow = 0;
+    R scale = R(1);
+    bool inside = true;
+    if constexpr (D == 3) {
+      int p1 = (int)(row % a.Nt[1]);
+      int p0 = (int)(row / a.Nt[1]);
+      int l0 = p0 < a.Nt[0] / 2 ? p0 : p0 - a.Nt[0];
+      int l1 = p1 < a.Nt[1] / 2 ? p1 : p1 - a.Nt[1];
+      int i0 = l0 + a.N[0] / 2, i1 = l1 + a.N[1] / 2;
+      inside = (i0 >= 0 && i0 < a.N[0] && i1 >= 0 && i1 < a.N[1]);
+      if (inside) {
+        frow = (int64_t)i0 * a.N[1] + i1;
+        scale = beta0[i0] * beta1[i1];
+      }
+    } else if constexpr (D == 2) {
+      int p0 = (int)row;
+      int l0 = p0 < a.Nt[0] / 2 ? p0 : p0 - a.Nt[0];
+      int i0 = l0 + a.N[0] / 2;
+      inside = (i0 >= 0 && i0 < a.N[0]);
+      if (inside) {
+        frow = i0;
+        scale = beta0[i0];
+      }
+    }
+    C out[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = 2 * pair + h;
+      const int l = p < a.Nt[last] / 2 ? p : p - a.Nt[last];
+      const int i = l + a.N[last] / 2;
+      C v;
+      v.x = R(0);
+      v.y = R(0);
+      if (inside && i >= 0 && i < a.N[last]) {
+        const R* bl = (D == 1) ? beta0 : (D == 2 ? beta1 : beta2);
+        const C x = f[frow * a.N[last] + i];
+        const R s = scale * bl[i];
+        v.x = x.x * s;
+        v.y = x.y * s;
+      }
+      out[h] = v;
+    }
+    C* dst = grid + row * a.Nt[last] + 2 * pair;
+    dst[0] = out[0];
+    dst[1] = out[1];
+  }
+}
+
+// Algorithm 2 lines 8-10: y_n = g[n mod N~] * prod_d beta_d(n_d), n in I_N.
+template <int D, typename R>
+__global__ void crop_deconv_kernel(DeconvArgs a, const typename Cplx<R>::type* __restrict__ grid,
+                                   typename Cplx<R>::type* __restrict__ y) {
+  using C = typename Cplx<R>::type;
+  const R* __restrict__ beta0 = (const R*)a.beta[0];
+  const R* __restrict__ beta1 = (const R*)a.beta[D > 1 ? 1 : 0];
+  const R* __restrict__ beta2 = (const R*)a.beta[D > 2 ? 2 : 0];
+  int64_t total = 1;
+  for (int d = 0; d < D; ++d) total *= a.N[d];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = t;
+    int i[kMaxD];
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) {
+      i[d] = (int)(rem % a.N[d]);
+      rem /= a.N[d];
+    }
+    int64_t lin = 0;
+    R s = R(1);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      int n = i[d] - a.N[d] / 2;
+      int p = n < 0 ? n + a.Nt[d] : n;
+      lin = lin * a.Nt[d] + p;
+      const R* bd = d == 0 ? beta0 : (d == 1 ? beta1 : beta2);
+      s *= bd[i[d]];
+    }
+    C g = grid[lin];
+    C out;
+    out.x = g.x * s;
+    out.y = g.y * s;
+    y[t] = out;
+  }
+}
+
+template <typename R>
+cudaError_t launch_deconv_pad(const DeconvArgs& a, const void* f, void* grid, cudaStream_t s) {
+  using C = typename Cplx<R>::type;
+  int64_t total = 1;
+  for (int d = 0; d < a.D; ++d) total *= a.Nt[d];
+  int blocks = launch_blocks(total / 2, 256);
+  if (a.D == 1)
+    deconv_pad_kernel<1, R><<<blocks, 256, 0, s>>>(a, (const C*)f, (C*)grid);
+  else if (a.D == 2)
+    deconv_pad_kernel<2, R><<<blocks, 256, 0, s>>>(a, (const C*)f, (C*)grid);
+  else
+    deconv_pad_kernel<3, R><<<blocks, 256, 0, s>>>(a, (const C*)f, (C*)grid);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_crop_deconv(const DeconvArgs& a, const void* grid, void* y, cudaStream_t s) {
+  using C = typename Cplx<R>::type;
+  int64_t total = 1;
+  for (int d = 0; d < a.D; ++d) total *= a.N[d];
+  int blocks = launch_blocks(total, 256);
+  if (a.D == 1)
+    crop_deconv_kernel<1, R><<<blocks, 256, 0, s>>>(a, (const C*)grid, (C*)y);
+  else if (a.D == 2)
+    crop_deconv_kernel<2, R><<<blocks, 256, 0, s>>>(a, (const C*)grid, (C*)y);
+  else
+    crop_deconv_kernel<3, R><<<blocks, 256, 0, s>>>(a, (const C*)grid, (C*)y);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_deconv_pad<float>(const DeconvArgs&, const void*, void*, cudaStream_t);
+template cudaError_t launch_deconv_pad<double>(const DeconvArgs&, const void*, void*, cudaStream_t);
+template cudaError_t launch_crop_deconv<float>(const DeconvArgs&, const void*, void*, cudaStream_t);
+template cudaError_t launch_crop_deconv<double>(const DeconvArgs&, const void*, void*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Node bin-sort (set_nodes).
+// x = N~_d k_{j,d} in FP64; cell c = floor(x) mod N~_d; fraction t = x - floor(x).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double load_k(const void* k, int k_is_fp64, int64_t idx) {
+  return k_is_fp64 ? ((const double*)k)[idx] : (double)((const float*)k)[idx];
+}
+
+__device__ __forceinline__ void split_coord(double kv, int Nt, int& cell, double& t) {
+  double x = (double)Nt * kv;
+  double fl = floor(x);
+  t = x - fl;
+  long long c = (long long)fl % (long long)Nt;
+  if (c < 0) c += Nt;
+  cell = (int)c;
+}
+
+__global__ void node_count_kernel(SortArgs a, const void* k, int k_is_fp64, int* tile_count,
+                                  int* key, int* rank) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.M; j += gridDim.x * blockDim.x) {
+    int lin = 0;
+    for (int d = 0; d < a.D; ++d) {
+      int c;
+      double t;
+      split_coord(load_k(k, k_is_fp64, (int64_t)j * a.D + d), a.Nt[d], c, t);
+      lin = lin * a.ntile[d] + c / a.T[d];
+    }
+    key[j] = lin;
+    rank[j] = atomicAdd(tile_count + lin, 1);
+  }
+}
+
+cudaError_t launch_node_count(const SortArgs& a, const void* k, int k_is_fp64, int* tile_count,
+                              int* key, int* rank, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(tile_count, 0, sizeof(int) * (size_t)a.n_tiles, s);
+  if (e != cudaSuccess) return e;
+  if (a.M == 0) return cudaSuccess;
+  node_count_kernel<<<launch_blocks(a.M, 256), 256, 0, s>>>(a, k, k_is_fp64, tile_count, key, rank);
+  return cudaGetLastError();
+}
+
+// One CTA: exclusive scan of the tile counts and of the per-tile work-item
+// counts ceil(count / cmax); then every non-empty tile writes its items.
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ int2 block_exclusive_scan2(int2 v, int2* total) {
+  __shared__ int2 warp_sums[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int2 incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int x = __shfl_up_sync(0xffffffffu, incl.x, o);
+    int y = __shfl_up_sync(0xffffffffu, incl.y, o);
+    if (lane >= o) {
+      incl.x += x;
+      incl.y += y;
+    }
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int2 ws = lane < kScanThreads / 32 ? warp_sums[lane] : make_int2(0, 0);
+    int2 wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int x = __shfl_up_sync(0xffffffffu, wi.x, o);
+      int y = __shfl_up_sync(0xffffffffu, wi.y, o);
+      if (lane >= o) {
+        wi.x += x;
+        wi.y += y;
+      }
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = make_int2(wi.x - ws.x, wi.y - ws.y);
+    if (lane == kScanThreads / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  int2 base = warp_sums[warp];
+  int2 out = make_int2(base.x + incl.x - v.x, base.y + incl.y - v.y);
+  __syncthreads();
+  return out;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    tile_scan_kernel(SortArgs a, const int* tile_count, int* tile_offset, int4* items, int* n_items) {
+  __shared__ int2 total;
+  int2 carry = make_int2(0, 0);
+  for (int base = 0; base < a.n_tiles; base += kScanThreads) {
+    const int t = base + threadIdx.x;
+    const int cnt = t < a.n_tiles ? tile_count[t] : 0;
+    const int nit = (cnt + a.cmax - 1) / a.cmax;
+    int2 ex = block_exclusive_scan2(make_int2(cnt, nit), &total);
+    __syncthreads();
+    if (t < a.n_tiles) {
+      const int off = carry.x + ex.x;
+      const int ioff = carry.y + ex.y;
+      tile_offset[t] = off;
+      for (int r = 0; r < nit && ioff + r < a.max_items; ++r) {
+        const int first = r * a.cmax;
+        const int c = min(a.cmax, cnt - first);
+        items[ioff + r] = make_int4(t, off + first, c, 0);
+      }
+    }
+    carry.x += total.x;
+    carry.y += total.y;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_items = min(carry.y, a.max_items);
+}
+
+cudaError_t launch_tile_scan(const SortArgs& a, const int* tile_count, int* tile_offset, int4* items,
+                             int* n_items, cudaStream_t s) {
+  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(a, tile_count, tile_offset, items, n_items);
+  return cudaGetLastError();
+}
+
+__global__ void node_place_kernel(SortArgs a, const void* k, int k_is_fp64, const int* key,
+                                  const int* rank, const int* tile_offset, int* cell, void* frac,
+                                  int frac_is_fp64, int* perm) {
+  const int64_t M = a.M;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.M; j += gridDim.x * blockDim.x) {
+    const int pos = tile_offset[key[j]] + rank[j];
+    for (int d = 0; d < a.D; ++d) {
+      int c;
+      double t;
+      split_coord(load_k(k, k_is_fp64, (int64_t)j * a.D + d), a.Nt[d], c, t);
+      cell[d * M + pos] = c;
+      if (frac_is_fp64) {
+        ((double*)frac)[d * M + pos] = t;
+      } else {
+        // round to FP32, keeping t < 1
+        float tf = (float)t;
+        if (tf >= 1.0f) tf = 0.99999994f;
+        ((float*)frac)[d * M + pos] = tf;
+      }
+    }
+    perm[pos] = j;
+  }
+}
+
+cudaError_t launch_node_place(const SortArgs& a, const void* k, int k_is_fp64, const int* key,
+                              const int* rank, const int* tile_offset, int* cell, void* frac,
+                              int frac_is_fp64, int* perm, cudaStream_t s) {
+  if (a.M == 0) return cudaSuccess;
+  node_place_kernel<<<launch_blocks(a.M, 256), 256, 0, s>>>(a, k, k_is_fp64, key, rank, tile_offset,
+                                                            cell, frac, frac_is_fp64, perm);
+  return cudaGetLastError();
+}
+
+}  // namespace nfftgb

@@ -1,0 +1,668 @@
+// Plan object and C ABI (see include/nfft_gb300.h).
+//
+// arXiv 2208.00049, Sec. 3.1-3.2: a plan holds every temporary (the
+// oversampled grid ghat, the FFT plans, the index/window data and the
+// blocking buffers) and does the precomputation, so that transforms allocate
+// nothing.  Algorithm 1 = deconv_pad -> FFT -> gather; Algorithm 2 =
+// scatter -> FFT^H -> crop_deconv.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "nfft_internal.cuh"
+
+using namespace nfftgb;
+
+struct nfft_plan {
+  int D = 0;
+  int64_t N[kMaxD] = {1, 1, 1};
+  int64_t Nt[kMaxD] = {1, 1, 1};
+  int64_t M = 0;
+  double sigma = 2.0;
+  int m = 4;
+  int dtype = NFFT_C64;
+  uint32_t flags = 0;
+  double b[kMaxD] = {0, 0, 0};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 1;
+  int K = 8, off = -3;
+
+  int64_t T[kMaxD] = {1, 1, 1};
+  int ntile[kMaxD] = {1, 1, 1};
+  int64_t n_tiles = 0;
+  int cmax = 256;
+  int64_t max_items = 0;
+  int ctas[4] = {0, 0, 0, 0};  // persistent grid per kernel kind
+
+  void* grid = nullptr;
+  double* beta64 = nullptr;
+  float* beta32 = nullptr;
+  int* cell = nullptr;
+  void* frac = nullptr;
+  int* perm = nullptr;
+  int* key = nullptr;
+  int* rank = nullptr;
+  int* tile_count = nullptr;
+  int* tile_offset = nullptr;
+  int4* items = nullptr;
+  int* n_items = nullptr;
+  int64_t tiles_cap = 0;
+  int64_t items_cap = 0;
+
+  void* stage[3] = {nullptr, nullptr, nullptr};
+  size_t stage_bytes[3] = {0, 0, 0};
+
+  cufftHandle fft = 0;
+  bool fft_ok = false;
+  bool has_nodes = false;
+  int err = NFFT_OK;
+};
+
+namespace {
+
+size_t real_size(const nfft_plan* p) { return p->dtype == NFFT_C128 ? 8 : 4; }
+size_t cplx_size(const nfft_plan* p) { return 2 * real_size(p); }
+int64_t prod_N(const nfft_plan* p) {
+  int64_t r = 1;
+  for (int d = 0; d < p->D; ++d) r *= p->N[d];
+  return r;
+}
+int64_t prod_Nt(const nfft_plan* p) {
+  int64_t r = 1;
+  for (int d = 0; d < p->D; ++d) r *= p->Nt[d];
+  return r;
+}
+
+int latch(nfft_plan* p, int code) {
+  if (p && p->err == NFFT_OK && code != NFFT_OK) p->err = code;
+  return code;
+}
+
+int cuda_status(nfft_plan* p, cudaError_t e) {
+  if (e == cudaSuccess) return NFFT_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return latch(p, NFFT_ERR_OOM);
+  }
+  return latch(p, NFFT_ERR_CUDA);
+}
+
+#define NFFT_CK(p, call)                         \
+  do {                                           \
+    int _s = cuda_status((p), (call));           \
+    if (_s != NFFT_OK) return _s;                \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+int dalloc(nfft_plan* p, T** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return latch(p, NFFT_ERR_OOM);
+  }
+  return NFFT_OK;
+}
+
+void dfree(void* ptr) {
+  if (ptr) cudaFree(ptr);
+}
+
+bool is_device_pointer(const void* ptr) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// Device buffer for a host argument: slot 0 = transform input, 1 = output,
+// 2 = second input.
+int stage_buffer(nfft_plan* p, int slot, size_t bytes, void** out) {
+  if (p->stage_bytes[slot] < bytes) {
+    dfree(p->stage[slot]);
+    p->stage[slot] = nullptr;
+    p->stage_bytes[slot] = 0;
+    int s = dalloc(p, &p->stage[slot], bytes);
+    if (s != NFFT_OK) return s;
+    p->stage_bytes[slot] = bytes;
+  }
+  *out = p->stage[slot];
+  return NFFT_OK;
+}
+
+// Input pointer -> device pointer (copying a host input to a stage buffer).
+int device_input(nfft_plan* p, int slot, const void* ptr, size_t bytes, const void** dev) {
+  if (bytes == 0 || is_device_pointer(ptr)) {
+    *dev = ptr;
+    return NFFT_OK;
+  }
+  void* buf = nullptr;
+  int s = stage_buffer(p, slot, bytes, &buf);
+  if (s != NFFT_OK) return s;
+  NFFT_CK(p, cudaMemcpyAsync(buf, ptr, bytes, cudaMemcpyHostToDevice, p->stream));
+  *dev = buf;
+  return NFFT_OK;
+}
+
+struct OutputBinding {
+  void* user = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+};
+
+int device_output(nfft_plan* p, int slot, void* ptr, size_t bytes, OutputBinding* ob) {
+  ob->user = ptr;
+  ob->bytes = bytes;
+  ob->host = bytes > 0 && !is_device_pointer(ptr);
+  if (!ob->host) {
+    ob->dev = ptr;
+    return NFFT_OK;
+  }
+  return stage_buffer(p, slot, bytes, &ob->dev);
+}
+
+int finish_output(nfft_plan* p, const OutputBinding& ob) {
+  if (!ob.host) return NFFT_OK;
+  NFFT_CK(p, cudaMemcpyAsync(ob.user, ob.dev, ob.bytes, cudaMemcpyDeviceToHost, p->stream));
+  NFFT_CK(p, cudaStreamSynchronize(p->stream));
+  return NFFT_OK;
+}
+
+Geometry make_geometry(const nfft_plan* p) {
+  Geometry g{};
+  g.D = p->D;
+  g.K = p->K;
+  g.off = p->off;
+  g.closed = (p->flags & NFFT_FLAG_CLOSED_SUPPORT) ? 1 : 0;
+  g.M = (int)p->M;
+  g.m = (double)p->m;
+  for (int d = 0; d < p->D; ++d) {
+    g.Nt[d] = (int)p->Nt[d];
+    g.T[d] = (int)p->T[d];
+    g.ntile[d] = p->ntile[d];
+    g.L[d] = (int)p->T[d] + p->K - 1;
+    g.b[d] = p->b[d];
+    g.norm[d] = (double)p->m / sinh(p->b[d] * (double)p->m);
+  }
+  return g;
+}
+
+DeconvArgs make_deconv(const nfft_plan* p) {
+  DeconvArgs a{};
+  a.D = p->D;
+  int64_t off = 0;
+  for (int d = 0; d < p->D; ++d) {
+    a.N[d] = (int)p->N[d];
+    a.Nt[d] = (int)p->Nt[d];
+    if (p->dtype == NFFT_C128)
+      a.beta[d] = p->beta64 + off;
+    else
+      a.beta[d] = p->beta32 + off;
+    off += p->N[d];
+  }
+  return a;
+}
+
+size_t region_bytes(const nfft_plan* p, const int64_t* T, int kind) {
+  size_t r = 1;
+  for (int d = 0; d < p->D; ++d) r *= (size_t)(T[d] + p->K - 1);
+  return r * cplx_size(p) * (kind == 2 ? 2 : 1);
+}
+
+// Default tile shape: the largest power-of-two cube (capped per dimension by
+// N~_d) whose expected node count stays near 2 nodes per thread and whose
+// shared-memory region (tile + halo) stays within 64 KB.
+void default_tile(const nfft_plan* p, int64_t* T) {
+  double density = (double)p->M / (double)prod_Nt(p);
+  int64_t best = 1;
+  for (int64_t t = 1; t <= 4096; t *= 2) {
+    int64_t TT[kMaxD];
+    double cells = 1;
+    for (int d = 0; d < p->D; ++d) {
+      TT[d] = t < p->Nt[d] ? t : p->Nt[d];
+      cells *= (double)TT[d];
+    }
+    if (region_bytes(p, TT, (p->flags & NFFT_FLAG_COMPENSATED) ? 2 : 1) > 64 * 1024) break;
+    best = t;
+    if (density * cells >= 2.0 * kResampleThreads) break;
+  }
+  for (int d = 0; d < p->D; ++d) T[d] = best < p->Nt[d] ? best : p->Nt[d];
+}
+
+int configure_tiles(nfft_plan* p, const int64_t* T) {
+  int64_t n_tiles = 1;
+  for (int d = 0; d < p->D; ++d) {
+    p->T[d] = T[d];
+    p->ntile[d] = (int)((p->Nt[d] + T[d] - 1) / T[d]);
+    n_tiles *= p->ntile[d];
+  }
+  if (n_tiles > (int64_t)1 << 30) return NFFT_ERR_INVALID_ARG;
+  p->n_tiles = n_tiles;
+  p->max_items = n_tiles + (p->M + p->cmax - 1) / p->cmax + 1;
+  if (p->tiles_cap < n_tiles) {
+    dfree(p->tile_count);
+    dfree(p->tile_offset);
+    p->tile_count = p->tile_offset = nullptr;
+    p->tiles_cap = 0;
+    int s = dalloc(p, &p->tile_count, sizeof(int) * n_tiles);
+    if (s == NFFT_OK) s = dalloc(p, &p->tile_offset, sizeof(int) * n_tiles);
+    if (s != NFFT_OK) return s;
+    p->tiles_cap = n_tiles;
+  }
+  if (p->items_cap < p->max_items) {
+    dfree(p->items);
+    p->items = nullptr;
+    p->items_cap = 0;
+    int s = dalloc(p, &p->items, sizeof(int4) * p->max_items);
+    if (s != NFFT_OK) return s;
+    p->items_cap = p->max_items;
+  }
+  Geometry g = make_geometry(p);
+  for (int kind = 0; kind < 4; ++kind) {
+    int per_sm = p->dtype == NFFT_C128 ? resample_ctas_per_sm<double>(g, kind)
+                                       : resample_ctas_per_sm<float>(g, kind);
+    if (per_sm <= 0) return NFFT_ERR_UNSUPPORTED;
+    p->ctas[kind] = per_sm * p->sms;
+  }
+  return NFFT_OK;
+}
+
+bool ready(nfft_plan* p, int* status) {
+  if (!p) {
+    *status = NFFT_ERR_INVALID_ARG;
+    return false;
+  }
+  if (p->err != NFFT_OK) {
+    *status = p->err;
+    return false;
+  }
+  *status = NFFT_OK;
+  return true;
+}
+
+NodeArrays node_arrays(const nfft_plan* p) {
+  NodeArrays na;
+  na.cell = p->cell;
+  na.frac = p->frac;
+  na.perm = p->perm;
+  na.items = p->items;
+  na.n_items = p->n_items;
+  return na;
+}
+
+int run_deconv_pad(nfft_plan* p, const void* f) {
+  DeconvArgs a = make_deconv(p);
+  cudaError_t e = p->dtype == NFFT_C128 ? launch_deconv_pad<double>(a, f, p->grid, p->stream)
+                                        : launch_deconv_pad<float>(a, f, p->grid, p->stream);
+  return cuda_status(p, e);
+}
+
+int run_fft(nfft_plan* p, int sign) {
+  cufftResult r;
+  int dir = sign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
+  if (p->dtype == NFFT_C128)
+    r = cufftExecZ2Z(p->fft, (cufftDoubleComplex*)p->grid, (cufftDoubleComplex*)p->grid, dir);
+  else
+    r = cufftExecC2C(p->fft, (cufftComplex*)p->grid, (cufftComplex*)p->grid, dir);
+  if (r != CUFFT_SUCCESS) return latch(p, NFFT_ERR_CUFFT);
+  return NFFT_OK;
+}
+
+int run_gather(nfft_plan* p, void* fhat) {
+  Geometry g = make_geometry(p);
+  NodeArrays na = node_arrays(p);
+  cudaError_t e = p->dtype == NFFT_C128
+                      ? launch_gather<double>(g, p->grid, na, fhat, p->ctas[0], p->stream)
+                      : launch_gather<float>(g, p->grid, na, fhat, p->ctas[0], p->stream);
+  return cuda_status(p, e);
+}
+
+int run_scatter(nfft_plan* p, const void* fhat) {
+  NFFT_CK(p, cudaMemsetAsync(p->grid, 0, (size_t)prod_Nt(p) * cplx_size(p), p->stream));
+  Geometry g = make_geometry(p);
+  NodeArrays na = node_arrays(p);
+  const int comp = (p->flags & NFFT_FLAG_COMPENSATED) && p->dtype == NFFT_C64 ? 1 : 0;
+  cudaError_t e =
+      p->dtype == NFFT_C128
+          ? launch_scatter<double>(g, p->grid, na, fhat, 0, p->ctas[1], p->stream)
+          : launch_scatter<float>(g, p->grid, na, fhat, comp, p->ctas[comp ? 2 : 1], p->stream);
+  return cuda_status(p, e);
+}
+
+int run_crop_deconv(nfft_plan* p, void* y) {
+  DeconvArgs a = make_deconv(p);
+  cudaError_t e = p->dtype == NFFT_C128 ? launch_crop_deconv<double>(a, p->grid, y, p->stream)
+                                        : launch_crop_deconv<float>(a, p->grid, y, p->stream);
+  return cuda_status(p, e);
+}
+
+int run_grad_gather(nfft_plan* p, const void* cot, void* gk) {
+  Geometry g = make_geometry(p);
+  NodeArrays na = node_arrays(p);
+  cudaError_t e =
+      p->dtype == NFFT_C128
+          ? launch_grad_gather<double>(g, p->grid, na, cot, gk, p->ctas[3], p->stream)
+          : launch_grad_gather<float>(g, p->grid, na, cot, gk, p->ctas[3], p->stream);
+  return cuda_status(p, e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nfft_strerror(int code) {
+  switch (code) {
+    case NFFT_OK: return "success";
+    case NFFT_ERR_INVALID_ARG: return "invalid argument";
+    case NFFT_ERR_NO_NODES: return "no nodes set (call nfft_set_nodes first)";
+    case NFFT_ERR_OOM: return "device memory allocation failed";
+    case NFFT_ERR_CUFFT: return "cuFFT error";
+    case NFFT_ERR_CUDA: return "CUDA runtime error";
+    case NFFT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case NFFT_ERR_DEVICE_CHECK: return "device-side range check failed";
+    case NFFT_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status code";
+  }
+}
+
+int nfft_plan_destroy(nfft_plan* p) {
+  if (!p) return NFFT_OK;
+  DeviceGuard guard(p->device);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->fft_ok) cufftDestroy(p->fft);
+  void* bufs[] = {p->grid, p->beta64, p->beta32, p->cell, p->frac, p->perm, p->key, p->rank,
+                  p->tile_count, p->tile_offset, p->items, p->n_items,
+                  p->stage[0], p->stage[1], p->stage[2]};
+  for (void* b : bufs) dfree(b);
+  delete p;
+  return NFFT_OK;
+}
+
+int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double sigma, int m,
+                     int dtype, uint32_t flags, void* stream) {
+  if (!out) return NFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (D < 1 || D > kMaxD || !N) return NFFT_ERR_INVALID_ARG;
+  if (!(sigma > 1.0) || m < 1 || m > kMaxM) return NFFT_ERR_INVALID_ARG;
+  if (dtype != NFFT_C64 && dtype != NFFT_C128) return NFFT_ERR_INVALID_ARG;
+  if (M < 0 || M >= ((int64_t)1 << 31)) return NFFT_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_COMPENSATED))
+    return NFFT_ERR_INVALID_ARG;
+  int64_t total = 1;
+  for (int d = 0; d < D; ++d) {
+    if (N[d] < 2 || N[d] > ((int64_t)1 << 28)) return NFFT_ERR_INVALID_ARG;
+    int64_t nt = 2 * (int64_t)ceil(sigma * (double)N[d] / 2.0 - 1e-12);
+    if (nt <= 2 * m || nt > ((int64_t)1 << 30)) return NFFT_ERR_INVALID_ARG;
+    total *= nt;
+    if (total > ((int64_t)1 << 40)) return NFFT_ERR_INVALID_ARG;
+  }
+
+  nfft_plan* p = new (std::nothrow) nfft_plan();
+  if (!p) return NFFT_ERR_OOM;
+  p->D = D;
+  p->M = M;
+  p->sigma = sigma;
+  p->m = m;
+  p->dtype = dtype;
+  p->flags = flags;
+  p->stream = (cudaStream_t)stream;
+  const bool closed = (flags & NFFT_FLAG_CLOSED_SUPPORT) != 0;
+  p->K = closed ? 2 * m + 2 : 2 * m;
+  p->off = closed ? -m : -m + 1;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return NFFT_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+  for (int d = 0; d < D; ++d) {
+    p->N[d] = N[d];
+    p->Nt[d] = 2 * (int64_t)ceil(sigma * (double)N[d] / 2.0 - 1e-12);
+    p->b[d] = M_PI * (2.0 - (double)N[d] / (double)p->Nt[d]);
+  }
+
+  int s = NFFT_OK;
+  int64_t sumN = 0;
+  for (int d = 0; d < D; ++d) sumN += N[d];
+  if (s == NFFT_OK) s = dalloc(p, &p->grid, (size_t)prod_Nt(p) * cplx_size(p));
+  if (s == NFFT_OK) s = dalloc(p, &p->beta64, sizeof(double) * sumN);
+  if (s == NFFT_OK) s = dalloc(p, &p->beta32, sizeof(float) * sumN);
+  if (s == NFFT_OK) s = dalloc(p, &p->cell, sizeof(int) * (size_t)(M * D));
+  if (s == NFFT_OK) s = dalloc(p, &p->frac, real_size(p) * (size_t)(M * D));
+  if (s == NFFT_OK) s = dalloc(p, &p->perm, sizeof(int) * (size_t)M);
+  if (s == NFFT_OK) s = dalloc(p, &p->key, sizeof(int) * (size_t)M);
+  if (s == NFFT_OK) s = dalloc(p, &p->rank, sizeof(int) * (size_t)M);
+  if (s == NFFT_OK) s = dalloc(p, &p->n_items, sizeof(int));
+  if (s == NFFT_OK) {
+    int64_t T[kMaxD];
+    default_tile(p, T);
+    s = configure_tiles(p, T);
+  }
+  if (s == NFFT_OK) {
+    int n[kMaxD];
+    for (int d = 0; d < D; ++d) n[d] = (int)p->Nt[d];
+    cufftResult r = cufftPlanMany(&p->fft, D, n, nullptr, 1, 0, nullptr, 1, 0,
+                                  dtype == NFFT_C128 ? CUFFT_Z2Z : CUFFT_C2C, 1);
+    if (r != CUFFT_SUCCESS) {
+      s = (r == CUFFT_ALLOC_FAILED) ? NFFT_ERR_OOM : NFFT_ERR_CUFFT;
+    } else {
+      p->fft_ok = true;
+      if (cufftSetStream(p->fft, p->stream) != CUFFT_SUCCESS) s = NFFT_ERR_CUFFT;
+    }
+  }
+  if (s == NFFT_OK) {
+    int Ni[kMaxD], Nti[kMaxD];
+    for (int d = 0; d < D; ++d) {
+      Ni[d] = (int)N[d];
+      Nti[d] = (int)p->Nt[d];
+    }
+    s = cuda_status(p, launch_build_beta(D, Ni, Nti, m, p->b, p->beta64, p->beta32, p->stream));
+  }
+  if (s == NFFT_OK) s = cuda_status(p, cudaMemsetAsync(p->n_items, 0, sizeof(int), p->stream));
+  if (s != NFFT_OK) {
+    nfft_plan_destroy(p);
+    return s;
+  }
+  *out = p;
+  return NFFT_OK;
+}
+
+int nfft_set_nodes(nfft_plan* p, const void* k, int k_is_fp64) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!k && p->M > 0) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  // k is FP64 (k_is_fp64 != 0) or FP32 for either plan dtype; FP32 nodes are
+  // promoted to FP64 before the split.
+  const void* kd = nullptr;
+  s = device_input(p, 2, k, p->M > 0 ? (size_t)(p->M * p->D) * (k_is_fp64 ? 8 : 4) : 0, &kd);
+  if (s != NFFT_OK) return s;
+  SortArgs a{};
+  a.D = p->D;
+  a.M = (int)p->M;
+  for (int d = 0; d < p->D; ++d) {
+    a.Nt[d] = (int)p->Nt[d];
+    a.T[d] = (int)p->T[d];
+    a.ntile[d] = p->ntile[d];
+  }
+  a.n_tiles = (int)p->n_tiles;
+  a.cmax = p->cmax;
+  a.max_items = (int)p->max_items;
+  NFFT_CK(p, launch_node_count(a, kd, k_is_fp64 ? 1 : 0, p->tile_count, p->key, p->rank, p->stream));
+  NFFT_CK(p, launch_tile_scan(a, p->tile_count, p->tile_offset, p->items, p->n_items, p->stream));
+  NFFT_CK(p, launch_node_place(a, kd, k_is_fp64 ? 1 : 0, p->key, p->rank, p->tile_offset, p->cell,
+                               p->frac, p->dtype == NFFT_C128 ? 1 : 0, p->perm, p->stream));
+  if (kd != k) NFFT_CK(p, cudaStreamSynchronize(p->stream));  // stage buffer reuse safety
+  p->has_nodes = true;
+  return NFFT_OK;
+}
+
+int nfft_forward(nfft_plan* p, const void* f, void* fhat) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!p->has_nodes) return NFFT_ERR_NO_NODES;
+  if (!f || (!fhat && p->M > 0)) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  const void* fd = nullptr;
+  OutputBinding ob;
+  if ((s = device_input(p, 0, f, (size_t)prod_N(p) * cplx_size(p), &fd)) != NFFT_OK) return s;
+  if ((s = device_output(p, 1, fhat, (size_t)p->M * cplx_size(p), &ob)) != NFFT_OK) return s;
+  if ((s = run_deconv_pad(p, fd)) != NFFT_OK) return s;
+  if ((s = run_fft(p, -1)) != NFFT_OK) return s;
+  if ((s = run_gather(p, ob.dev)) != NFFT_OK) return s;
+  return finish_output(p, ob);
+}
+
+int nfft_adjoint(nfft_plan* p, const void* fhat, void* y) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!p->has_nodes) return NFFT_ERR_NO_NODES;
+  if (!y || (!fhat && p->M > 0)) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  const void* fd = nullptr;
+  OutputBinding ob;
+  if ((s = device_input(p, 0, fhat, (size_t)p->M * cplx_size(p), &fd)) != NFFT_OK) return s;
+  if ((s = device_output(p, 1, y, (size_t)prod_N(p) * cplx_size(p), &ob)) != NFFT_OK) return s;
+  if ((s = run_scatter(p, fd)) != NFFT_OK) return s;
+  if ((s = run_fft(p, +1)) != NFFT_OK) return s;
+  if ((s = run_crop_deconv(p, ob.dev)) != NFFT_OK) return s;
+  return finish_output(p, ob);
+}
+
+int nfft_grad(nfft_plan* p, const void* f, const void* cot, void* gk) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!p->has_nodes) return NFFT_ERR_NO_NODES;
+  if (!f || ((!cot || !gk) && p->M > 0)) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  const void* fd = nullptr;
+  const void* cd = nullptr;
+  OutputBinding ob;
+  if ((s = device_input(p, 0, f, (size_t)prod_N(p) * cplx_size(p), &fd)) != NFFT_OK) return s;
+  if ((s = device_input(p, 2, cot, (size_t)p->M * cplx_size(p), &cd)) != NFFT_OK) return s;
+  if ((s = device_output(p, 1, gk, (size_t)(p->M * p->D) * real_size(p), &ob)) != NFFT_OK) return s;
+  if ((s = run_deconv_pad(p, fd)) != NFFT_OK) return s;
+  if ((s = run_fft(p, -1)) != NFFT_OK) return s;
+  if ((s = run_grad_gather(p, cd, ob.dev)) != NFFT_OK) return s;
+  return finish_output(p, ob);
+}
+
+int nfft_plan_sync(nfft_plan* p) {
+  if (!p) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_status(p, e);
+  return p->err;
+}
+
+int nfft_plan_info(nfft_plan* p, int64_t* Ntilde3, int64_t* tile3, int64_t* n_items) {
+  if (!p) return NFFT_ERR_INVALID_ARG;
+  for (int d = 0; d < kMaxD; ++d) {
+    if (Ntilde3) Ntilde3[d] = d < p->D ? p->Nt[d] : 1;
+    if (tile3) tile3[d] = d < p->D ? p->T[d] : 1;
+  }
+  if (n_items) {
+    *n_items = 0;
+    if (p->has_nodes) {
+      DeviceGuard guard(p->device);
+      int h = 0;
+      NFFT_CK(p, cudaMemcpyAsync(&h, p->n_items, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+      NFFT_CK(p, cudaStreamSynchronize(p->stream));
+      *n_items = h;
+    }
+  }
+  return p->err;
+}
+
+void* nfft_plan_grid(nfft_plan* p) { return p ? p->grid : nullptr; }
+
+int nfft_plan_set_tile(nfft_plan* p, const int64_t* tile3) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!tile3) return NFFT_ERR_INVALID_ARG;
+  int64_t T[kMaxD] = {1, 1, 1};
+  for (int d = 0; d < p->D; ++d) {
+    if (tile3[d] < 1 || tile3[d] > p->Nt[d]) return NFFT_ERR_INVALID_ARG;
+    T[d] = tile3[d];
+  }
+  const int kind = (p->flags & NFFT_FLAG_COMPENSATED) ? 2 : 1;
+  if (region_bytes(p, T, kind) > 227 * 1024) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  s = configure_tiles(p, T);
+  if (s != NFFT_OK) return s;
+  p->has_nodes = false;  // the bin-sort depends on the tile shape
+  return NFFT_OK;
+}
+
+int nfft_step_deconv_pad(nfft_plan* p, const void* f) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!f) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  return run_deconv_pad(p, f);
+}
+
+int nfft_step_fft(nfft_plan* p, int sign) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (sign != -1 && sign != 1) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  return run_fft(p, sign);
+}
+
+int nfft_step_gather(nfft_plan* p, void* fhat) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!p->has_nodes) return NFFT_ERR_NO_NODES;
+  if (!fhat && p->M > 0) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  return run_gather(p, fhat);
+}
+
+int nfft_step_scatter(nfft_plan* p, const void* fhat) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!p->has_nodes) return NFFT_ERR_NO_NODES;
+  if (!fhat && p->M > 0) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  return run_scatter(p, fhat);
+}
+
+int nfft_step_crop_deconv(nfft_plan* p, void* y) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!y) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  return run_crop_deconv(p, y);
+}
+
+int nfft_step_grad_gather(nfft_plan* p, const void* cot, void* gk) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!p->has_nodes) return NFFT_ERR_NO_NODES;
+  if ((!cot || !gk) && p->M > 0) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  return run_grad_gather(p, cot, gk);
+}
+
+}  // extern "C"

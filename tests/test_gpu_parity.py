@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: relative L2 <= 1e-5 for complex64 and <= 1e-12 for complex128
+(the stated targets), element-wise max within 10x that.  The oracle is the
+plain FP64 NFFT of Algorithms 1/2 (same window, same footprint convention),
+so the comparison isolates the arithmetic of the kernels; comparisons with
+the exact NDFT check the method's accuracy as well.
+"""
+import numpy as np
+import pytest
+
+from oracle import ndft as ondft
+from oracle import nfft as onfft
+from paper_2208_00049_gb300 import inputs
+
+from gpu_helpers import TOL, assert_close, cdtype, rel_l2, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _plan(N, M, sigma, m, dt, flags=0):
+    from paper_2208_00049_gb300.nfft import Plan
+    return Plan(N, M, sigma=sigma, m=m, dtype=cdtype(dt), flags=flags)
+
+
+def _run(case, dt, flags=0, tile=None):
+    N, M, sigma, m = case["N"], case["M"], case["sigma"], case["m"]
+    plan = _plan(N, M, sigma, m, dt, flags)
+    if tile is not None:
+        plan.set_tile(tile)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    fh = plan.forward(to_dev(case["f"], cdtype(dt))).cpu().numpy()
+    y = plan.adjoint(to_dev(case["w"], cdtype(dt))).cpu().numpy()
+    plan.close()
+    return fh, y
+
+
+SMALL = [
+    # (N, M, sigma, m): several tiles, ragged tails, odd sizes, non powers of 2
+    ((300,), 700, 2.0, 4),
+    ((257,), 513, 2.0, 3),
+    ((48, 40), 2500, 2.0, 4),
+    ((33, 47), 1777, 1.5, 5),
+    ((64, 64), 4096, 2.0, 8),
+    ((20, 18, 16), 5000, 2.0, 4),
+    ((17, 23, 12), 3001, 2.0, 3),
+    ((16, 16, 16), 4096, 1.25, 6),
+    ((12, 10, 14), 1500, 2.0, 8),
+    ((6, 8, 10), 500, 2.0, 2),
+]
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("N,M,sigma,m", SMALL)
+def test_small_cases_match_oracle(N, M, sigma, m, dt):
+    case = inputs.small_case(N, M, seed=hash((N, M, m)) % 10000, sigma=sigma, m=m)
+    fh, y = _run(case, dt)
+    want_f = onfft.forward(case["k"], case["f"], sigma, m)
+    want_a = onfft.adjoint(case["k"], case["w"], N, sigma, m)
+    tol = TOL[dt] * (10 if (dt == "c128" and m <= 3) else 1)
+    assert_close(fh, want_f, tol, "forward")
+    assert_close(y, want_a, tol, "adjoint")
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_closed_support_matches_oracle(dt):
+    """(2m+1)^D variant: nodes on grid lines get the u = +m tap."""
+    N = (24, 20)
+    case = inputs.small_case(N, 800, seed=3, m=3)
+    p = onfft.Params(N, 2.0, 3)
+    case["k"][:200, 0] = np.round(case["k"][:200, 0] * p.Nt[0]) / p.Nt[0]   # on a grid line
+    case["k"][100:300, 1] = np.round(case["k"][100:300, 1] * p.Nt[1]) / p.Nt[1]
+    from paper_2208_00049_gb300 import binding as B
+    fh, y = _run(case, dt, flags=B.NFFT_FLAG_CLOSED_SUPPORT)
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 3, closed=True), TOL[dt], "forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 3, closed=True), TOL[dt], "adjoint")
+
+
+def test_workload1_1d_against_oracle_and_ndft():
+    wl = inputs.workload("1d")
+    for dt in ("c128", "c64"):
+        fh, y = _run(wl, dt)
+        assert_close(fh, onfft.forward(wl["k"], wl["f"], 2.0, 4), TOL[dt], "forward vs oracle")
+        assert_close(y, onfft.adjoint(wl["k"], wl["w"], wl["N"], 2.0, 4), TOL[dt], "adjoint vs oracle")
+        assert rel_l2(fh, ondft.ndft(wl["k"], wl["f"])) <= 1e-5
+        assert rel_l2(y, ondft.ndft_adjoint(wl["k"], wl["w"], wl["N"])) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["2d_c64", "2d_c128"])
+def test_workload2_2d_full_size(name):
+    wl = inputs.workload(name)
+    dt, m = wl["dtype"], wl["m"]
+    fh, y = _run(wl, dt)
+    assert_close(fh, onfft.forward(wl["k"], wl["f"], 2.0, m), TOL[dt], "forward vs oracle")
+    assert_close(y, onfft.adjoint(wl["k"], wl["w"], wl["N"], 2.0, m), TOL[dt], "adjoint vs oracle")
+    # accuracy against the exact NDFT on 256 sampled nodes / 256 sampled outputs
+    rng = np.random.default_rng(5)
+    sel = rng.choice(wl["M"], 256, replace=False)
+    ex = ondft.ndft(wl["k"][sel], wl["f"])
+    assert rel_l2(fh[sel], ex) <= TOL[dt]
+    flat = rng.choice(int(np.prod(wl["N"])), 256, replace=False)
+    idx = np.unravel_index(flat, wl["N"])
+    n = np.stack([idx[d] - wl["N"][d] // 2 for d in range(2)], axis=1).astype(float)
+    ph = n @ wl["k"].T
+    ph -= np.floor(ph)
+    exa = np.exp(2j * np.pi * ph) @ wl["w"]
+    assert rel_l2(y[idx], exa) <= TOL[dt]
+
+
+@pytest.mark.parametrize("name", ["3d", "3d_lean"])
+def test_workload3_3d_full_size_sampled(name):
+    """Full 3D size in the launch configuration the bench times: forward on
+    4096 sampled nodes against the plain oracle (which needs only those
+    nodes' footprints) and 64 against the exact NDFT, adjoint on 64 sampled outputs against the exact NDFT,
+    and the adjoint identity over all nodes."""
+    wl = inputs.workload(name)
+    sigma, m = wl["sigma"], wl["m"]
+    fh, y = _run(wl, "c64")
+    rng = np.random.default_rng(6)
+    sel = rng.choice(wl["M"], 4096, replace=False)
+    want = onfft.forward(wl["k"][sel], wl["f"], sigma, m)
+    assert_close(fh[sel], want, 1e-5, "forward (sampled) vs oracle")
+    # exact NDFT on 64 of them
+    ex = ondft.ndft(wl["k"][sel[:64]], wl["f"])
+    assert rel_l2(fh[sel[:64]], ex) <= 1e-5
+    flat = rng.choice(int(np.prod(wl["N"])), 64, replace=False)
+    idx = np.unravel_index(flat, wl["N"])
+    n = np.stack([idx[d] - wl["N"][d] // 2 for d in range(3)], axis=1).astype(float)
+    exa = np.empty(64, complex)
+    for s in range(0, 64, 8):
+        ph = n[s:s + 8] @ wl["k"].T
+        ph -= np.floor(ph)
+        exa[s:s + 8] = np.exp(2j * np.pi * ph) @ wl["w"]
+    assert rel_l2(y[idx], exa) <= 1e-5
+    lhs = np.vdot(wl["w"], fh)
+    rhs = np.vdot(y, wl["f"])
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_radial_set_on_grid_nodes():
+    """Radial sets put the r = 0 sample of every spoke exactly on a grid
+    point and two spokes on grid lines (t = 0 fractions)."""
+    rad = inputs.radial_rhs(n_rhs=1)
+    k = rad["k"]
+    case = dict(N=rad["N"], M=k.shape[0], sigma=2.0, m=4, k=k, f=rad["f"][0], w=rad["w"][0])
+    for dt in ("c64", "c128"):
+        fh, y = _run(case, dt)
+        assert_close(fh, onfft.forward(k, case["f"], 2.0, 4), TOL[dt], "forward")
+        assert_close(y, onfft.adjoint(k, case["w"], case["N"], 2.0, 4), TOL[dt], "adjoint")
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_edge_cases(dt):
+    # M = 0: empty forward, zero adjoint
+    plan = _plan((16, 16), 0, 2.0, 4, dt)
+    plan.set_nodes(torch.zeros((0, 2), dtype=torch.float64, device="cuda"))
+    assert plan.forward(to_dev(np.ones((16, 16)), cdtype(dt))).numel() == 0
+    y = plan.adjoint(torch.zeros(0, dtype=cdtype(dt), device="cuda"))
+    assert torch.count_nonzero(y).item() == 0
+    plan.close()
+    # M = 1, nodes at the -1/2 corner and outside [-1/2, 1/2) (wrapped)
+    for kval in ([-0.5, -0.5], [0.5, 0.25], [1.3, -0.7], [0.0, 0.0]):
+        case = inputs.small_case((10, 12), 1, seed=1, m=2)
+        case["k"] = np.array([kval])
+        fh, y = _run(case, dt)
+        kw = np.mod(case["k"] + 0.5, 1.0) - 0.5
+        assert_close(fh, onfft.forward(kw, case["f"], 2.0, 2), TOL[dt] * 10, "M=1 forward")
+        assert_close(y, onfft.adjoint(kw, case["w"], (10, 12), 2.0, 2), TOL[dt] * 10, "M=1 adjoint")
+    # smallest grid: N = 2, m = 1
+    case = inputs.small_case((2,), 5, seed=2, m=1)
+    fh, y = _run(case, dt)
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 1), TOL[dt], "N=2")
+    # one hot tile: every node in the same cell neighbourhood -> many work items
+    case = inputs.small_case((64, 64), 5000, seed=3, m=4)
+    case["k"] = 0.01 * case["k"]
+    fh, y = _run(case, dt)
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), TOL[dt], "hot tile forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], (64, 64), 2.0, 4), TOL[dt], "hot tile adjoint")
+
+
+@pytest.mark.parametrize("tile", [(4, 4, 4), (7, 5, 3), (8, 8, 16), (12, 32, 8)])
+def test_tile_shapes_agree(tile):
+    """Any tile shape (dividing N~ or not) gives the oracle's result."""
+    N = (20, 16, 24)
+    case = inputs.small_case(N, 4000, seed=9, m=4)
+    fh, y = _run(case, "c128", tile=tile)
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), 1e-12, "forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), 1e-12, "adjoint")
+
+
+def test_compensated_scatter():
+    from paper_2208_00049_gb300 import binding as B
+    N = (48, 40)
+    case = inputs.small_case(N, 20000, seed=11, m=4)
+    want = onfft.adjoint(case["k"], case["w"], N, 2.0, 4)
+    _, y0 = _run(case, "c64")
+    _, y1 = _run(case, "c64", flags=B.NFFT_FLAG_COMPENSATED)
+    e0 = assert_close(y0, want, 1e-5, "plain")
+    e1 = assert_close(y1, want, 1e-5, "compensated")
+    assert e1 <= 1.5 * e0 + 1e-7
+
+
+def test_steps_match_oracle_steps():
+    """Each exported step against the oracle's step on the same input."""
+    N, M, m = (30, 26), 3000, 4
+    case = inputs.small_case(N, M, seed=13, m=m)
+    p = onfft.Params(N, 2.0, m)
+    plan = _plan(N, M, 2.0, m, "c128")
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    f = to_dev(case["f"], torch.complex128)
+    plan.step_deconv_pad(f)
+    grid = plan.grid_tensor().cpu().numpy()
+    want_g = onfft.correction_pad(p, case["f"])
+    # the library scales the deconvolution by the window peak prod_d psi_d(0)
+    peak = np.prod([float(onfft.psi(0.0, m, b)) for b in p.b])
+    assert_close(grid / peak, want_g, 1e-13, "deconv_pad")
+    # gather from a given grid
+    ghat = np.random.default_rng(1).standard_normal(p.Nt) + 0j
+    plan.grid_tensor().copy_(torch.from_numpy(ghat))
+    out = torch.empty(M, dtype=torch.complex128, device="cuda")
+    plan.step_gather(out)
+    assert_close(out.cpu().numpy() * peak, onfft.resample(p, case["k"], ghat), 1e-13, "gather")
+    plan.step_scatter(to_dev(case["w"], torch.complex128))
+    got = plan.grid_tensor().cpu().numpy() * peak
+    assert_close(got, onfft.resample_adjoint(p, case["k"], case["w"]), 1e-13, "scatter")
+    plan.close()
+
+
+def test_host_pointers_match_device_path():
+    N, M = (32, 24), 1500
+    case = inputs.small_case(N, M, seed=17, m=4)
+    plan = _plan(N, M, 2.0, 4, "c64")
+    plan.set_nodes(torch.from_numpy(case["k"]))                 # pageable host nodes
+    f_h = torch.from_numpy(case["f"]).to(torch.complex64).pin_memory()
+    fh_host = plan.forward(f_h)                                  # pinned host in/out
+    assert not fh_host.is_cuda
+    fh_dev = plan.forward(f_h.cuda()).cpu()
+    assert torch.equal(fh_host, fh_dev)
+    w_h = torch.from_numpy(case["w"]).to(torch.complex64)        # pageable
+    y_host = plan.adjoint(w_h)
+    y_dev = plan.adjoint(w_h.cuda()).cpu()
+    assert rel_l2(y_host.numpy(), y_dev.numpy()) <= 1e-6
+    plan.close()
+
+
+def test_gather_is_deterministic_and_fp32_nodes_accepted():
+    N, M = (40, 40), 3000
+    case = inputs.small_case(N, M, seed=19, m=4)
+    plan = _plan(N, M, 2.0, 4, "c64")
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    f = to_dev(case["f"], torch.complex64)
+    a = plan.forward(f).clone()
+    b = plan.forward(f).clone()
+    assert torch.equal(a, b)
+    k32 = case["k"].astype(np.float32)
+    plan.set_nodes(torch.from_numpy(k32).cuda())
+    c = plan.forward(f).cpu().numpy()
+    assert_close(c, onfft.forward(k32.astype(np.float64), case["f"], 2.0, 4), 1e-5, "fp32 nodes")
+    plan.close()
