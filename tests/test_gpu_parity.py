@@ -13,7 +13,7 @@ from oracle import ndft as ondft
 from oracle import nfft as onfft
 from paper_2208_00049_gb300 import inputs
 
-from gpu_helpers import TOL, assert_close, cdtype, rel_l2, require_gpu, to_dev
+from gpu_helpers import TOL, assert_close, cdtype, rel_l2, require_gpu, to_dev, tol_for
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -63,7 +63,7 @@ def test_small_cases_match_oracle(N, M, sigma, m, dt):
     fh, y = _run(case, dt)
     want_f = onfft.forward(case["k"], case["f"], sigma, m)
     want_a = onfft.adjoint(case["k"], case["w"], N, sigma, m)
-    tol = TOL[dt] * (10 if (dt == "c128" and m <= 3) else 1)
+    tol = tol_for(N, sigma, m, dt) * (10 if (dt == "c128" and m <= 3) else 1)
     assert_close(fh, want_f, tol, "forward")
     assert_close(y, want_a, tol, "adjoint")
 
@@ -121,14 +121,15 @@ def test_workload3_3d_full_size_sampled(name):
     and the adjoint identity over all nodes."""
     wl = inputs.workload(name)
     sigma, m = wl["sigma"], wl["m"]
+    tol = tol_for(wl["N"], sigma, m, "c64")
     fh, y = _run(wl, "c64")
     rng = np.random.default_rng(6)
     sel = rng.choice(wl["M"], 4096, replace=False)
     want = onfft.forward(wl["k"][sel], wl["f"], sigma, m)
-    assert_close(fh[sel], want, 1e-5, "forward (sampled) vs oracle")
+    assert_close(fh[sel], want, tol, "forward (sampled) vs oracle")
     # exact NDFT on 64 of them
     ex = ondft.ndft(wl["k"][sel[:64]], wl["f"])
-    assert rel_l2(fh[sel[:64]], ex) <= 1e-5
+    assert rel_l2(fh[sel[:64]], ex) <= tol
     flat = rng.choice(int(np.prod(wl["N"])), 64, replace=False)
     idx = np.unravel_index(flat, wl["N"])
     n = np.stack([idx[d] - wl["N"][d] // 2 for d in range(3)], axis=1).astype(float)
@@ -137,10 +138,11 @@ def test_workload3_3d_full_size_sampled(name):
         ph = n[s:s + 8] @ wl["k"].T
         ph -= np.floor(ph)
         exa[s:s + 8] = np.exp(2j * np.pi * ph) @ wl["w"]
-    assert rel_l2(y[idx], exa) <= 1e-5
+    assert rel_l2(y[idx], exa) <= tol
     lhs = np.vdot(wl["w"], fh)
     rhs = np.vdot(y, wl["f"])
-    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    # relative to the Cauchy-Schwarz scale (random vectors make <w, Af> itself small)
+    assert abs(lhs - rhs) <= tol * np.linalg.norm(wl["w"]) * np.linalg.norm(fh)
 
 
 def test_radial_set_on_grid_nodes():

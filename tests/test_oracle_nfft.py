@@ -207,3 +207,28 @@ def test_node_grad_close_to_exact_ndft_gradient():
     g = nfft.node_grad(k, f, cot, 2.0, 8)
     ge = ndft.ndft_node_grad(k, f, cot)
     assert np.linalg.norm(g - ge) <= 1e-10 * np.linalg.norm(ge)
+
+
+@pytest.mark.parametrize("N,sigma,m", [((16, 16, 16), 1.25, 6), ((64, 64), 1.25, 6), ((20, 18, 16), 2.0, 4),
+                                       ((12, 10, 14), 2.0, 8), ((33, 47), 1.5, 5)])
+def test_fp32_rounding_bound(N, sigma, m):
+    """The complex64 parity tolerance max(1e-5, u32 * kappa) bounds the error
+    of the plain algorithm when its deconvolved grid (scaled to O(1) by the
+    window peak, as single precision requires) and its FFT are rounded to
+    single precision; kappa is the deconvolution's amplification."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from gpu_helpers import tol_for
+    rng = np.random.default_rng(21)
+    M = 3000
+    k = rng.random((M, len(N))) - 0.5
+    f = _cn(rng, N)
+    p = nfft.Params(N, sigma, m)
+    peak = np.prod([float(window.psi(0.0, m, b)) for b in p.b])
+    g = nfft.correction_pad(p, f) * peak
+    ref = nfft.resample(p, k, nfft.fft_forward(g))
+    g32 = np.fft.fftn(g.astype(np.complex64))
+    assert g32.dtype == np.complex64
+    err = np.linalg.norm(nfft.resample(p, k, g32.astype(np.complex128)) - ref) / np.linalg.norm(ref)
+    assert err <= tol_for(N, sigma, m, "c64") / 4
