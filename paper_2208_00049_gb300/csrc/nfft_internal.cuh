@@ -94,6 +94,14 @@ size_t resample_smem_bytes(const Geometry& g, int kind);  // kind 0 gather, 1 sc
 template <typename R>
 int resample_ctas_per_sm(const Geometry& g, int kind);
 
+// 3D, m = 4, complex64 warp-per-node kernels (resample3d.cu)
+bool fast3d_supported(const Geometry& g, int cmax);
+int fast3d_ctas_per_sm(const Geometry& g, int kind);  // kind 0 gather, 1 scatter
+cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na, void* fhat,
+                                 int ctas, cudaStream_t s);
+cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat,
+                                  int ctas, cudaStream_t s);
+
 // deconvolution, tables, sorting (nfft_kernels.cu)
 struct DeconvArgs {
   int D;

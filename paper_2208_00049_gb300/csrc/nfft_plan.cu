@@ -34,9 +34,11 @@ struct nfft_plan {
   int64_t T[kMaxD] = {1, 1, 1};
   int ntile[kMaxD] = {1, 1, 1};
   int64_t n_tiles = 0;
-  int cmax = 256;
+  int cmax = 128;
   int64_t max_items = 0;
   int ctas[4] = {0, 0, 0, 0};  // persistent grid per kernel kind
+  bool fast3d = false;         // 3D m = 4 complex64 warp-per-node kernels
+  int fast_ctas[2] = {0, 0};
 
   void* grid = nullptr;
   double* beta64 = nullptr;
@@ -246,7 +248,11 @@ void default_tile(const nfft_plan* p, int64_t* T) {
     best = t;
     if (density * cells >= 2.0 * kResampleThreads) break;
   }
-  for (int d = 0; d < p->D; ++d) T[d] = best < p->Nt[d] ? best : p->Nt[d];
+  for (int d = 0; d < p->D; ++d) {
+    int64_t cap = p->Nt[d] - p->K + 1;  // keeps region coordinates within [-N~, 2 N~)
+    if (cap < 1) cap = 1;
+    T[d] = best < cap ? best : cap;
+  }
 }
 
 int configure_tiles(nfft_plan* p, const int64_t* T) {
@@ -278,6 +284,18 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
     p->items_cap = p->max_items;
   }
   Geometry g = make_geometry(p);
+  p->fast3d = p->dtype == NFFT_C64 && !(p->flags & NFFT_FLAG_COMPENSATED) &&
+              fast3d_supported(g, p->cmax);
+  if (p->fast3d) {
+    for (int kind = 0; kind < 2; ++kind) {
+      int per_sm = fast3d_ctas_per_sm(g, kind);
+      if (per_sm <= 0) {
+        p->fast3d = false;
+        break;
+      }
+      p->fast_ctas[kind] = per_sm * p->sms;
+    }
+  }
   for (int kind = 0; kind < 4; ++kind) {
     int per_sm = p->dtype == NFFT_C128 ? resample_ctas_per_sm<double>(g, kind)
                                        : resample_ctas_per_sm<float>(g, kind);
@@ -331,7 +349,8 @@ int run_fft(nfft_plan* p, int sign) {
 int run_gather(nfft_plan* p, void* fhat) {
   Geometry g = make_geometry(p);
   NodeArrays na = node_arrays(p);
-  cudaError_t e = p->dtype == NFFT_C128
+  cudaError_t e = p->fast3d ? launch_gather3d_fast(g, p->grid, na, fhat, p->fast_ctas[0], p->stream)
+                  : p->dtype == NFFT_C128
                       ? launch_gather<double>(g, p->grid, na, fhat, p->ctas[0], p->stream)
                       : launch_gather<float>(g, p->grid, na, fhat, p->ctas[0], p->stream);
   return cuda_status(p, e);
@@ -343,7 +362,8 @@ int run_scatter(nfft_plan* p, const void* fhat) {
   NodeArrays na = node_arrays(p);
   const int comp = (p->flags & NFFT_FLAG_COMPENSATED) && p->dtype == NFFT_C64 ? 1 : 0;
   cudaError_t e =
-      p->dtype == NFFT_C128
+      p->fast3d ? launch_scatter3d_fast(g, p->grid, na, fhat, p->fast_ctas[1], p->stream)
+      : p->dtype == NFFT_C128
           ? launch_scatter<double>(g, p->grid, na, fhat, 0, p->ctas[1], p->stream)
           : launch_scatter<float>(g, p->grid, na, fhat, comp, p->ctas[comp ? 2 : 1], p->stream);
   return cuda_status(p, e);

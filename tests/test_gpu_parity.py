@@ -265,3 +265,27 @@ def test_gather_is_deterministic_and_fp32_nodes_accepted():
     c = plan.forward(f).cpu().numpy()
     assert_close(c, onfft.forward(k32.astype(np.float64), case["f"], 2.0, 4), 1e-5, "fp32 nodes")
     plan.close()
+
+
+@pytest.mark.parametrize("tile", [(8, 8, 8), (5, 7, 9), (16, 4, 3), (8, 8, 1), (3, 11, 2)])
+def test_fast3d_m4_tile_shapes(tile):
+    """3D, m = 4, complex64 (the warp-per-node kernels): any admissible tile
+    shape, dividing N~ or not, gives the oracle's result."""
+    N = (24, 20, 28)
+    case = inputs.small_case(N, 6000, seed=23, m=4)
+    fh, y = _run(case, "c64", tile=tile)
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), 1e-5, "forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), 1e-5, "adjoint")
+
+
+def test_fast3d_m4_hot_tile_and_boundaries():
+    """Many nodes in one tile (work items split at the per-item cap) and nodes
+    on the periodic boundary of the 3D grid."""
+    N = (16, 16, 16)
+    case = inputs.small_case(N, 7000, seed=29, m=4)
+    case["k"][:5000] = 0.02 * case["k"][:5000]                  # hot tiles near the origin
+    case["k"][5000:5500, 0] = -0.5                              # on the lower boundary
+    case["k"][5500:6000, 2] = 0.5 - 1e-9                        # just below the upper boundary
+    fh, y = _run(case, "c64")
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), 1e-5, "forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), 1e-5, "adjoint")
