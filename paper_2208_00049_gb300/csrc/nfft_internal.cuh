@@ -94,13 +94,14 @@ size_t resample_smem_bytes(const Geometry& g, int kind);  // kind 0 gather, 1 sc
 template <typename R>
 int resample_ctas_per_sm(const Geometry& g, int kind);
 
-// 3D, m = 4, complex64 warp-per-node kernels (resample3d.cu)
+// 3D, m = 4, complex64 warp-per-node kernels (resample3d.cu); `poly` holds
+// the FP32 polynomial window coefficients [3][8][9] (launch_build_poly).
 bool fast3d_supported(const Geometry& g, int cmax);
 int fast3d_ctas_per_sm(const Geometry& g, int kind);  // kind 0 gather, 1 scatter
-cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na, void* fhat,
-                                 int ctas, cudaStream_t s);
-cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat,
-                                  int ctas, cudaStream_t s);
+cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na,
+                                 const float* poly, void* fhat, int ctas, cudaStream_t s);
+cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
+                                  const float* poly, const void* fhat, int ctas, cudaStream_t s);
 
 // deconvolution, tables, sorting (nfft_kernels.cu)
 struct DeconvArgs {
@@ -113,6 +114,16 @@ template <typename R>
 cudaError_t launch_deconv_pad(const DeconvArgs& a, const void* f, void* grid, cudaStream_t s);
 template <typename R>
 cudaError_t launch_crop_deconv(const DeconvArgs& a, const void* grid, void* y, cudaStream_t s);
+
+struct PolyArgs {
+  int D;
+  int K;     // taps per dimension
+  int off;   // first tap offset (-m + 1)
+  int deg;   // polynomial degree (2m)
+  int m;
+  double b[kMaxD];
+};
+cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s);
 
 cudaError_t launch_build_beta(int D, const int* N, const int* Nt, int m, const double* b,
                               double* beta64, float* beta32, cudaStream_t s);

@@ -85,6 +85,69 @@ cudaError_t launch_build_beta(int D, const int* N, const int* Nt, int m, const d
 }
 
 // ---------------------------------------------------------------------------
+// POLYNOMIAL window precomputation (Sec. 3.7.4, item 5): the window is split
+// into the K unit intervals of its taps; on each, with zeta = t - 1/2 in
+// [-1/2, 1/2] (t the node's fraction), the tap value is a polynomial of degree
+// `deg` in zeta.  Coefficients: interpolation at the deg + 1 Chebyshev points
+// of [-1/2, 1/2] (instead of the paper's least squares on 2(deg + 1)
+// equispaced samples), solved in FP64 by Gaussian elimination with partial
+// pivoting, one thread per (dimension, tap).  Stored as FP32 in
+// coef[(d * K + i) * (deg + 1) + z], for the scaled window w(u)/w(0).
+// ---------------------------------------------------------------------------
+constexpr int kMaxPolyCoef = 2 * kMaxM + 1;
+
+__global__ void build_poly_kernel(PolyArgs a, float* coef) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.D * a.K) return;
+  const int d = idx / a.K, i = idx % a.K;
+  const int Z = a.deg + 1;
+  double V[kMaxPolyCoef][kMaxPolyCoef + 1];
+  const double center = 0.5 - (double)a.off - (double)i;  // u = zeta + center
+  const double m = (double)a.m, b = a.b[d];
+  const double norm = m / sinh(b * m);
+  for (int j = 0; j < Z; ++j) {
+    const double zeta = 0.5 * cos(M_PI * (j + 0.5) / Z);
+    const double u = center + zeta;
+    const double s2 = (m - u) * (m + u);
+    const double s = sqrt(s2 > 0.0 ? s2 : 0.0);
+    const double val = (s == 0.0) ? b * norm : sinh(b * s) / s * norm;
+    double p = 1.0;
+    for (int z = 0; z < Z; ++z) {
+      V[j][z] = p;
+      p *= zeta;
+    }
+    V[j][Z] = val;
+  }
+  for (int col = 0; col < Z; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < Z; ++r)
+      if (fabs(V[r][col]) > fabs(V[piv][col])) piv = r;
+    if (piv != col)
+      for (int c = col; c <= Z; ++c) {
+        double tmp = V[col][c];
+        V[col][c] = V[piv][c];
+        V[piv][c] = tmp;
+      }
+    for (int r = col + 1; r < Z; ++r) {
+      const double f = V[r][col] / V[col][col];
+      for (int c = col; c <= Z; ++c) V[r][c] -= f * V[col][c];
+    }
+  }
+  for (int r = Z - 1; r >= 0; --r) {
+    double acc = V[r][Z];
+    for (int c = r + 1; c < Z; ++c) acc -= V[r][c] * V[c][Z];
+    V[r][Z] = acc / V[r][r];
+  }
+  for (int z = 0; z < Z; ++z) coef[(d * a.K + i) * Z + z] = (float)V[z][Z];
+}
+
+cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s) {
+  if (a.deg + 1 > kMaxPolyCoef) return cudaErrorInvalidValue;
+  build_poly_kernel<<<1, 64, 0, s>>>(a, coef);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Algorithm 1 lines 1-3: g[p] = f_n * prod_d beta_d(n_d) where the grid
 // position p_d = n_d mod N~_d, zero at every other position.  One thread
 // writes two adjacent grid points (16 B for complex64) of the last dimension.

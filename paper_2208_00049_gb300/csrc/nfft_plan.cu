@@ -43,6 +43,7 @@ struct nfft_plan {
   void* grid = nullptr;
   double* beta64 = nullptr;
   float* beta32 = nullptr;
+  float* poly = nullptr;  // POLYNOMIAL window coefficients [D][K][2m + 1] (FP32)
   int* cell = nullptr;
   void* frac = nullptr;
   int* perm = nullptr;
@@ -349,7 +350,7 @@ int run_fft(nfft_plan* p, int sign) {
 int run_gather(nfft_plan* p, void* fhat) {
   Geometry g = make_geometry(p);
   NodeArrays na = node_arrays(p);
-  cudaError_t e = p->fast3d ? launch_gather3d_fast(g, p->grid, na, fhat, p->fast_ctas[0], p->stream)
+  cudaError_t e = p->fast3d ? launch_gather3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[0], p->stream)
                   : p->dtype == NFFT_C128
                       ? launch_gather<double>(g, p->grid, na, fhat, p->ctas[0], p->stream)
                       : launch_gather<float>(g, p->grid, na, fhat, p->ctas[0], p->stream);
@@ -362,7 +363,7 @@ int run_scatter(nfft_plan* p, const void* fhat) {
   NodeArrays na = node_arrays(p);
   const int comp = (p->flags & NFFT_FLAG_COMPENSATED) && p->dtype == NFFT_C64 ? 1 : 0;
   cudaError_t e =
-      p->fast3d ? launch_scatter3d_fast(g, p->grid, na, fhat, p->fast_ctas[1], p->stream)
+      p->fast3d ? launch_scatter3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[1], p->stream)
       : p->dtype == NFFT_C128
           ? launch_scatter<double>(g, p->grid, na, fhat, 0, p->ctas[1], p->stream)
           : launch_scatter<float>(g, p->grid, na, fhat, comp, p->ctas[comp ? 2 : 1], p->stream);
@@ -410,7 +411,7 @@ int nfft_plan_destroy(nfft_plan* p) {
   DeviceGuard guard(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->fft_ok) cufftDestroy(p->fft);
-  void* bufs[] = {p->grid, p->beta64, p->beta32, p->cell, p->frac, p->perm, p->key, p->rank,
+  void* bufs[] = {p->grid, p->beta64, p->beta32, p->poly, p->cell, p->frac, p->perm, p->key, p->rank,
                   p->tile_count, p->tile_offset, p->items, p->n_items,
                   p->stage[0], p->stage[1], p->stage[2]};
   for (void* b : bufs) dfree(b);
@@ -467,6 +468,7 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
   if (s == NFFT_OK) s = dalloc(p, &p->grid, (size_t)prod_Nt(p) * cplx_size(p));
   if (s == NFFT_OK) s = dalloc(p, &p->beta64, sizeof(double) * sumN);
   if (s == NFFT_OK) s = dalloc(p, &p->beta32, sizeof(float) * sumN);
+  if (s == NFFT_OK) s = dalloc(p, &p->poly, sizeof(float) * D * p->K * (2 * m + 1));
   if (s == NFFT_OK) s = dalloc(p, &p->cell, sizeof(int) * (size_t)(M * D));
   if (s == NFFT_OK) s = dalloc(p, &p->frac, real_size(p) * (size_t)(M * D));
   if (s == NFFT_OK) s = dalloc(p, &p->perm, sizeof(int) * (size_t)M);
@@ -497,6 +499,16 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
       Nti[d] = (int)p->Nt[d];
     }
     s = cuda_status(p, launch_build_beta(D, Ni, Nti, m, p->b, p->beta64, p->beta32, p->stream));
+  }
+  if (s == NFFT_OK && !closed) {
+    PolyArgs pa{};
+    pa.D = D;
+    pa.K = p->K;
+    pa.off = p->off;
+    pa.deg = 2 * m;
+    pa.m = m;
+    for (int d = 0; d < D; ++d) pa.b[d] = p->b[d];
+    s = cuda_status(p, launch_build_poly(pa, p->poly, p->stream));
   }
   if (s == NFFT_OK) s = cuda_status(p, cudaMemsetAsync(p->n_items, 0, sizeof(int), p->stream));
   if (s != NFFT_OK) {
