@@ -168,6 +168,39 @@ int nfft_step_crop_deconv(nfft_plan *p, void *y);
  * ghat = F D f): gk[j][d] = Re(conj(cot_j) d fhat_j / d k_{j,d}). */
 int nfft_step_grad_gather(nfft_plan *p, const void *cot, void *gk);
 
+/* ---- spreading without device allocation ------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not call cudaMalloc: code running while a CUDA graph is being
+ * captured (an allocation there breaks the capture), code living under
+ * another framework's allocator (a raw cudaMalloc beside a caching allocator
+ * fragments memory and may synchronise the device), and services whose
+ * device memory must be reserved when the library loads.
+ *
+ * It performs the adjoint resampling of Algorithm 2 lines 1-3 (complex64,
+ * half-open support, 2m taps per dimension) without a plan:
+ *   grid[l] = sum_j fhat_j prod_d w_d(N~_d k_{j,d} - l_d),
+ * with the Kaiser-Bessel window scaled to 1 at u = 0 (the same quantity
+ * nfft_step_scatter leaves in a plan's grid).  grid is N~_1 x ... x N~_D
+ * complex64 in natural FFT order, N~_d = sigma N_d rounded up to even; it is
+ * overwritten.  k: (M, D) FP64, fhat: M complex64; all three are device
+ * pointers owned by the caller; the call is asynchronous on `stream`.
+ *
+ * Scratch: the bin-sort buffers live in one static device array sized for
+ * M <= NFFT_NOALLOC_MAX_NODES nodes and at most NFFT_NOALLOC_MAX_TILES
+ * tiles (about 11 MB, held on every GPU that loads the library until the
+ * process exits).  Larger sizes return NFFT_ERR_UNSUPPORTED; invalid
+ * arguments or host pointers return NFFT_ERR_INVALID_ARG.  Nothing is
+ * allocated: no cudaMalloc, no cudaFree, no allocating library routine.
+ * The array is shared by all calls on a device and keeps the last call's
+ * contents (each call clears what must start at zero); calls that overlap on
+ * the GPU race on it and must be serialised by the caller.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it, so make that first call before any stream capture. */
+#define NFFT_NOALLOC_MAX_NODES  262144
+#define NFFT_NOALLOC_MAX_TILES  65536
+int nfft_spread_noalloc(int D, const int64_t *N, double sigma, int m, int64_t M,
+                        const double *k, const void *fhat, void *grid, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

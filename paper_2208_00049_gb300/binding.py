@@ -50,7 +50,11 @@ SIGNATURES = {
     "nfft_step_scatter": (_i, [_p, _p]),
     "nfft_step_crop_deconv": (_i, [_p, _p]),
     "nfft_step_grad_gather": (_i, [_p, _p, _p]),
+    "nfft_spread_noalloc": (_i, [_i, _i64p, ctypes.c_double, _i, ctypes.c_int64, _p, _p, _p, _p]),
 }
+
+NFFT_NOALLOC_MAX_NODES = 262144
+NFFT_NOALLOC_MAX_TILES = 65536
 
 _lib = None
 
@@ -171,3 +175,9 @@ def nfft_step_crop_deconv(plan, y_ptr):
 
 def nfft_step_grad_gather(plan, cot_ptr, gk_ptr):
     return lib().nfft_step_grad_gather(_p(plan), _p(cot_ptr), _p(gk_ptr))
+
+
+def nfft_spread_noalloc(D, N, sigma, m, M, k_ptr, fhat_ptr, grid_ptr, stream):
+    """Adjoint resampling onto a caller grid with no device allocation (see the header)."""
+    return lib().nfft_spread_noalloc(int(D), _i64_array(N, max(3, len(N))), float(sigma), int(m),
+                                     int(M), _p(k_ptr), _p(fhat_ptr), _p(grid_ptr), _p(stream or None))
