@@ -36,8 +36,7 @@ constexpr int kScatterWarps = 4;
 constexpr int kItemCap = 128;       // nodes per work item staged in shared memory
 
 struct NodeStage {
-  int apack[kItemCap];   // a0 | a1 << 8 | a2 << 16: cell offsets inside the tile
-  float t[3][kItemCap];  // fractions
+  float4 rec[kItemCap];  // {t0, t1, t2, bits of a0 | a1 << 8 | a2 << 16}: fractions, cell offsets in the tile
   int perm[kItemCap];
   float2 v[kItemCap];    // scatter: the node's fhat value
 };
@@ -99,32 +98,48 @@ __device__ __forceinline__ void stage_nodes(const Geometry& g, const NodeArrays&
   for (int i = tid; i < item.z; i += nthreads) {
     const int q = item.y + i;
     int pk = 0;
+    float t[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       pk |= (na.cell[d * M + q] - tc[d] * g.T[d]) << (8 * d);
-      ns.t[d][i] = frac[d * M + q];
+      t[d] = frac[d * M + q];
     }
-    ns.apack[i] = pk;
+    ns.rec[i] = make_float4(t[0], t[1], t[2], __int_as_float(pk));
     const int j = na.perm[q];
     ns.perm[i] = j;
     if (fhat) ns.v[i] = fhat[j];
   }
 }
 
-// Tile + halo rows: two rows of <= 16 elements per warp step.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Tile + halo rows: two rows of <= 16 elements per warp step, copied with
+// cp.async (the caller waits with cp_async_wait_all before its barrier).
 __device__ __forceinline__ void load_tile(const Geometry& g, const int* start, const float2* grid,
                                           float2* tile, int warp, int lane, int nwarps) {
   const int L1 = g.L[1], L2 = g.L[2];
   const int half = lane >> 4, e = lane & 15;
   const int rows = g.L[0] * L1;
+  const int step = 2 * nwarps;  // rows advance by `step` (< L1 is not assumed)
   const int g2 = wrap1(start[2] + e, g.Nt[2]);
-#pragma unroll 4
-  for (int r = 2 * warp + half; r < rows; r += 2 * nwarps) {
-    const int r0 = r / L1, r1 = r - r0 * L1;
-    if (e < L2) {
+  int r = 2 * warp + half;
+  int r0 = r / L1, r1 = r - r0 * L1;
+  const int s0 = step / L1, s1 = step - s0 * L1;
+  if (e < L2) {
+    for (; r < rows; r += step) {
       const int g0 = wrap1(start[0] + r0, g.Nt[0]);
       const int g1 = wrap1(start[1] + r1, g.Nt[1]);
-      tile[(r0 * L1 + r1) * kPitch + e] = grid[((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + g2];
+      cp_async8(tile + (r0 * L1 + r1) * kPitch + e, grid + ((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + g2);
+      r0 += s0;
+      r1 += s1;
+      if (r1 >= L1) {
+        r1 -= L1;
+        ++r0;
+      }
     }
   }
 }
@@ -158,13 +173,15 @@ __global__ void __launch_bounds__(32 * kGatherWarps)
     __syncthreads();
     load_tile(g, start, grid, tile, warp, lane, kGatherWarps);
     stage_nodes(g, na, item, tc, ns, nullptr, threadIdx.x, blockDim.x);
+    cp_async_wait_all();
     __syncthreads();
 
     for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * kGatherWarps) {
       const int s = min(s0 + half, item.z - 1);  // a half without a node repeats the last one
-      const float wA = horner(cA, ns.t[grp][s] - 0.5f);
-      const float wB = horner(cB, ns.t[2][s] - 0.5f);
-      const int pk = ns.apack[s];
+      const float4 rc = ns.rec[s];
+      const float wA = horner(cA, (grp == 0 ? rc.x : rc.y) - 0.5f);
+      const float wB = horner(cB, rc.z - 0.5f);
+      const int pk = __float_as_int(rc.w);
       const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
       f32x2 w12[4];
 #pragma unroll
@@ -230,8 +247,9 @@ __global__ void __launch_bounds__(32 * kScatterWarps)
     __syncthreads();
 
     for (int s = 0; s < item.z; ++s) {
-      const float w = horner(c, ns.t[dl][s] - 0.5f);
-      const int pk = ns.apack[s];
+      const float4 rc = ns.rec[s];
+      const float w = horner(c, (dl == 0 ? rc.x : (dl == 1 ? rc.y : rc.z)) - 0.5f);
+      const int pk = __float_as_int(rc.w);
       const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
       const int i0a = (warp - a0) & (kScatterWarps - 1);  // planes i0a, i0a + 4 are this warp's
       const float w2 = __shfl_sync(0xffffffffu, w, 16 + i2);
