@@ -168,6 +168,51 @@ int nfft_step_crop_deconv(nfft_plan *p, void *y);
  * ghat = F D f): gk[j][d] = Re(conj(cot_j) d fhat_j / d k_{j,d}). */
 int nfft_step_grad_gather(nfft_plan *p, const void *cot, void *gk);
 
+/* Tile-shape autotuner.  The paper sweeps the block size (Sec. 5.2) and
+ * proposes choosing it automatically by measurement, like FFTW_MEASURE
+ * (Sec. 6): for each candidate tile this times forward + adjoint on the
+ * given nodes (k as for nfft_set_nodes), keeps the fastest, caches the
+ * choice per (device, D, N, M, sigma, m, dtype, flags) for the process, and
+ * leaves the plan with that tile and the nodes set.  chosen3 (may be NULL)
+ * receives the tile.  Allocates temporary device buffers; synchronises. */
+int nfft_plan_autotune(nfft_plan *p, const void *k, int k_is_fp64, int64_t *chosen3);
+
+/* ---- batched transforms -------------------------------------------------
+ * Many independent problems of one dimension D, sigma, m and dtype, with
+ * uneven sizes, run as one persistent gather / scatter launch over all their
+ * work items, one deconvolution launch, and one batched cuFFT per distinct
+ * oversampled size (Algorithms 1 and 2 applied to each problem).
+ *   B problems; problem p has coefficient size N[p*D .. p*D+D-1] and uses
+ *   node set set_of[p] (0 <= set_of[p] < S).  S node sets, set s has
+ *   M_set[s] nodes; problems sharing a node set must have equal N (several
+ *   right-hand sides on one set).  Every set must be used.
+ * Buffers are device pointers to concatenations, in order:
+ *   k    : node sets in set order, each (M_set[s], D), FP64 if k_is_fp64;
+ *   f, y : problems in problem order, each N_p row-major complex;
+ *   fhat : problems in problem order, each M_set[set_of[p]] complex.
+ * All calls are asynchronous on `stream` except nfft_batch_set_nodes and
+ * nfft_batch_autotune, which synchronise.  Status codes as above. */
+typedef struct nfft_batch nfft_batch;
+int nfft_batch_create(nfft_batch **out, int D, int B, const int64_t *N, const int32_t *set_of, int S,
+                      const int64_t *M_set, double sigma, int m, int dtype, uint32_t flags,
+                      void *stream);
+int nfft_batch_destroy(nfft_batch *b);
+int nfft_batch_set_nodes(nfft_batch *b, const void *k, int k_is_fp64);
+int nfft_batch_forward(nfft_batch *b, const void *f, void *fhat);
+int nfft_batch_adjoint(nfft_batch *b, const void *fhat, void *y);
+/* Graph mode: each direction is captured once into a CUDA graph (on an
+ * internal stream) and replayed on `stream` while the buffers passed stay
+ * the same; new buffers trigger a re-capture. */
+int nfft_batch_set_graph(nfft_batch *b, int enable);
+/* Common tile shape (cells per dimension, clamped per problem); discards the
+ * node sort (call nfft_batch_set_nodes again). */
+int nfft_batch_set_tile(nfft_batch *b, const int64_t *tile3);
+/* Tile shape, total work items (0 before set_nodes; synchronises) and the
+ * number of distinct oversampled sizes (one cuFFT plan each). */
+int nfft_batch_info(nfft_batch *b, int64_t *tile3, int64_t *n_items, int64_t *n_fft_classes);
+/* Autotuner for a batch: as nfft_plan_autotune, timing the whole batch. */
+int nfft_batch_autotune(nfft_batch *b, const void *k, int k_is_fp64, int64_t *chosen3);
+
 /* ---- spreading without device allocation ------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not call cudaMalloc: code running while a CUDA graph is being

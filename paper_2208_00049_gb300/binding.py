@@ -50,6 +50,17 @@ SIGNATURES = {
     "nfft_step_scatter": (_i, [_p, _p]),
     "nfft_step_crop_deconv": (_i, [_p, _p]),
     "nfft_step_grad_gather": (_i, [_p, _p, _p]),
+    "nfft_plan_autotune": (_i, [_p, _p, _i, _i64p]),
+    "nfft_batch_create": (_i, [ctypes.POINTER(_p), _i, _i, _i64p, ctypes.POINTER(ctypes.c_int32), _i, _i64p,
+                               ctypes.c_double, _i, _i, ctypes.c_uint32, _p]),
+    "nfft_batch_destroy": (_i, [_p]),
+    "nfft_batch_set_nodes": (_i, [_p, _p, _i]),
+    "nfft_batch_forward": (_i, [_p, _p, _p]),
+    "nfft_batch_adjoint": (_i, [_p, _p, _p]),
+    "nfft_batch_set_graph": (_i, [_p, _i]),
+    "nfft_batch_set_tile": (_i, [_p, _i64p]),
+    "nfft_batch_info": (_i, [_p, _i64p, _i64p, _i64p]),
+    "nfft_batch_autotune": (_i, [_p, _p, _i, _i64p]),
     "nfft_spread_noalloc": (_i, [_i, _i64p, ctypes.c_double, _i, ctypes.c_int64, _p, _p, _p, _p]),
 }
 
@@ -175,6 +186,65 @@ def nfft_step_crop_deconv(plan, y_ptr):
 
 def nfft_step_grad_gather(plan, cot_ptr, gk_ptr):
     return lib().nfft_step_grad_gather(_p(plan), _p(cot_ptr), _p(gk_ptr))
+
+
+def nfft_plan_autotune(plan, k_ptr, k_is_fp64):
+    """Returns (status, chosen tile3)."""
+    t = (ctypes.c_int64 * 3)()
+    s = lib().nfft_plan_autotune(_p(plan), _p(k_ptr), int(k_is_fp64), t)
+    return s, tuple(t)
+
+
+def nfft_batch_create(D, N_flat, set_of, M_set, sigma, m, dtype, flags, stream):
+    """Returns (status, batch handle or None)."""
+    out = _p()
+    B = len(set_of)
+    Narr = _i64_array(N_flat, len(N_flat))
+    sarr = (ctypes.c_int32 * B)(*[int(v) for v in set_of])
+    Marr = _i64_array(M_set, len(M_set))
+    s = lib().nfft_batch_create(ctypes.byref(out), int(D), B, Narr, sarr, len(M_set), Marr, float(sigma),
+                                int(m), int(dtype), int(flags), _p(stream or None))
+    return s, out.value
+
+
+def nfft_batch_destroy(batch):
+    return lib().nfft_batch_destroy(_p(batch))
+
+
+def nfft_batch_set_nodes(batch, k_ptr, k_is_fp64):
+    return lib().nfft_batch_set_nodes(_p(batch), _p(k_ptr), int(k_is_fp64))
+
+
+def nfft_batch_forward(batch, f_ptr, fhat_ptr):
+    return lib().nfft_batch_forward(_p(batch), _p(f_ptr), _p(fhat_ptr))
+
+
+def nfft_batch_adjoint(batch, fhat_ptr, y_ptr):
+    return lib().nfft_batch_adjoint(_p(batch), _p(fhat_ptr), _p(y_ptr))
+
+
+def nfft_batch_set_graph(batch, enable):
+    return lib().nfft_batch_set_graph(_p(batch), int(enable))
+
+
+def nfft_batch_set_tile(batch, tile3):
+    return lib().nfft_batch_set_tile(_p(batch), _i64_array(list(tile3) + [1] * (3 - len(tile3))))
+
+
+def nfft_batch_info(batch):
+    """Returns (status, tile3, n_items, n_fft_classes)."""
+    t = (ctypes.c_int64 * 3)()
+    ni = ctypes.c_int64()
+    nc = ctypes.c_int64()
+    s = lib().nfft_batch_info(_p(batch), t, ctypes.byref(ni), ctypes.byref(nc))
+    return s, tuple(t), ni.value, nc.value
+
+
+def nfft_batch_autotune(batch, k_ptr, k_is_fp64):
+    """Returns (status, chosen tile3)."""
+    t = (ctypes.c_int64 * 3)()
+    s = lib().nfft_batch_autotune(_p(batch), _p(k_ptr), int(k_is_fp64), t)
+    return s, tuple(t)
 
 
 def nfft_spread_noalloc(D, N, sigma, m, M, k_ptr, fhat_ptr, grid_ptr, stream):

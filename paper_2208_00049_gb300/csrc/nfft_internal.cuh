@@ -80,6 +80,32 @@ struct NodeArrays {
   const int* n_items;
 };
 
+// Batched execution: one problem of a batch (geometry and buffer offsets).
+struct BatchProblem {
+  Geometry g;        // g.M = the problem's node count
+  int N[kMaxD];      // coefficient sizes
+  int64_t grid_off;  // complex elements into the batch grid buffer
+  int64_t node_off;  // node-set offset: cell / frac planes start at D * node_off, perm at node_off
+  int64_t out_off;   // offset of this problem's fhat in the concatenated fhat buffer
+  int64_t in_off;    // offset of this problem's f / y in the concatenated coefficient buffer
+  int64_t beta_off;  // offset of this problem's deconvolution vectors
+};
+struct BatchNodes {
+  const int* cell;
+  const void* frac;
+  const int* perm;   // node-set-local indices
+  const int4* items; // {tile, first sorted node (set-local), count, problem}
+  const int* n_items;
+};
+template <typename R>
+cudaError_t launch_gather_batch(const BatchProblem* probs_dev, const Geometry& gmax, const void* grid,
+                                const BatchNodes& nb, void* fhat, int ctas, cudaStream_t s);
+template <typename R>
+cudaError_t launch_scatter_batch(const BatchProblem* probs_dev, const Geometry& gmax, void* grid,
+                                 const BatchNodes& nb, const void* fhat, int ctas, cudaStream_t s);
+template <typename R>
+int resample_batch_ctas_per_sm(const Geometry& gmax, int kind);  // kind 0 gather, 1 scatter
+
 template <typename R>
 cudaError_t launch_gather(const Geometry& g, const void* grid, const NodeArrays& na,
                           void* fhat, int grid_ctas, cudaStream_t s);
@@ -124,6 +150,15 @@ struct PolyArgs {
   double b[kMaxD];
 };
 cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s);
+
+template <typename R>
+cudaError_t launch_deconv_pad_batch(int D, int B, int64_t max_grid, const BatchProblem* probs,
+                                    const void* beta_all, const void* f, void* grid, cudaStream_t s);
+template <typename R>
+cudaError_t launch_crop_deconv_batch(int D, int B, int64_t max_n, const BatchProblem* probs,
+                                     const void* beta_all, const void* grid, void* y, cudaStream_t s);
+cudaError_t launch_items_expand(const int4* src, const int* n_src, int max_n, int4* dst, const int* dst_off, int p,
+                                cudaStream_t s);
 
 cudaError_t launch_build_beta(int D, const int* N, const int* Nt, int m, const double* b,
                               double* beta64, float* beta32, cudaStream_t s);

@@ -153,8 +153,8 @@ cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s) {
 // writes two adjacent grid points (16 B for complex64) of the last dimension.
 // ---------------------------------------------------------------------------
 template <int D, typename R>
-__global__ void deconv_pad_kernel(DeconvArgs a, const typename Cplx<R>::type* __restrict__ f,
-                                  typename Cplx<R>::type* __restrict__ grid) {
+__device__ __forceinline__ void deconv_pad_body(const DeconvArgs& a, const typename Cplx<R>::type* __restrict__ f,
+                                                typename Cplx<R>::type* __restrict__ grid) {
   using C = typename Cplx<R>::type;
   const R* __restrict__ beta0 = (const R*)a.beta[0];
   const R* __restrict__ beta1 = (const R*)a.beta[D > 1 ? 1 : 0];
@@ -217,10 +217,41 @@ __global__ void deconv_pad_kernel(DeconvArgs a, const typename Cplx<R>::type* __
   }
 }
 
+template <int D, typename R>
+__global__ void deconv_pad_kernel(DeconvArgs a, const typename Cplx<R>::type* __restrict__ f,
+                                  typename Cplx<R>::type* __restrict__ grid) {
+  deconv_pad_body<D, R>(a, f, grid);
+}
+
+// Batched: blockIdx.y selects the problem; sizes and offsets from the table.
+template <int D, typename R>
+__device__ __forceinline__ DeconvArgs batch_deconv_args(const BatchProblem& P, const R* beta_all) {
+  DeconvArgs a{};
+  a.D = D;
+  int64_t off = P.beta_off;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    a.N[d] = P.N[d];
+    a.Nt[d] = P.g.Nt[d];
+    a.beta[d] = beta_all + off;
+    off += P.N[d];
+  }
+  return a;
+}
+
+template <int D, typename R>
+__global__ void deconv_pad_batch_kernel(const BatchProblem* __restrict__ probs, const R* __restrict__ beta_all,
+                                        const typename Cplx<R>::type* __restrict__ f,
+                                        typename Cplx<R>::type* __restrict__ grid) {
+  const BatchProblem& P = probs[blockIdx.y];
+  const DeconvArgs a = batch_deconv_args<D, R>(P, beta_all);
+  deconv_pad_body<D, R>(a, f + P.in_off, grid + P.grid_off);
+}
+
 // Algorithm 2 lines 8-10: y_n = g[n mod N~] * prod_d beta_d(n_d), n in I_N.
 template <int D, typename R>
-__global__ void crop_deconv_kernel(DeconvArgs a, const typename Cplx<R>::type* __restrict__ grid,
-                                   typename Cplx<R>::type* __restrict__ y) {
+__device__ __forceinline__ void crop_deconv_body(const DeconvArgs& a, const typename Cplx<R>::type* __restrict__ grid,
+                                                 typename Cplx<R>::type* __restrict__ y) {
   using C = typename Cplx<R>::type;
   const R* __restrict__ beta0 = (const R*)a.beta[0];
   const R* __restrict__ beta1 = (const R*)a.beta[D > 1 ? 1 : 0];
@@ -254,6 +285,21 @@ __global__ void crop_deconv_kernel(DeconvArgs a, const typename Cplx<R>::type* _
   }
 }
 
+template <int D, typename R>
+__global__ void crop_deconv_kernel(DeconvArgs a, const typename Cplx<R>::type* __restrict__ grid,
+                                   typename Cplx<R>::type* __restrict__ y) {
+  crop_deconv_body<D, R>(a, grid, y);
+}
+
+template <int D, typename R>
+__global__ void crop_deconv_batch_kernel(const BatchProblem* __restrict__ probs, const R* __restrict__ beta_all,
+                                         const typename Cplx<R>::type* __restrict__ grid,
+                                         typename Cplx<R>::type* __restrict__ y) {
+  const BatchProblem& P = probs[blockIdx.y];
+  const DeconvArgs a = batch_deconv_args<D, R>(P, beta_all);
+  crop_deconv_body<D, R>(a, grid + P.grid_off, y + P.in_off);
+}
+
 template <typename R>
 cudaError_t launch_deconv_pad(const DeconvArgs& a, const void* f, void* grid, cudaStream_t s) {
   using C = typename Cplx<R>::type;
@@ -283,6 +329,46 @@ cudaError_t launch_crop_deconv(const DeconvArgs& a, const void* grid, void* y, c
     crop_deconv_kernel<3, R><<<blocks, 256, 0, s>>>(a, (const C*)grid, (C*)y);
   return cudaGetLastError();
 }
+
+
+template <typename R>
+cudaError_t launch_deconv_pad_batch(int D, int B, int64_t max_grid, const BatchProblem* probs,
+                                    const void* beta_all, const void* f, void* grid, cudaStream_t s) {
+  using C = typename Cplx<R>::type;
+  dim3 blocks(launch_blocks(max_grid / 2, 256), B);
+  const R* beta = (const R*)beta_all;
+  if (D == 1)
+    deconv_pad_batch_kernel<1, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)f, (C*)grid);
+  else if (D == 2)
+    deconv_pad_batch_kernel<2, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)f, (C*)grid);
+  else
+    deconv_pad_batch_kernel<3, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)f, (C*)grid);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_crop_deconv_batch(int D, int B, int64_t max_n, const BatchProblem* probs,
+                                     const void* beta_all, const void* grid, void* y, cudaStream_t s) {
+  using C = typename Cplx<R>::type;
+  dim3 blocks(launch_blocks(max_n, 256), B);
+  const R* beta = (const R*)beta_all;
+  if (D == 1)
+    crop_deconv_batch_kernel<1, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)grid, (C*)y);
+  else if (D == 2)
+    crop_deconv_batch_kernel<2, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)grid, (C*)y);
+  else
+    crop_deconv_batch_kernel<3, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)grid, (C*)y);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_deconv_pad_batch<float>(int, int, int64_t, const BatchProblem*, const void*,
+                                                    const void*, void*, cudaStream_t);
+template cudaError_t launch_deconv_pad_batch<double>(int, int, int64_t, const BatchProblem*, const void*,
+                                                     const void*, void*, cudaStream_t);
+template cudaError_t launch_crop_deconv_batch<float>(int, int, int64_t, const BatchProblem*, const void*,
+                                                     const void*, void*, cudaStream_t);
+template cudaError_t launch_crop_deconv_batch<double>(int, int, int64_t, const BatchProblem*, const void*,
+                                                      const void*, void*, cudaStream_t);
 
 template cudaError_t launch_deconv_pad<float>(const DeconvArgs&, const void*, void*, cudaStream_t);
 template cudaError_t launch_deconv_pad<double>(const DeconvArgs&, const void*, void*, cudaStream_t);
@@ -434,6 +520,23 @@ cudaError_t launch_node_place(const SortArgs& a, const void* k, int k_is_fp64, c
   if (a.M == 0) return cudaSuccess;
   node_place_kernel<<<launch_blocks(a.M, 256), 256, 0, s>>>(a, k, k_is_fp64, key, rank, tile_offset,
                                                             cell, frac, frac_is_fp64, perm);
+  return cudaGetLastError();
+}
+
+// Copy a node set's work items into the batch list, tagging them with problem p.
+__global__ void items_expand_kernel(const int4* src, const int* n_src, int4* dst, const int* dst_off, int p) {
+  const int n = *n_src;
+  const int base = *dst_off;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int4 v = src[i];
+    v.w = p;
+    dst[base + i] = v;
+  }
+}
+
+cudaError_t launch_items_expand(const int4* src, const int* n_src, int max_n, int4* dst, const int* dst_off, int p,
+                                cudaStream_t s) {
+  items_expand_kernel<<<launch_blocks(max_n, 256), 256, 0, s>>>(src, n_src, dst, dst_off, p);
   return cudaGetLastError();
 }
 

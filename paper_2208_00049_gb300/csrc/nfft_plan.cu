@@ -10,7 +10,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "nfft_internal.cuh"
 
@@ -643,6 +647,101 @@ int nfft_plan_set_tile(nfft_plan* p, const int64_t* tile3) {
   s = configure_tiles(p, T);
   if (s != NFFT_OK) return s;
   p->has_nodes = false;  // the bin-sort depends on the tile shape
+  return NFFT_OK;
+}
+
+// Tile-shape autotuner (Sec. 5.2 sweeps the block size; Sec. 6 proposes an
+// FFTW_MEASURE-like automatic choice): time forward + adjoint for each
+// candidate tile on the caller's nodes, keep the fastest, cache it per shape.
+namespace {
+std::mutex g_plan_tune_mutex;
+std::map<std::string, std::vector<int64_t>> g_plan_tune_cache;
+
+std::vector<std::vector<int64_t>> plan_tile_candidates(const nfft_plan* p) {
+  std::vector<std::vector<int64_t>> c;
+  if (p->D == 1) {
+    for (int64_t t : {64, 128, 256, 512, 1024, 2048, 4096}) c.push_back({t, 1, 1});
+  } else if (p->D == 2) {
+    for (int64_t t : {8, 16, 32, 64}) c.push_back({t, t, 1});
+    c.push_back({16, 32, 1});
+    c.push_back({32, 16, 1});
+  } else {
+    for (int64_t t : {4, 8, 16}) c.push_back({t, t, t});
+    c.push_back({8, 8, 4});
+    c.push_back({4, 8, 8});
+    c.push_back({16, 8, 8});
+  }
+  std::vector<std::vector<int64_t>> ok;
+  const int kind = (p->flags & NFFT_FLAG_COMPENSATED) ? 2 : 1;
+  for (auto& t : c) {
+    bool fits = true;
+    for (int d = 0; d < p->D; ++d)
+      if (t[d] > p->Nt[d]) fits = false;
+    if (fits && region_bytes(p, t.data(), kind) <= 160 * 1024) ok.push_back(t);
+  }
+  return ok;
+}
+}  // namespace
+
+int nfft_plan_autotune(nfft_plan* p, const void* k, int k_is_fp64, int64_t* chosen3) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!k && p->M > 0) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  std::string key = "plan:" + std::to_string(p->device) + ":" + std::to_string(p->D) + ":" +
+                    std::to_string(p->m) + ":" + std::to_string(p->dtype) + ":" + std::to_string(p->flags) +
+                    ":" + std::to_string(p->M) + ":" + std::to_string(p->sigma);
+  for (int d = 0; d < p->D; ++d) key += "," + std::to_string(p->N[d]);
+  std::vector<int64_t> best;
+  {
+    std::lock_guard<std::mutex> lock(g_plan_tune_mutex);
+    auto it = g_plan_tune_cache.find(key);
+    if (it != g_plan_tune_cache.end()) best = it->second;
+  }
+  if (best.empty()) {
+    void *f = nullptr, *fh = nullptr;
+    s = dalloc(p, &f, (size_t)prod_N(p) * cplx_size(p));
+    if (s == NFFT_OK) s = dalloc(p, &fh, (size_t)p->M * cplx_size(p));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s == NFFT_OK) {
+      cudaMemsetAsync(f, 0, (size_t)prod_N(p) * cplx_size(p), p->stream);
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+    }
+    float best_ms = 1e30f;
+    for (auto& t : plan_tile_candidates(p)) {
+      if (s != NFFT_OK) break;
+      if ((s = configure_tiles(p, t.data())) != NFFT_OK) break;
+      if ((s = nfft_set_nodes(p, k, k_is_fp64)) != NFFT_OK) break;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3 && s == NFFT_OK; ++rep) {
+        cudaEventRecord(e0, p->stream);
+        s = nfft_forward(p, f, fh);
+        if (s == NFFT_OK) s = nfft_adjoint(p, fh, f);
+        cudaEventRecord(e1, p->stream);
+        cudaEventSynchronize(e1);
+        float t_ms = 0.f;
+        cudaEventElapsedTime(&t_ms, e0, e1);
+        if (rep > 0) ms += t_ms;  // the first repeat warms up
+      }
+      if (s == NFFT_OK && ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dfree(f);
+    dfree(fh);
+    if (s != NFFT_OK) return s;
+    if (best.empty()) return NFFT_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_plan_tune_mutex);
+    g_plan_tune_cache[key] = best;
+  }
+  if ((s = configure_tiles(p, best.data())) != NFFT_OK) return s;
+  if ((s = nfft_set_nodes(p, k, k_is_fp64)) != NFFT_OK) return s;
+  if (chosen3)
+    for (int d = 0; d < kMaxD; ++d) chosen3[d] = d < p->D ? best[d] : 1;
   return NFFT_OK;
 }
 

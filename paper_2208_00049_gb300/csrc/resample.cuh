@@ -111,6 +111,90 @@ __device__ __forceinline__ void node_weight_derivs(const Geometry& g, int d, int
 // ---------------------------------------------------------------------------
 // Direct resampling (Algorithm 3)
 // ---------------------------------------------------------------------------
+// One work item (tile + a slice of its sorted nodes) of the direct resampling.
+template <int D, int K, typename R>
+__device__ __forceinline__ void gather_item(const Geometry& g, const typename CplxT<R>::type* __restrict__ grid,
+                                            const NodeArrays& na, const int4 item,
+                                            typename CplxT<R>::type* __restrict__ fhat,
+                                            typename CplxT<R>::type* tile) {
+  using C = typename CplxT<R>::type;
+  const R* __restrict__ frac = reinterpret_cast<const R*>(na.frac);
+  const int region = region_size<D>(g);
+  const int mi = (int)g.m;
+  const int64_t M = g.M;
+  int tc[kMaxD], start[kMaxD];
+  tile_coords<D>(g, item.x, tc);
+#pragma unroll
+  for (int d = 0; d < D; ++d) start[d] = tc[d] * g.T[d] + g.off;
+
+  __syncthreads();  // the previous item's nodes are done with the tile
+  for (int e = threadIdx.x; e < region; e += blockDim.x) tile[e] = grid[region_to_grid<D>(g, start, e)];
+  __syncthreads();
+
+  for (int q = item.y + threadIdx.x; q < item.y + item.z; q += blockDim.x) {
+    R w[D][K];
+    int a[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      a[d] = na.cell[d * M + q] - tc[d] * g.T[d];
+      node_weights<K, R>(g, d, mi, frac[d * M + q], w[d]);
+    }
+    R re = R(0), im = R(0);
+    if constexpr (D == 1) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        C v = tile[a[0] + i];
+        re += w[0][i] * v.x;
+        im += w[0][i] * v.y;
+      }
+    } else if constexpr (D == 2) {
+#pragma unroll
+      for (int i0 = 0; i0 < K; ++i0) {
+        const C* row = tile + (a[0] + i0) * g.L[1] + a[1];
+        R sr = R(0), si = R(0);
+#pragma unroll
+        for (int i1 = 0; i1 < K; ++i1) {
+          C v = row[i1];
+          sr += w[1][i1] * v.x;
+          si += w[1][i1] * v.y;
+        }
+        re += w[0][i0] * sr;
+        im += w[0][i0] * si;
+      }
+    } else {
+#pragma unroll 1
+      for (int i0 = 0; i0 < K; ++i0) {
+        const C* plane = tile + ((a[0] + i0) * g.L[1] + a[1]) * g.L[2] + a[2];
+        R s1r = R(0), s1i = R(0);
+#pragma unroll
+        for (int i1 = 0; i1 < K; ++i1) {
+          const C* row = plane + i1 * g.L[2];
+          R s2r = R(0), s2i = R(0);
+#pragma unroll
+          for (int i2 = 0; i2 < K; ++i2) {
+            C v = row[i2];
+            s2r += w[2][i2] * v.x;
+            s2i += w[2][i2] * v.y;
+          }
+          s1r += w[1][i1] * s2r;
+          s1i += w[1][i1] * s2i;
+        }
+        // w[0] is indexed by a rolled loop: keep the select explicit so the
+        // array stays in registers.
+        R w0 = R(0);
+#pragma unroll
+        for (int i = 0; i < K; ++i) w0 = (i == i0) ? w[0][i] : w0;
+        re += w0 * s1r;
+        im += w0 * s1i;
+      }
+    }
+    C out;
+    out.x = re;
+    out.y = im;
+    fhat[na.perm[q]] = out;
+  }
+}
+
 template <int D, int K, typename R>
 __global__ void __launch_bounds__(kResampleThreads)
     gather_kernel(Geometry g, const typename CplxT<R>::type* __restrict__ grid, NodeArrays na,
@@ -118,86 +202,30 @@ __global__ void __launch_bounds__(kResampleThreads)
   using C = typename CplxT<R>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tile = reinterpret_cast<C*>(smem_raw);
-  const R* __restrict__ frac = reinterpret_cast<const R*>(na.frac);
   const int nitems = *na.n_items;
-  const int region = region_size<D>(g);
-  const int mi = (int)g.m;
-  const int64_t M = g.M;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x)
+    gather_item<D, K, R>(g, grid, na, na.items[it], fhat, tile);
+}
 
+// Batched: one persistent launch over the work items of many problems; item.w
+// names the problem, whose geometry and buffer offsets come from `probs`.
+template <int D, int K, typename R>
+__global__ void __launch_bounds__(kResampleThreads)
+    gather_batch_kernel(const BatchProblem* __restrict__ probs, const typename CplxT<R>::type* __restrict__ grid,
+                        BatchNodes nb, typename CplxT<R>::type* __restrict__ fhat) {
+  using C = typename CplxT<R>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tile = reinterpret_cast<C*>(smem_raw);
+  const int nitems = *nb.n_items;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int4 item = na.items[it];
-    int tc[kMaxD], start[kMaxD];
-    tile_coords<D>(g, item.x, tc);
-#pragma unroll
-    for (int d = 0; d < D; ++d) start[d] = tc[d] * g.T[d] + g.off;
-
-    __syncthreads();  // the previous item's nodes are done with the tile
-    for (int e = threadIdx.x; e < region; e += blockDim.x)
-      tile[e] = grid[region_to_grid<D>(g, start, e)];
-    __syncthreads();
-
-    for (int q = item.y + threadIdx.x; q < item.y + item.z; q += blockDim.x) {
-      R w[D][K];
-      int a[D];
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        a[d] = na.cell[d * M + q] - tc[d] * g.T[d];
-        node_weights<K, R>(g, d, mi, frac[d * M + q], w[d]);
-      }
-      R re = R(0), im = R(0);
-      if constexpr (D == 1) {
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-          C v = tile[a[0] + i];
-          re += w[0][i] * v.x;
-          im += w[0][i] * v.y;
-        }
-      } else if constexpr (D == 2) {
-#pragma unroll
-        for (int i0 = 0; i0 < K; ++i0) {
-          const C* row = tile + (a[0] + i0) * g.L[1] + a[1];
-          R sr = R(0), si = R(0);
-#pragma unroll
-          for (int i1 = 0; i1 < K; ++i1) {
-            C v = row[i1];
-            sr += w[1][i1] * v.x;
-            si += w[1][i1] * v.y;
-          }
-          re += w[0][i0] * sr;
-          im += w[0][i0] * si;
-        }
-      } else {
-#pragma unroll 1
-        for (int i0 = 0; i0 < K; ++i0) {
-          const C* plane = tile + ((a[0] + i0) * g.L[1] + a[1]) * g.L[2] + a[2];
-          R s1r = R(0), s1i = R(0);
-#pragma unroll
-          for (int i1 = 0; i1 < K; ++i1) {
-            const C* row = plane + i1 * g.L[2];
-            R s2r = R(0), s2i = R(0);
-#pragma unroll
-            for (int i2 = 0; i2 < K; ++i2) {
-              C v = row[i2];
-              s2r += w[2][i2] * v.x;
-              s2i += w[2][i2] * v.y;
-            }
-            s1r += w[1][i1] * s2r;
-            s1i += w[1][i1] * s2i;
-          }
-          // w[0] is indexed by a rolled loop: keep the select explicit so the
-          // array stays in registers.
-          R w0 = R(0);
-#pragma unroll
-          for (int i = 0; i < K; ++i) w0 = (i == i0) ? w[0][i] : w0;
-          re += w0 * s1r;
-          im += w0 * s1i;
-        }
-      }
-      C out;
-      out.x = re;
-      out.y = im;
-      fhat[na.perm[q]] = out;
-    }
+    const int4 item = nb.items[it];
+    const BatchProblem& P = probs[item.w];
+    const Geometry g = P.g;
+    NodeArrays na;
+    na.cell = nb.cell + D * P.node_off;
+    na.frac = reinterpret_cast<const R*>(nb.frac) + D * P.node_off;
+    na.perm = nb.perm + P.node_off;
+    gather_item<D, K, R>(g, grid + P.grid_off, na, item, fhat + P.out_off, tile);
   }
 }
 
@@ -227,91 +255,114 @@ __device__ __forceinline__ void grid_add(double2* p, double re, double im) {
 }
 
 template <int D, int K, typename R, bool COMP>
+__device__ __forceinline__ void scatter_item(const Geometry& g, typename CplxT<R>::type* __restrict__ grid,
+                                             const NodeArrays& na, const int4 item,
+                                             const typename CplxT<R>::type* __restrict__ fhat, R* acc) {
+  using C = typename CplxT<R>::type;
+  const int region = region_size<D>(g);
+  R* comp = acc + (COMP ? 2 * region : 0);  // TwoSum error terms
+  const R* __restrict__ frac = reinterpret_cast<const R*>(na.frac);
+  const int mi = (int)g.m;
+  const int64_t M = g.M;
+  int tc[kMaxD], start[kMaxD];
+  tile_coords<D>(g, item.x, tc);
+#pragma unroll
+  for (int d = 0; d < D; ++d) start[d] = tc[d] * g.T[d] + g.off;
+
+  __syncthreads();  // previous flush finished reading the tile
+  for (int e = threadIdx.x; e < 2 * region * (COMP ? 2 : 1); e += blockDim.x) acc[e] = R(0);
+  __syncthreads();
+
+  for (int q = item.y + threadIdx.x; q < item.y + item.z; q += blockDim.x) {
+    R w[D][K];
+    int a[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      a[d] = na.cell[d * M + q] - tc[d] * g.T[d];
+      node_weights<K, R>(g, d, mi, frac[d * M + q], w[d]);
+    }
+    const C v = fhat[na.perm[q]];
+    if constexpr (D == 1) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int idx = 2 * (a[0] + i);
+        smem_add<R, COMP>(acc, comp, idx, v.x * w[0][i]);
+        smem_add<R, COMP>(acc, comp, idx + 1, v.y * w[0][i]);
+      }
+    } else if constexpr (D == 2) {
+#pragma unroll
+      for (int i0 = 0; i0 < K; ++i0) {
+        const R vr = v.x * w[0][i0], vi = v.y * w[0][i0];
+        const int rowi = (a[0] + i0) * g.L[1] + a[1];
+#pragma unroll
+        for (int i1 = 0; i1 < K; ++i1) {
+          const int idx = 2 * (rowi + i1);
+          smem_add<R, COMP>(acc, comp, idx, vr * w[1][i1]);
+          smem_add<R, COMP>(acc, comp, idx + 1, vi * w[1][i1]);
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int i0 = 0; i0 < K; ++i0) {
+        R w0 = R(0);
+#pragma unroll
+        for (int i = 0; i < K; ++i) w0 = (i == i0) ? w[0][i] : w0;
+        const R v0r = v.x * w0, v0i = v.y * w0;
+        const int planei = ((a[0] + i0) * g.L[1] + a[1]) * g.L[2] + a[2];
+#pragma unroll
+        for (int i1 = 0; i1 < K; ++i1) {
+          const R vr = v0r * w[1][i1], vi = v0i * w[1][i1];
+          const int rowi = planei + i1 * g.L[2];
+#pragma unroll
+          for (int i2 = 0; i2 < K; ++i2) {
+            const int idx = 2 * (rowi + i2);
+            smem_add<R, COMP>(acc, comp, idx, vr * w[2][i2]);
+            smem_add<R, COMP>(acc, comp, idx + 1, vi * w[2][i2]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // Add the tile (block plus halo) back to the grid; wrap applied here only.
+  for (int e = threadIdx.x; e < region; e += blockDim.x) {
+    R re = acc[2 * e], im = acc[2 * e + 1];
+    if constexpr (COMP) {
+      re += comp[2 * e];
+      im += comp[2 * e + 1];
+    }
+    if (re != R(0) || im != R(0)) grid_add(grid + region_to_grid<D>(g, start, e), re, im);
+  }
+}
+
+template <int D, int K, typename R, bool COMP>
 __global__ void __launch_bounds__(kResampleThreads)
     scatter_kernel(Geometry g, typename CplxT<R>::type* __restrict__ grid, NodeArrays na,
                    const typename CplxT<R>::type* __restrict__ fhat) {
-  using C = typename CplxT<R>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int region = region_size<D>(g);
-  R* acc = reinterpret_cast<R*>(smem_raw);     // interleaved re, im
-  R* comp = acc + (COMP ? 2 * region : 0);     // TwoSum error terms
-  const R* __restrict__ frac = reinterpret_cast<const R*>(na.frac);
+  R* acc = reinterpret_cast<R*>(smem_raw);  // interleaved re, im
   const int nitems = *na.n_items;
-  const int mi = (int)g.m;
-  const int64_t M = g.M;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x)
+    scatter_item<D, K, R, COMP>(g, grid, na, na.items[it], fhat, acc);
+}
 
+template <int D, int K, typename R>
+__global__ void __launch_bounds__(kResampleThreads)
+    scatter_batch_kernel(const BatchProblem* __restrict__ probs, typename CplxT<R>::type* __restrict__ grid,
+                         BatchNodes nb, const typename CplxT<R>::type* __restrict__ fhat) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* acc = reinterpret_cast<R*>(smem_raw);
+  const int nitems = *nb.n_items;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int4 item = na.items[it];
-    int tc[kMaxD], start[kMaxD];
-    tile_coords<D>(g, item.x, tc);
-#pragma unroll
-    for (int d = 0; d < D; ++d) start[d] = tc[d] * g.T[d] + g.off;
-
-    __syncthreads();  // previous flush finished reading the tile
-    for (int e = threadIdx.x; e < 2 * region * (COMP ? 2 : 1); e += blockDim.x) acc[e] = R(0);
-    __syncthreads();
-
-    for (int q = item.y + threadIdx.x; q < item.y + item.z; q += blockDim.x) {
-      R w[D][K];
-      int a[D];
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        a[d] = na.cell[d * M + q] - tc[d] * g.T[d];
-        node_weights<K, R>(g, d, mi, frac[d * M + q], w[d]);
-      }
-      const C v = fhat[na.perm[q]];
-      if constexpr (D == 1) {
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-          const int idx = 2 * (a[0] + i);
-          smem_add<R, COMP>(acc, comp, idx, v.x * w[0][i]);
-          smem_add<R, COMP>(acc, comp, idx + 1, v.y * w[0][i]);
-        }
-      } else if constexpr (D == 2) {
-#pragma unroll
-        for (int i0 = 0; i0 < K; ++i0) {
-          const R vr = v.x * w[0][i0], vi = v.y * w[0][i0];
-          const int rowi = (a[0] + i0) * g.L[1] + a[1];
-#pragma unroll
-          for (int i1 = 0; i1 < K; ++i1) {
-            const int idx = 2 * (rowi + i1);
-            smem_add<R, COMP>(acc, comp, idx, vr * w[1][i1]);
-            smem_add<R, COMP>(acc, comp, idx + 1, vi * w[1][i1]);
-          }
-        }
-      } else {
-#pragma unroll 1
-        for (int i0 = 0; i0 < K; ++i0) {
-          R w0 = R(0);
-#pragma unroll
-          for (int i = 0; i < K; ++i) w0 = (i == i0) ? w[0][i] : w0;
-          const R v0r = v.x * w0, v0i = v.y * w0;
-          const int planei = ((a[0] + i0) * g.L[1] + a[1]) * g.L[2] + a[2];
-#pragma unroll
-          for (int i1 = 0; i1 < K; ++i1) {
-            const R vr = v0r * w[1][i1], vi = v0i * w[1][i1];
-            const int rowi = planei + i1 * g.L[2];
-#pragma unroll
-            for (int i2 = 0; i2 < K; ++i2) {
-              const int idx = 2 * (rowi + i2);
-              smem_add<R, COMP>(acc, comp, idx, vr * w[2][i2]);
-              smem_add<R, COMP>(acc, comp, idx + 1, vi * w[2][i2]);
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-
-    // Add the tile (block plus halo) back to the grid; wrap applied here only.
-    for (int e = threadIdx.x; e < region; e += blockDim.x) {
-      R re = acc[2 * e], im = acc[2 * e + 1];
-      if constexpr (COMP) {
-        re += comp[2 * e];
-        im += comp[2 * e + 1];
-      }
-      if (re != R(0) || im != R(0)) grid_add(grid + region_to_grid<D>(g, start, e), re, im);
-    }
+    const int4 item = nb.items[it];
+    const BatchProblem& P = probs[item.w];
+    const Geometry g = P.g;
+    NodeArrays na;
+    na.cell = nb.cell + D * P.node_off;
+    na.frac = reinterpret_cast<const R*>(nb.frac) + D * P.node_off;
+    na.perm = nb.perm + P.node_off;
+    scatter_item<D, K, R, false>(g, grid + P.grid_off, na, item, fhat + P.out_off, acc);
   }
 }
 
@@ -453,6 +504,24 @@ void* pick_scatter(int D, int K, int compensated) {
     }                                                                        \
     return compensated ? nullptr : (void*)scatter_kernel<DD, KK, R, false>;  \
   }
+  NFFTGB_FOR_EACH_DK(NFFTGB_PICK)
+#undef NFFTGB_PICK
+  return nullptr;
+}
+
+template <typename R>
+void* pick_gather_batch(int D, int K) {
+#define NFFTGB_PICK(DD, KK) \
+  if (D == DD && K == KK) return (void*)gather_batch_kernel<DD, KK, R>;
+  NFFTGB_FOR_EACH_DK(NFFTGB_PICK)
+#undef NFFTGB_PICK
+  return nullptr;
+}
+
+template <typename R>
+void* pick_scatter_batch(int D, int K) {
+#define NFFTGB_PICK(DD, KK) \
+  if (D == DD && K == KK) return (void*)scatter_batch_kernel<DD, KK, R>;
   NFFTGB_FOR_EACH_DK(NFFTGB_PICK)
 #undef NFFTGB_PICK
   return nullptr;

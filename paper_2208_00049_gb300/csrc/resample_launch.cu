@@ -10,6 +10,10 @@ template <typename R>
 void* pick_scatter(int D, int K, int compensated);
 template <typename R>
 void* pick_grad(int D, int K);
+template <typename R>
+void* pick_gather_batch(int D, int K);
+template <typename R>
+void* pick_scatter_batch(int D, int K);
 
 template <typename R>
 struct CplxL;
@@ -102,6 +106,48 @@ cudaError_t launch_grad_gather(const Geometry& g, const void* grid, const NodeAr
   return cudaGetLastError();
 }
 
+template <typename R>
+int resample_batch_ctas_per_sm(const Geometry& gmax, int kind) {
+  void* k = kind == 0 ? pick_gather_batch<R>(gmax.D, gmax.K) : pick_scatter_batch<R>(gmax.D, gmax.K);
+  if (!k) return 0;
+  size_t smem = resample_smem_bytes<R>(gmax, kind == 0 ? 0 : 1);
+  if (prepare_smem(k, smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kResampleThreads, smem) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+// gmax: a geometry whose region L is the largest of the batch (sizes the
+// shared-memory tile); the kernels read each problem's own geometry.
+template <typename R>
+cudaError_t launch_gather_batch(const BatchProblem* probs, const Geometry& gmax, const void* grid,
+                                const BatchNodes& nb, void* fhat, int ctas, cudaStream_t s) {
+  using C = typename CplxL<R>::type;
+  void* k = pick_gather_batch<R>(gmax.D, gmax.K);
+  if (!k) return cudaErrorInvalidValue;
+  size_t smem = resample_smem_bytes<R>(gmax, 0);
+  cudaError_t e = prepare_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  auto kern = reinterpret_cast<void (*)(const BatchProblem*, const C*, BatchNodes, C*)>(k);
+  kern<<<ctas, kResampleThreads, smem, s>>>(probs, (const C*)grid, nb, (C*)fhat);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_scatter_batch(const BatchProblem* probs, const Geometry& gmax, void* grid,
+                                 const BatchNodes& nb, const void* fhat, int ctas, cudaStream_t s) {
+  using C = typename CplxL<R>::type;
+  void* k = pick_scatter_batch<R>(gmax.D, gmax.K);
+  if (!k) return cudaErrorInvalidValue;
+  size_t smem = resample_smem_bytes<R>(gmax, 1);
+  cudaError_t e = prepare_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  auto kern = reinterpret_cast<void (*)(const BatchProblem*, C*, BatchNodes, const C*)>(k);
+  kern<<<ctas, kResampleThreads, smem, s>>>(probs, (C*)grid, nb, (const C*)fhat);
+  return cudaGetLastError();
+}
+
 #define NFFTGB_INSTANTIATE_LAUNCH(R)                                                             \
   template size_t resample_smem_bytes<R>(const Geometry&, int);                                 \
   template int resample_ctas_per_sm<R>(const Geometry&, int);                                   \
@@ -110,7 +156,12 @@ cudaError_t launch_grad_gather(const Geometry& g, const void* grid, const NodeAr
   template cudaError_t launch_scatter<R>(const Geometry&, void*, const NodeArrays&, const void*,\
                                          int, int, cudaStream_t);                               \
   template cudaError_t launch_grad_gather<R>(const Geometry&, const void*, const NodeArrays&,   \
-                                             const void*, void*, int, cudaStream_t);
+                                             const void*, void*, int, cudaStream_t);            \
+  template int resample_batch_ctas_per_sm<R>(const Geometry&, int);                             \
+  template cudaError_t launch_gather_batch<R>(const BatchProblem*, const Geometry&, const void*, \
+                                              const BatchNodes&, void*, int, cudaStream_t);     \
+  template cudaError_t launch_scatter_batch<R>(const BatchProblem*, const Geometry&, void*,      \
+                                               const BatchNodes&, const void*, int, cudaStream_t);
 NFFTGB_INSTANTIATE_LAUNCH(float)
 NFFTGB_INSTANTIATE_LAUNCH(double)
 

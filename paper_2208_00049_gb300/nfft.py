@@ -133,6 +133,14 @@ class Plan:
         B.check(B.nfft_plan_set_tile(self.handle, tile), "nfft_plan_set_tile")
         self._nodes_key = None
 
+    def autotune(self, k):
+        """Choose the tile shape by timing candidates on these nodes (leaves them set)."""
+        self._check_tensor(k, (self.M, self.D), k.dtype, "k")
+        s, tile = B.nfft_plan_autotune(self.handle, _ptr(k), k.dtype == torch.float64)
+        B.check(s, "nfft_plan_autotune")
+        self._nodes_key = (k.data_ptr(), k._version, k.device)
+        return tile[:self.D]
+
     @property
     def Ntilde(self):
         return self.info()["Ntilde"]
@@ -170,6 +178,73 @@ class Plan:
         self._check_tensor(out, (self.M, self.D), self.real_dtype, "out")
         B.check(B.nfft_step_grad_gather(self.handle, _ptr(cot), _ptr(out)), "nfft_step_grad_gather")
         return out
+
+
+class Batch:
+    """Many NFFTs in one launch per step (nfft_batch_*): problems with their own
+    sizes N[p] on node sets set_of[p] with M_set[s] nodes."""
+
+    def __init__(self, Ns, set_of, M_set, sigma=2.0, m=4, dtype=torch.complex64, flags=0, stream=None):
+        if dtype not in _DTYPES:
+            raise TypeError("dtype must be torch.complex64 or torch.complex128")
+        self.Ns = [tuple(int(v) for v in n) for n in Ns]
+        self.D = len(self.Ns[0])
+        self.set_of = [int(v) for v in set_of]
+        self.M_set = [int(v) for v in M_set]
+        self.dtype = dtype
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        flat = [v for n in self.Ns for v in n]
+        s, h = B.nfft_batch_create(self.D, flat, self.set_of, self.M_set, sigma, m, _DTYPES[dtype], flags,
+                                   self.stream.cuda_stream)
+        B.check(s, "nfft_batch_create")
+        self._h = h
+        self.in_sizes = [int(torch.tensor(n).prod()) for n in self.Ns]
+        self.out_sizes = [self.M_set[p] for p in self.set_of]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.nfft_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_nodes(self, k_all):
+        """k_all: the node sets concatenated, (sum M_set, D) float64 on the device."""
+        B.check(B.nfft_batch_set_nodes(self._h, _ptr(k_all), k_all.dtype == torch.float64), "nfft_batch_set_nodes")
+
+    def forward(self, f_all, out=None):
+        """f_all: concatenated flattened coefficient arrays; returns concatenated fhat."""
+        if out is None:
+            out = torch.empty(sum(self.out_sizes), dtype=self.dtype, device=self.device)
+        B.check(B.nfft_batch_forward(self._h, _ptr(f_all), _ptr(out)), "nfft_batch_forward")
+        return out
+
+    def adjoint(self, fhat_all, out=None):
+        if out is None:
+            out = torch.empty(sum(self.in_sizes), dtype=self.dtype, device=self.device)
+        B.check(B.nfft_batch_adjoint(self._h, _ptr(fhat_all), _ptr(out)), "nfft_batch_adjoint")
+        return out
+
+    def set_graph(self, enable=True):
+        B.check(B.nfft_batch_set_graph(self._h, enable), "nfft_batch_set_graph")
+
+    def set_tile(self, tile):
+        B.check(B.nfft_batch_set_tile(self._h, tile), "nfft_batch_set_tile")
+
+    def autotune(self, k_all):
+        s, tile = B.nfft_batch_autotune(self._h, _ptr(k_all), k_all.dtype == torch.float64)
+        B.check(s, "nfft_batch_autotune")
+        return tile[:self.D]
+
+    def info(self):
+        s, tile, n_items, n_cls = B.nfft_batch_info(self._h)
+        B.check(s, "nfft_batch_info")
+        return {"tile": tile[:self.D], "n_items": n_items, "fft_classes": n_cls}
 
 
 def _view_device_memory(ptr, shape, dtype, device):

@@ -291,3 +291,19 @@ def test_fast3d_m4_hot_tile_and_boundaries():
     fh, y = _run(case, "c64")
     assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), 1e-5, "forward")
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), 1e-5, "adjoint")
+
+
+@pytest.mark.parametrize("N,M,dt", [((40, 36), 3000, "c64"), ((24, 20, 28), 6000, "c64"), ((300,), 900, "c128")])
+def test_autotuned_plan_matches_oracle(N, M, dt):
+    """The autotuner picks a tile by timing candidates; results stay exact."""
+    from paper_2208_00049_gb300.nfft import Plan
+    case = inputs.small_case(N, M, seed=59, m=4)
+    plan = Plan(N, M, sigma=2.0, m=4, dtype=cdtype(dt))
+    k = to_dev(case["k"], torch.float64)
+    tile = plan.autotune(k)
+    assert len(tile) == len(N) and plan.info()["tile"] == tuple(tile)
+    fh = plan.forward(to_dev(case["f"], cdtype(dt))).cpu().numpy()
+    y = plan.adjoint(to_dev(case["w"], cdtype(dt))).cpu().numpy()
+    plan.close()
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), TOL[dt], "forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), TOL[dt], "adjoint")
