@@ -37,6 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
 WORKLOADS = {
+    "batched": "batched",
     "3d": "3d",
     "3d_lean": "3d_lean",
     "2d_c64": "2d_c64",
@@ -48,14 +49,16 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=131072,
                     help="nodes in the oracle's bounded sample")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the complex128 (FP64) comparison run")
     return ap.parse_args()
 
 
@@ -205,7 +208,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2208_00049_gb300 import inputs
-    wl = inputs.workload(WORKLOADS[args.workload])
+    wl = inputs.workload(WORKLOADS[args.workload] if args.workload != "batched" else "3d")
     vals = []
     det = None
     for _ in range(max(1, args.warmup)):
@@ -245,6 +248,102 @@ def algorithmic_bytes(wl, kernel):
     if kernel == "crop_deconv":
         return 2 * nvals
     raise KeyError(kernel)
+
+
+def time_steps(step_fn, steps, warmup, stream, flush):
+    """Mean ms of step_fn over `steps` event-timed runs (L2 flushed before each)."""
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        step_fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        step_fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def fp64_form(wl, fhat32, steps, warmup, flush):
+    """The plain FP64 form (complex128 plan, same kernels' FP64 instantiation)
+    on the same workload: throughput and the FP32 result's distance to it."""
+    import numpy as np
+    import torch
+    from paper_2208_00049_gb300.nfft import Plan
+    stream = torch.cuda.current_stream()
+    plan = Plan(wl["N"], wl["M"], sigma=wl["sigma"], m=wl["m"], dtype=torch.complex128)
+    plan.set_nodes(torch.from_numpy(wl["k"]).cuda())
+    f = torch.from_numpy(wl["f"]).cuda()
+    w = torch.from_numpy(wl["w"]).cuda()
+    fh = torch.empty(wl["M"], dtype=torch.complex128, device="cuda")
+    y = torch.empty(wl["N"], dtype=torch.complex128, device="cuda")
+
+    def step():
+        plan.forward(f, fh)
+        plan.adjoint(w, y)
+    ms = time_steps(step, steps, warmup, stream, flush)
+    ref = fh.cpu().numpy()
+    plan.close()
+    err = float(np.linalg.norm(fhat32.astype(np.complex128) - ref) / np.linalg.norm(ref))
+    return {"value": wl["M"] / (ms * 1e-3), "unit": UNIT, "ms_per_step": round(ms, 3), "dtype": "f64",
+            "steps": steps}, ref, err
+
+
+def ndft_sample_error(wl, fhat, n=48, seed=11):
+    """Relative L2 error of fhat against the exact FP64 NDFT (oracle) on n sampled nodes."""
+    import numpy as np
+    from oracle import ndft as ondft
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(wl["M"], n, replace=False)
+    ex = ondft.ndft(wl["k"][sel], wl["f"])
+    return float(np.linalg.norm(fhat[sel] - ex) / np.linalg.norm(ex))
+
+
+def run_batched(args):
+    """Workload 4: 64 uneven 2D problems in one persistent launch per step,
+    graph-captured, autotuned tile (nodes/s summed over the problems)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_00049_gb300 import inputs
+    from paper_2208_00049_gb300.nfft import Batch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    probs = inputs.batched_problems(n_problems=64)
+    Ns = [p["N"] for p in probs]
+    Ms = [p["M"] for p in probs]
+    b = Batch(Ns, list(range(64)), Ms, sigma=2.0, m=4, dtype=torch.complex64)
+    k_all = torch.from_numpy(np.concatenate([p["k"] for p in probs])).cuda()
+    tile = b.autotune(k_all)
+    b.set_graph(True)
+    f_all = torch.cat([torch.from_numpy(p["f"].ravel()) for p in probs]).to(torch.complex64).cuda()
+    w_all = torch.cat([torch.from_numpy(p["w"]) for p in probs]).to(torch.complex64).cuda()
+    fh = torch.empty(sum(Ms), dtype=torch.complex64, device="cuda")
+    y = torch.empty(f_all.numel(), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        b.forward(f_all, fh)
+        b.adjoint(w_all, y)
+    with ClockSampler(local) as clk:
+        ms = time_steps(step, args.steps, max(3, args.warmup), stream, flush)
+    info = b.info()
+    b.close()
+    M = sum(Ms)
+    line = {"metric": "batched NFFT fwd+adj nodes/s (64 uneven 2D problems, one launch per step)",
+            "value": M / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded PCG64)",
+            "config": {"workload": "batched 64 x 2D N in {64..512}^2, M = N1 N2 U(0.5,2), total M = %d" % M,
+                       "tile": list(tile), "work_items": info["n_items"], "fft_classes": info["fft_classes"],
+                       "graph": True, "l2": "flushed between steps (256 MiB write)"},
+            "clocks": clk.summary()}
+    print(json.dumps(line))
 
 
 def run_gpu(args):
@@ -367,7 +466,7 @@ def run_gpu(args):
             plan.forward(f_h, out=fh_h)
             plan.adjoint(w_h, out=y_h)
         times = []
-        for _ in range(max(3, args.steps // 2)):
+        for _ in range(min(50, max(3, args.steps // 2))):
             flush.zero_()
             ee[0].record(stream)
             plan.forward(f_h, out=fh_h)
@@ -385,11 +484,20 @@ def run_gpu(args):
         e2e = {"value": world * wl["M"] / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": ob, "ms_per_step": round(e2e_ms, 3)}
 
+    # FP64 form on the same workload, and the FP32 result's accuracy
+    fhat32 = fhat_d.cpu().numpy()
+    fp64 = None
+    accuracy = {}
+    if rank == 0 and not args.no_fp64_form and dt == torch.complex64:
+        fp64, ref64, err = fp64_form(wl, fhat32, min(10, max(3, args.steps // 4)), 2, flush)
+        accuracy["rel_l2_fp32_vs_fp64_form"] = err
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, det = oracle_throughput(wl, args.cpu_sample)
         cpu = {"value": v, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
                "sample": det["sample"], "detail": det}
+        accuracy["rel_l2_vs_ndft_48_sampled_nodes"] = ndft_sample_error(wl, fhat32)
 
     launches_per_step = 4  # deconv_pad, gather, scatter, crop_deconv (cuFFT and memset not counted)
     plan.close()
@@ -406,6 +514,8 @@ def run_gpu(args):
             "set_nodes_ms": round(set_nodes_ms, 3),
             "kernels": kernel_table,
             "roofline": roofline,
+            "fp64_form": fp64,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
@@ -421,6 +531,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_gpu(args)
 
