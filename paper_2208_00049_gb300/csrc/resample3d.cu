@@ -16,11 +16,14 @@
 //  * gather: a half-warp per node (a warp instruction serves two nodes);
 //    lane (g, i2) of a half owns taps (i1 = j + 4g, i2), j = 0..3, and loops
 //    over i0, then the half reduces its 16 partial sums;
-//  * scatter: four warps share one accumulator tile, warp w updating only the
-//    planes i0 with (a0 + i0) = w (mod 4), so no two warps touch the same
-//    element and the read-modify-writes need no atomics; the tile (block plus
-//    halo) is then added to the grid with vector global reductions;
+//  * scatter: W warps (default 2, measured best of 1/2/4/8) share one
+//    accumulator tile, warp w updating only the planes i0 with
+//    (a0 + i0) = w (mod W), so no two warps touch the same element and the
+//    read-modify-writes need no atomics; the tile (block plus halo) is then
+//    added to the grid with vector global reductions;
 //  * the node records of a work item are staged in shared memory with the tile.
+#include <stdlib.h>
+
 #include "nfft_internal.cuh"
 
 namespace nfftgb {
@@ -32,13 +35,16 @@ constexpr int kCoef = kDeg + 1;
 constexpr int kPitch = 18;          // shared row pitch (complex) along dim 2
 constexpr int kMaxTile2 = 9;        // L2 = T2 + 7 <= 16: two rows per warp step
 constexpr int kGatherWarps = 4;
-constexpr int kScatterWarps = 4;
 constexpr int kItemCap = 128;       // nodes per work item staged in shared memory
 
+// One staged node = 8 words {t0, t1, t2, a0 | a1 << 8 | a2 << 16, perm, re v, im v, 0}
+// (fractions, cell offsets in the tile, caller index, scatter input).  A warp
+// reads a node with one 32-bit load per lane (lane & 7 -> word) and hands the
+// words out with shuffles: one shared wavefront per node instead of one per
+// field and quarter-warp.
+constexpr int kRecWords = 8;
 struct NodeStage {
-  float4 rec[kItemCap];  // {t0, t1, t2, bits of a0 | a1 << 8 | a2 << 16}: fractions, cell offsets in the tile
-  int perm[kItemCap];
-  float2 v[kItemCap];    // scatter: the node's fhat value
+  float w[kItemCap][kRecWords];
 };
 
 // Packed pairs of FP32 (re, im) in one 64-bit register.
@@ -104,10 +110,11 @@ __device__ __forceinline__ void stage_nodes(const Geometry& g, const NodeArrays&
       pk |= (na.cell[d * M + q] - tc[d] * g.T[d]) << (8 * d);
       t[d] = frac[d * M + q];
     }
-    ns.rec[i] = make_float4(t[0], t[1], t[2], __int_as_float(pk));
     const int j = na.perm[q];
-    ns.perm[i] = j;
-    if (fhat) ns.v[i] = fhat[j];
+    const float2 v = fhat ? fhat[j] : make_float2(0.f, 0.f);
+    float4* dst = reinterpret_cast<float4*>(ns.w[i]);
+    dst[0] = make_float4(t[0], t[1], t[2], __int_as_float(pk));
+    dst[1] = make_float4(__int_as_float(j), v.x, v.y, 0.f);
   }
 }
 
@@ -117,28 +124,43 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Tile + halo rows: two rows of <= 16 elements per warp step, copied with
-// cp.async (the caller waits with cp_async_wait_all before its barrier).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Tile + halo into shared memory with cp.async (the caller waits with
+// cp_async_wait_all before its barrier).  Shared row r holds the 18 grid
+// points starting at start[2] - shift:
+//  * shift = 1 (T2 even): start[2] - 1 = tc2 T2 - 4 is even, so each row is 9
+//    aligned 16-byte chunks; N~ is even, so a chunk never straddles the
+//    periodic wrap and wraps as a whole.  Three rows per warp step.
+//  * shift = 0 (T2 odd): 8-byte copies of the L2 region points, two rows per
+//    warp step.
 __device__ __forceinline__ void load_tile(const Geometry& g, const int* start, const float2* grid,
-                                          float2* tile, int warp, int lane, int nwarps) {
-  const int L1 = g.L[1], L2 = g.L[2];
-  const int half = lane >> 4, e = lane & 15;
+                                          float2* tile, int warp, int lane, int nwarps, int shift) {
+  const int L1 = g.L[1];
   const int rows = g.L[0] * L1;
-  const int step = 2 * nwarps;  // rows advance by `step` (< L1 is not assumed)
-  const int g2 = wrap1(start[2] + e, g.Nt[2]);
-  int r = 2 * warp + half;
-  int r0 = r / L1, r1 = r - r0 * L1;
-  const int s0 = step / L1, s1 = step - s0 * L1;
-  if (e < L2) {
-    for (; r < rows; r += step) {
-      const int g0 = wrap1(start[0] + r0, g.Nt[0]);
-      const int g1 = wrap1(start[1] + r1, g.Nt[1]);
-      cp_async8(tile + (r0 * L1 + r1) * kPitch + e, grid + ((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + g2);
-      r0 += s0;
-      r1 += s1;
-      if (r1 >= L1) {
-        r1 -= L1;
-        ++r0;
+  if (shift) {
+    const int ro = lane / 9, q = lane - 9 * ro;
+    if (ro < 3) {
+      const int x = wrap1(start[2] - 1 + 2 * q, g.Nt[2]);
+      for (int r = 3 * warp + ro; r < rows; r += 3 * nwarps) {
+        const int r0 = r / L1, r1 = r - r0 * L1;
+        const int g0 = wrap1(start[0] + r0, g.Nt[0]);
+        const int g1 = wrap1(start[1] + r1, g.Nt[1]);
+        cp_async16(tile + (r0 * L1 + r1) * kPitch + 2 * q, grid + ((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + x);
+      }
+    }
+  } else {
+    const int half = lane >> 4, e = lane & 15;
+    if (e < g.L[2]) {
+      const int x = wrap1(start[2] + e, g.Nt[2]);
+      for (int r = 2 * warp + half; r < rows; r += 2 * nwarps) {
+        const int r0 = r / L1, r1 = r - r0 * L1;
+        const int g0 = wrap1(start[0] + r0, g.Nt[0]);
+        const int g1 = wrap1(start[1] + r1, g.Nt[1]);
+        cp_async8(tile + (r0 * L1 + r1) * kPitch + e, grid + ((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + x);
       }
     }
   }
@@ -162,6 +184,7 @@ __global__ void __launch_bounds__(32 * kGatherWarps)
   load_coef(poly, grp, i2, cA);
   load_coef(poly, 2, i2, cB);
   const int nitems = *na.n_items;
+  const int shift = (g.T[2] & 1) ? 0 : 1;
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 item = na.items[it];
@@ -171,17 +194,20 @@ __global__ void __launch_bounds__(32 * kGatherWarps)
     for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
 
     __syncthreads();
-    load_tile(g, start, grid, tile, warp, lane, kGatherWarps);
+    load_tile(g, start, grid, tile, warp, lane, kGatherWarps, shift);
     stage_nodes(g, na, item, tc, ns, nullptr, threadIdx.x, blockDim.x);
     cp_async_wait_all();
     __syncthreads();
 
     for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * kGatherWarps) {
       const int s = min(s0 + half, item.z - 1);  // a half without a node repeats the last one
-      const float4 rc = ns.rec[s];
-      const float wA = horner(cA, (grp == 0 ? rc.x : rc.y) - 0.5f);
-      const float wB = horner(cB, rc.z - 0.5f);
-      const int pk = __float_as_int(rc.w);
+      const float word = ns.w[s][lane & 7];
+      const float tA = __shfl_sync(0xffffffffu, word, hbase + grp);
+      const float tB = __shfl_sync(0xffffffffu, word, hbase + 2);
+      const int pk = __float_as_int(__shfl_sync(0xffffffffu, word, hbase + 3));
+      const int jout = __float_as_int(__shfl_sync(0xffffffffu, word, hbase + 4));
+      const float wA = horner(cA, tA - 0.5f);
+      const float wB = horner(cB, tB - 0.5f);
       const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
       f32x2 w12[4];
 #pragma unroll
@@ -189,7 +215,8 @@ __global__ void __launch_bounds__(32 * kGatherWarps)
         const float w = __shfl_sync(0xffffffffu, wA, hbase + 8 + j + 4 * grp) * wB;
         w12[j] = pack2(w, w);
       }
-      const f32x2* p = reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1 + 4 * grp) * kPitch + a2 + i2);
+      const f32x2* p =
+          reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1 + 4 * grp) * kPitch + a2 + i2 + shift);
       f32x2 acc = pack2(0.f, 0.f);
 #pragma unroll
       for (int i0 = 0; i0 < kTaps; ++i0) {
@@ -207,15 +234,19 @@ __global__ void __launch_bounds__(32 * kGatherWarps)
         r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
         r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
       }
-      if (lane16 == 0 && s0 + half < item.z) fhat[ns.perm[s]] = r;
+      if (lane16 == 0 && s0 + half < item.z) fhat[jout] = r;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kScatterWarps)
+// W warps share one accumulator tile; warp w updates only the planes
+// i0 = i0a + j W (j = 0 .. 8/W - 1) with (a0 + i0a) = w (mod W).
+template <int W>
+__global__ void __launch_bounds__(32 * W)
     scatter3d_m4_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na,
                         const float* __restrict__ poly, const float2* __restrict__ fhat) {
+  constexpr int kPlanes = kTaps / W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NodeStage& ns = *reinterpret_cast<NodeStage*>(smem_raw);
   float2* acc = reinterpret_cast<float2*>(smem_raw + sizeof(NodeStage));
@@ -247,25 +278,33 @@ __global__ void __launch_bounds__(32 * kScatterWarps)
     __syncthreads();
 
     for (int s = 0; s < item.z; ++s) {
-      const float4 rc = ns.rec[s];
-      const float w = horner(c, (dl == 0 ? rc.x : (dl == 1 ? rc.y : rc.z)) - 0.5f);
-      const int pk = __float_as_int(rc.w);
+      const float word = ns.w[s][lane & 7];
+      const float t = __shfl_sync(0xffffffffu, word, dl);
+      const int pk = __float_as_int(__shfl_sync(0xffffffffu, word, 3));
+      const float2 v = make_float2(__shfl_sync(0xffffffffu, word, 5), __shfl_sync(0xffffffffu, word, 6));
+      const float w = horner(c, t - 0.5f);
       const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
-      const int i0a = (warp - a0) & (kScatterWarps - 1);  // planes i0a, i0a + 4 are this warp's
+      const int i0a = (warp - a0) & (W - 1);  // this warp's planes: i0a + j W
       const float w2 = __shfl_sync(0xffffffffu, w, 16 + i2);
       const float wa = __shfl_sync(0xffffffffu, w, 8 + ra) * w2;
       const float wb = __shfl_sync(0xffffffffu, w, 8 + rb) * w2;
-      const float w0a = __shfl_sync(0xffffffffu, w, i0a);
-      const float w0b = __shfl_sync(0xffffffffu, w, i0a + 4);
-      const float2 v = ns.v[s];
-      const f32x2 vv = pack2(v.x, v.y);
+      const f32x2 va = mul2(pack2(v.x, v.y), pack2(wa, wa));
+      const f32x2 vb = mul2(pack2(v.x, v.y), pack2(wb, wb));
       f32x2* pa = reinterpret_cast<f32x2*>(acc + ((a0 + i0a) * L1 + a1 + ra) * kPitch + a2 + i2);
       f32x2* pb = pa + 2 * kPitch;
-      const f32x2 t0 = pa[0], t1 = pb[0], t2 = pa[4 * plane], t3 = pb[4 * plane];
-      pa[0] = fma2(vv, pack2(wa * w0a, wa * w0a), t0);
-      pb[0] = fma2(vv, pack2(wb * w0a, wb * w0a), t1);
-      pa[4 * plane] = fma2(vv, pack2(wa * w0b, wa * w0b), t2);
-      pb[4 * plane] = fma2(vv, pack2(wb * w0b, wb * w0b), t3);
+      f32x2 ta[kPlanes], tb[kPlanes];
+#pragma unroll
+      for (int j = 0; j < kPlanes; ++j) {
+        ta[j] = pa[j * W * plane];
+        tb[j] = pb[j * W * plane];
+      }
+#pragma unroll
+      for (int j = 0; j < kPlanes; ++j) {
+        const float w0 = __shfl_sync(0xffffffffu, w, i0a + j * W);
+        const f32x2 ww0 = pack2(w0, w0);
+        pa[j * W * plane] = fma2(va, ww0, ta[j]);
+        pb[j * W * plane] = fma2(vb, ww0, tb[j]);
+      }
       __syncwarp();
     }
     __syncthreads();
@@ -275,7 +314,7 @@ __global__ void __launch_bounds__(32 * kScatterWarps)
       const int half = lane >> 4, e = lane & 15;
       const int rows = L0 * L1;
       const int g2 = wrap1(start[2] + e, g.Nt[2]);
-      for (int r = 2 * warp + half; r < rows; r += 2 * kScatterWarps) {
+      for (int r = 2 * warp + half; r < rows; r += 2 * W) {
         const int r0 = r / L1, r1 = r - r0 * L1;
         if (e < L2) {
           const float2 val = acc[(r0 * L1 + r1) * kPitch + e];
@@ -285,6 +324,24 @@ __global__ void __launch_bounds__(32 * kScatterWarps)
         }
       }
     }
+  }
+}
+
+int scatter_warps() {
+  static int w = [] {
+    const char* e = getenv("NFFT_GB300_SCATTER_WARPS");
+    const int v = e ? atoi(e) : 2;
+    return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 4;
+  }();
+  return w;
+}
+
+void* scatter_kernel_for(int w) {
+  switch (w) {
+    case 1: return (void*)scatter3d_m4_kernel<1>;
+    case 2: return (void*)scatter3d_m4_kernel<2>;
+    case 8: return (void*)scatter3d_m4_kernel<8>;
+    default: return (void*)scatter3d_m4_kernel<4>;
   }
 }
 
@@ -311,8 +368,8 @@ bool fast3d_supported(const Geometry& g, int cmax) {
 
 int fast3d_ctas_per_sm(const Geometry& g, int kind) {
   const size_t smem = smem_bytes(g);
-  void* k = kind == 0 ? (void*)gather3d_m4_kernel : (void*)scatter3d_m4_kernel;
-  const int threads = kind == 0 ? 32 * kGatherWarps : 32 * kScatterWarps;
+  void* k = kind == 0 ? (void*)gather3d_m4_kernel : scatter_kernel_for(scatter_warps());
+  const int threads = kind == 0 ? 32 * kGatherWarps : 32 * scatter_warps();
   if (set_smem(k, smem) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
@@ -332,10 +389,12 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
                                   const float* poly, const void* fhat, int ctas, cudaStream_t s) {
   const size_t smem = smem_bytes(g);
-  cudaError_t e = set_smem(scatter3d_m4_kernel, smem);
+  const int w = scatter_warps();
+  void* k = scatter_kernel_for(w);
+  cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
-  scatter3d_m4_kernel<<<ctas, 32 * kScatterWarps, smem, s>>>(g, (float2*)grid, na, poly,
-                                                            (const float2*)fhat);
+  auto kern = reinterpret_cast<void (*)(Geometry, float2*, NodeArrays, const float*, const float2*)>(k);
+  kern<<<ctas, 32 * w, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
   return cudaGetLastError();
 }
 
