@@ -260,6 +260,25 @@ def algorithmic_bytes(wl, kernel):
     raise KeyError(kernel)
 
 
+def aggregate_replicas(local_ms_total, units_per_rank, steps):
+    """Whole-job numbers for independent replicas (one per rank): the slowest
+    rank's total time (max over ranks, as the timing rules ask) and the units
+    of all ranks over it.  Works with any initialised process group (NCCL on
+    GPUs, gloo in the CPU tests); world size 1 needs none."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    total = float(local_ms_total)
+    if world > 1:
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    ms_per_step = total / steps
+    return {"world": world, "ms_total_max": total, "ms_per_step": ms_per_step,
+            "value": world * units_per_rank / (ms_per_step * 1e-3)}
+
+
 def time_steps(step_fn, steps, warmup, stream, flush):
     """Mean ms of step_fn over `steps` event-timed runs (L2 flushed before each)."""
     import torch
@@ -436,13 +455,9 @@ def run_gpu(args):
         steps_ms.append(evs[0].elapsed_time(evs[6]))
         for j, n in enumerate(names):
             per[n].append(evs[j].elapsed_time(evs[j + 1]))
-    total_ms = sum(steps_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * wl["M"] / (ms_per_step * 1e-3)
+    agg = aggregate_replicas(sum(steps_ms), wl["M"], args.steps)
+    ms_per_step = agg["ms_per_step"]
+    value = agg["value"]
     mean = {n: statistics.mean(v) for n, v in per.items()}
     conv_ms = mean["deconv_pad"] + mean["gather"] + mean["scatter"] + mean["crop_deconv"]
 
