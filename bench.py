@@ -59,6 +59,8 @@ def parse():
                     help="nodes in the oracle's bounded sample")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip the complex128 (FP64) comparison run")
+    ap.add_argument("--no-full-form", action="store_true",
+                    help="skip the FULL sparse-matrix (cuSPARSE) comparison run")
     return ap.parse_args()
 
 
@@ -321,6 +323,43 @@ def fp64_form(wl, fhat32, steps, warmup, flush):
             "steps": steps}, ref, err
 
 
+def full_matrix_form(wl, steps, warmup, flush):
+    """The FULL-precomputation form (the paper's GPU prototype: the sparse
+    matrix B on the device, applied with cuSPARSE) on the same workload."""
+    import torch
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300.nfft import Plan
+    stream = torch.cuda.current_stream()
+    dt = torch.complex64 if wl["dtype"] == "c64" else torch.complex128
+    plan = Plan(wl["N"], wl["M"], sigma=wl["sigma"], m=wl["m"], dtype=dt, flags=B.NFFT_FLAG_FULL_MATRIX)
+    k = torch.from_numpy(wl["k"]).cuda()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plan.set_nodes(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    f = torch.from_numpy(wl["f"]).to(dt).cuda()
+    w = torch.from_numpy(wl["w"]).to(dt).cuda()
+    fh = torch.empty(wl["M"], dtype=dt, device="cuda")
+    y = torch.empty(wl["N"], dtype=dt, device="cuda")
+    h = plan.handle
+
+    def step():
+        B.check(B.nfft_step_deconv_pad(h, f.data_ptr()))
+        B.check(B.nfft_step_fft(h, -1))
+        B.check(B.nfft_step_gather(h, fh.data_ptr()))
+        B.check(B.nfft_step_scatter(h, w.data_ptr()))
+        B.check(B.nfft_step_fft(h, +1))
+        B.check(B.nfft_step_crop_deconv(h, y.data_ptr()))
+    ms = time_steps(step, steps, warmup, stream, flush)
+    plan.close()
+    nnz = wl["M"] * (2 * wl["m"]) ** len(wl["N"])
+    return {"value": wl["M"] / (ms * 1e-3), "unit": UNIT, "ms_per_step": round(ms, 3), "steps": steps,
+            "set_nodes_ms_incl_matrix_build": round(build_ms, 2), "nnz": nnz}
+
+
 def ndft_sample_error(wl, fhat, n=48, seed=11):
     """Relative L2 error of fhat against the exact FP64 NDFT (oracle) on n sampled nodes."""
     import numpy as np
@@ -516,6 +555,12 @@ def run_gpu(args):
     if rank == 0 and not args.no_fp64_form and dt == torch.complex64:
         fp64, ref64, err = fp64_form(wl, fhat32, min(10, max(3, args.steps // 4)), 2, flush)
         accuracy["rel_l2_fp32_vs_fp64_form"] = err
+    full = None
+    if rank == 0 and not args.no_full_form:
+        try:
+            full = full_matrix_form(wl, min(10, max(3, args.steps // 4)), 2, flush)
+        except Exception as exc:  # e.g. too many nonzeros for 32-bit CSR indices
+            full = {"unavailable": str(exc)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -540,6 +585,7 @@ def run_gpu(args):
             "kernels": kernel_table,
             "roofline": roofline,
             "fp64_form": fp64,
+            "full_matrix_form": full,
             "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -62,6 +62,13 @@ extern "C" {
 /* FP32 scatter: each shared-memory tile sum also accumulates the rounding
    error of every addition (TwoSum) and adds it back at the flush. */
 #define NFFT_FLAG_COMPENSATED     0x2u
+/* FULL precomputation (Sec. 3.7.4 item 2; the paper's GPU prototype of
+   Sec. 6): nfft_set_nodes also builds the sparse matrix B of Eq. Bmatrix
+   ((2m)^D values and column indices per node) and its transpose, and the
+   resampling steps apply them with cuSPARSE SpMM instead of the tiled
+   kernels.  A comparison form: it stores and moves far more than the grid.
+   NFFT_ERR_UNSUPPORTED when M (2m)^D >= 2^31 or D = 3 with m > 6. */
+#define NFFT_FLAG_FULL_MATRIX     0x4u
 
 typedef struct nfft_plan nfft_plan;
 

@@ -81,7 +81,7 @@ def build(verbose=False, jobs=None):
     libdir = _cuda_lib_dir(nvcc)
     tmp = LIB + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + [
-        "-L" + libdir, "-lcufft", "-Xlinker", "-rpath," + libdir]
+        "-L" + libdir, "-lcufft", "-lcusparse", "-Xlinker", "-rpath," + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

@@ -129,6 +129,13 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
                                   const float* poly, const void* fhat, int ctas, cudaStream_t s);
 
+// FULL precomputation: B as a CSR matrix, applied with cuSPARSE (nfft_full.cu)
+struct FullMatrix;
+int full_build(FullMatrix** out, const Geometry& g, int dtype, const NodeArrays& na, cudaStream_t s);
+int full_forward(FullMatrix* F, const void* grid, void* fhat, cudaStream_t s);
+int full_adjoint(FullMatrix* F, const void* fhat, void* grid, cudaStream_t s);
+void full_destroy(FullMatrix* F);
+
 // deconvolution, tables, sorting (nfft_kernels.cu)
 struct DeconvArgs {
   int D;

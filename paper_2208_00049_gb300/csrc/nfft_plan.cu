@@ -42,6 +42,7 @@ struct nfft_plan {
   int64_t max_items = 0;
   int ctas[4] = {0, 0, 0, 0};  // persistent grid per kernel kind
   bool fast3d = false;         // 3D m = 4 complex64 warp-per-node kernels
+  FullMatrix* full = nullptr;  // NFFT_FLAG_FULL_MATRIX: B and B^T as CSR
   int fast_ctas[2] = {0, 0};
 
   void* grid = nullptr;
@@ -354,6 +355,7 @@ int run_fft(nfft_plan* p, int sign) {
 int run_gather(nfft_plan* p, void* fhat) {
   Geometry g = make_geometry(p);
   NodeArrays na = node_arrays(p);
+  if (p->full) return latch(p, full_forward(p->full, p->grid, fhat, p->stream));
   cudaError_t e = p->fast3d ? launch_gather3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[0], p->stream)
                   : p->dtype == NFFT_C128
                       ? launch_gather<double>(g, p->grid, na, fhat, p->ctas[0], p->stream)
@@ -362,6 +364,7 @@ int run_gather(nfft_plan* p, void* fhat) {
 }
 
 int run_scatter(nfft_plan* p, const void* fhat) {
+  if (p->full) return latch(p, full_adjoint(p->full, fhat, p->grid, p->stream));
   NFFT_CK(p, cudaMemsetAsync(p->grid, 0, (size_t)prod_Nt(p) * cplx_size(p), p->stream));
   Geometry g = make_geometry(p);
   NodeArrays na = node_arrays(p);
@@ -415,6 +418,7 @@ int nfft_plan_destroy(nfft_plan* p) {
   DeviceGuard guard(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->fft_ok) cufftDestroy(p->fft);
+  full_destroy(p->full);
   void* bufs[] = {p->grid, p->beta64, p->beta32, p->poly, p->cell, p->frac, p->perm, p->key, p->rank,
                   p->tile_count, p->tile_offset, p->items, p->n_items,
                   p->stage[0], p->stage[1], p->stage[2]};
@@ -431,7 +435,7 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
   if (!(sigma > 1.0) || m < 1 || m > kMaxM) return NFFT_ERR_INVALID_ARG;
   if (dtype != NFFT_C64 && dtype != NFFT_C128) return NFFT_ERR_INVALID_ARG;
   if (M < 0 || M >= ((int64_t)1 << 31)) return NFFT_ERR_INVALID_ARG;
-  if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_COMPENSATED))
+  if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_COMPENSATED | NFFT_FLAG_FULL_MATRIX))
     return NFFT_ERR_INVALID_ARG;
   int64_t total = 1;
   for (int d = 0; d < D; ++d) {
@@ -548,6 +552,10 @@ int nfft_set_nodes(nfft_plan* p, const void* k, int k_is_fp64) {
   NFFT_CK(p, launch_tile_scan(a, p->tile_count, p->tile_offset, p->items, p->n_items, p->stream));
   NFFT_CK(p, launch_node_place(a, kd, k_is_fp64 ? 1 : 0, p->key, p->rank, p->tile_offset, p->cell,
                                p->frac, p->dtype == NFFT_C128 ? 1 : 0, p->perm, p->stream));
+  if (p->flags & NFFT_FLAG_FULL_MATRIX) {
+    s = full_build(&p->full, make_geometry(p), p->dtype, node_arrays(p), p->stream);
+    if (s != NFFT_OK) return latch(p, s);
+  }
   if (kd != k) NFFT_CK(p, cudaStreamSynchronize(p->stream));  // stage buffer reuse safety
   p->has_nodes = true;
   return NFFT_OK;

@@ -307,3 +307,16 @@ def test_autotuned_plan_matches_oracle(N, M, dt):
     plan.close()
     assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), TOL[dt], "forward")
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), TOL[dt], "adjoint")
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("N,M,m", [((300,), 700, 4), ((40, 36), 2500, 4), ((20, 18, 16), 3000, 4),
+                                   ((12, 10, 14), 1500, 3), ((64, 48), 3000, 8)])
+def test_full_matrix_form_matches_oracle(N, M, m, dt):
+    """NFFT_FLAG_FULL_MATRIX (B and B^T as CSR applied with cuSPARSE)."""
+    from paper_2208_00049_gb300 import binding as B
+    case = inputs.small_case(N, M, seed=67, m=m)
+    fh, y = _run(case, dt, flags=B.NFFT_FLAG_FULL_MATRIX)
+    tol = TOL[dt] * (10 if dt == "c128" and m <= 3 else 1)
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, m), tol, "forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, m), tol, "adjoint")
