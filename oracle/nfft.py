@@ -25,7 +25,9 @@ dimension; Sec. 3.7.5).  The printed closed form omega is read as this set
 (it is off by N~/2 as printed); the tests also check this enumeration against
 the set definition by brute force.  With ``closed=True`` the support is
 [-m, m] and the footprint has 2m + 1 points l' = floor(N~k) - m + i,
-i = 0, ..., 2m (the (2m+1)^D variant).
+i = 0, ..., 2m (the (2m+1)^D variant).  With ``wide=True`` the footprint has
+2m + 2 points l' = floor(N~k) - m + i, i = 0, ..., 2m + 1, weighted with the
+untruncated window (the NFFT3 variant of Sec. 3.7.5).
 
 N~ k is formed in FP64 and its floor taken in FP64.
 """
@@ -33,19 +35,22 @@ import itertools
 
 import numpy as np
 
-from .window import (deconv_factor, dpsi, index_set, kb_shape,
-                     oversampled_size, psi)
+from .window import (deconv_factor, dpsi, dpsi_full, index_set, kb_shape,
+                     oversampled_size, psi, psi_full)
 
 
 class Params:
     """Sizes and window shape of one transform (plan-time quantities)."""
 
-    def __init__(self, N, sigma=2.0, m=4, closed=False):
+    def __init__(self, N, sigma=2.0, m=4, closed=False, wide=False):
         self.N = tuple(int(v) for v in N)
         self.D = len(self.N)
         self.sigma = float(sigma)
         self.m = int(m)
         self.closed = bool(closed)
+        self.wide = bool(wide)
+        if self.closed and self.wide:
+            raise ValueError("closed and wide are exclusive")
         self.Nt = tuple(oversampled_size(n, sigma) for n in self.N)
         self.b = tuple(kb_shape(n, nt) for n, nt in zip(self.N, self.Nt))
         for n, nt in zip(self.N, self.Nt):
@@ -53,7 +58,15 @@ class Params:
                 raise ValueError("need 2m < N~")
 
     def taps(self):
+        if self.wide:
+            return 2 * self.m + 2
         return 2 * self.m + 1 if self.closed else 2 * self.m
+
+    def window(self, u, b):
+        return psi_full(u, self.m, b) if self.wide else psi(u, self.m, b, self.closed)
+
+    def dwindow(self, u, b):
+        return dpsi_full(u, self.m, b) if self.wide else dpsi(u, self.m, b, self.closed)
 
 
 def _correction(p):
@@ -94,7 +107,7 @@ def footprint(p, k):
     u = N~ k - l' (M, taps), with N~ k and its floor in FP64."""
     k = np.asarray(k, dtype=np.float64)
     ls, us = [], []
-    first = -p.m if p.closed else -p.m + 1
+    first = -p.m if (p.closed or p.wide) else -p.m + 1
     offs = np.arange(p.taps()) + first
     for d in range(p.D):
         x = p.Nt[d] * k[:, d]
@@ -108,7 +121,7 @@ def footprint(p, k):
 def resample(p, k, ghat):
     """Alg. 1 lines 7-9 (Eq. SumOverNode): fhat_j = sum_l ghat_l psi~(k_j - l/N~)."""
     ls, us = footprint(p, k)
-    w = [psi(u, p.m, b, p.closed) for u, b in zip(us, p.b)]
+    w = [p.window(u, b) for u, b in zip(us, p.b)]
     M = ls[0].shape[0]
     out = np.zeros(M, dtype=np.complex128)
     for tap in itertools.product(range(p.taps()), repeat=p.D):
@@ -125,7 +138,7 @@ def resample_adjoint(p, k, fhat):
     Sec. 2.2.2 describes: every node adds fhat_j psi~ into its footprint."""
     fhat = np.asarray(fhat, dtype=np.complex128).ravel()
     ls, us = footprint(p, k)
-    w = [psi(u, p.m, b, p.closed) for u, b in zip(us, p.b)]
+    w = [p.window(u, b) for u, b in zip(us, p.b)]
     M = fhat.shape[0]
     acc = np.zeros(int(np.prod(p.Nt)), dtype=np.complex128)
     for tap in itertools.product(range(p.taps()), repeat=p.D):
@@ -148,18 +161,18 @@ def fft_adjoint(ghat):
     return np.fft.ifftn(ghat, norm="forward")
 
 
-def forward(k, f, sigma=2.0, m=4, closed=False):
+def forward(k, f, sigma=2.0, m=4, closed=False, wide=False):
     """Direct NFFT, Algorithm 1: fhat ~= A f."""
     f = np.asarray(f, dtype=np.complex128)
-    p = Params(f.shape, sigma, m, closed)
+    p = Params(f.shape, sigma, m, closed, wide)
     g = correction_pad(p, f)
     ghat = fft_forward(g)
     return resample(p, k, ghat)
 
 
-def adjoint(k, fhat, N, sigma=2.0, m=4, closed=False):
+def adjoint(k, fhat, N, sigma=2.0, m=4, closed=False, wide=False):
     """Adjoint NFFT, Algorithm 2: y ~= A^H fhat."""
-    p = Params(N, sigma, m, closed)
+    p = Params(N, sigma, m, closed, wide)
     ghat = resample_adjoint(p, k, fhat)
     g = fft_adjoint(ghat)
     return crop_correction(p, g)
@@ -173,8 +186,8 @@ def resample_node_derivative(p, k, ghat):
     Returns a complex (M, D) array.
     """
     ls, us = footprint(p, k)
-    w = [psi(u, p.m, b, p.closed) for u, b in zip(us, p.b)]
-    dw = [dpsi(u, p.m, b, p.closed) for u, b in zip(us, p.b)]
+    w = [p.window(u, b) for u, b in zip(us, p.b)]
+    dw = [p.dwindow(u, b) for u, b in zip(us, p.b)]
     M = ls[0].shape[0]
     out = np.zeros((M, p.D), dtype=np.complex128)
     for tap in itertools.product(range(p.taps()), repeat=p.D):
@@ -189,12 +202,12 @@ def resample_node_derivative(p, k, ghat):
     return out
 
 
-def node_grad(k, f, cot, sigma=2.0, m=4, closed=False):
+def node_grad(k, f, cot, sigma=2.0, m=4, closed=False, wide=False):
     """Node gradient of a real loss through the NFFT fhat = A f:
     g[j, d] = Re(conj(cot_j) d fhat_j / d k_{j,d}) (PyTorch's convention for a
     real loss of complex outputs)."""
     f = np.asarray(f, dtype=np.complex128)
-    p = Params(f.shape, sigma, m, closed)
+    p = Params(f.shape, sigma, m, closed, wide)
     ghat = fft_forward(correction_pad(p, f))
     dk = resample_node_derivative(p, k, ghat)
     return np.real(np.conj(np.asarray(cot, dtype=np.complex128))[:, None] * dk)

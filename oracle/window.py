@@ -62,6 +62,52 @@ def psi(u, m, b, closed=False):
     return np.where(inside, val, 0.0)
 
 
+def psi_full(u, m, b):
+    """The untruncated window in grid units (the phi-hat of Sec. 2.2 before
+    Eq. approxTrunc): sinh(b s)/(pi s) with s = sqrt(m^2 - u^2) for |u| < m,
+    b/pi at |u| = m, and sin(b s')/(pi s') with s' = sqrt(u^2 - m^2) beyond
+    (the same analytic function continued past the support).  Used by the
+    (2m+2)-point variant that Sec. 3.7.5 attributes to NFFT3."""
+    u = np.asarray(u, dtype=np.float64)
+    d = m * m - u * u
+    s_in = np.sqrt(np.maximum(d, 0.0))
+    s_out = np.sqrt(np.maximum(-d, 0.0))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        inner = np.sinh(b * s_in) / (np.pi * s_in)
+        outer = np.sin(b * s_out) / (np.pi * s_out)
+    val = np.where(d > 0, inner, outer)
+    return np.where(d == 0.0, b / np.pi, val)
+
+
+def dpsi_full(u, m, b):
+    """d psi_full / du.  Inside: -u (z cosh z - sinh z)/(pi s^3) b^0 with
+    z = b s; outside: u (z cos z - sin z)/(pi s'^3), z = b s'.  For small z
+    both use the series b^3 h(z) with h = 1/3 + z^2/30 + ... inside and
+    -1/3 + z^2/30 - ... outside (12 terms)."""
+    u = np.asarray(u, dtype=np.float64)
+    d = m * m - u * u
+    inside = d >= 0
+    s = np.sqrt(np.abs(d))
+    z = b * s
+    small = z < 0.5
+    zs = np.where(small, z, 0.0)
+    ser_in = np.zeros_like(zs)
+    ser_out = np.zeros_like(zs)
+    fact = 6.0
+    for k in range(1, 13):
+        if k > 1:
+            fact *= (2 * k) * (2 * k + 1)
+        term = (2.0 * k) / fact * zs ** (2 * k - 2)
+        ser_in += term
+        ser_out += term * (-1.0) ** k      # (z cos z - sin z)/z^3 = sum (-1)^k 2k z^(2k-2)/(2k+1)!
+    zb = np.where(small, 1.0, z)
+    dir_in = (zb * np.cosh(zb) - np.sinh(zb)) / zb ** 3
+    dir_out = (zb * np.cos(zb) - np.sin(zb)) / zb ** 3
+    h_in = np.where(small, ser_in, dir_in)
+    h_out = np.where(small, ser_out, dir_out)
+    return np.where(inside, -u * b ** 3 * h_in / np.pi, u * b ** 3 * h_out / np.pi)
+
+
 def dpsi(u, m, b, closed=False):
     """Derivative d psi / d u inside the support (0 outside).
 

@@ -232,3 +232,48 @@ def test_fp32_rounding_bound(N, sigma, m):
     assert g32.dtype == np.complex64
     err = np.linalg.norm(nfft.resample(p, k, g32.astype(np.complex128)) - ref) / np.linalg.norm(ref)
     assert err <= tol_for(N, sigma, m, "c64") / 4
+
+
+def test_wide_footprint_against_paper_claims():
+    """Sec. 5.1 / Sec. 6: NFFT3's (2m+2)-point footprint with the untruncated
+    window is more accurate than 2m points at the same m, but increasing m by
+    one (2(m+1) points) gains much more."""
+    rng = np.random.default_rng(22)
+    N = (24, 20)
+    M = 300
+    k = rng.random((M, 2)) - 0.5
+    f = _cn(rng, N)
+    ex = ndft.ndft(k, f)
+    err = lambda fh: np.linalg.norm(fh - ex) / np.linalg.norm(ex)
+    for m in (2, 3, 4, 5):
+        e2m = err(nfft.forward(k, f, 2.0, m))
+        ewide = err(nfft.forward(k, f, 2.0, m, wide=True))
+        enext = err(nfft.forward(k, f, 2.0, m + 1))
+        assert ewide < e2m
+        assert enext < ewide
+
+
+def test_wide_footprint_invariants():
+    rng = np.random.default_rng(23)
+    N = (16, 12)
+    k = rng.random((80, 2)) - 0.5
+    f = _cn(rng, N)
+    w = _cn(rng, 80)
+    lhs = np.vdot(w, nfft.forward(k, f, 2.0, 3, wide=True))
+    rhs = np.vdot(nfft.adjoint(k, w, N, 2.0, 3, wide=True), f)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(f) * np.linalg.norm(w)
+    p = nfft.Params(N, 2.0, 3, wide=True)
+    e = np.array([0.0, 1.0 / p.Nt[1]])
+    ph = np.exp(-2j * np.pi * window.index_set(N[1]).reshape(1, -1) / p.Nt[1])
+    a = nfft.forward(k + e, f, 2.0, 3, wide=True)
+    b = nfft.forward(k, f * ph, 2.0, 3, wide=True)
+    assert np.allclose(a, b, rtol=0, atol=1e-12 * np.abs(b).max())
+    # node derivative of the wide form by finite differences
+    ghat = nfft.fft_forward(nfft.correction_pad(p, f))
+    dk = nfft.resample_node_derivative(p, k, ghat)
+    h = 1e-7
+    for d in range(2):
+        ee = np.zeros(2)
+        ee[d] = h
+        fd = (nfft.resample(p, k + ee, ghat) - nfft.resample(p, k - ee, ghat)) / (2 * h)
+        assert np.allclose(dk[:, d], fd, rtol=0, atol=2e-6 * np.abs(fd).max())

@@ -130,3 +130,26 @@ def test_deconv_factor_is_reciprocal_of_scaled_phi():
     n = np.arange(-32, 32)
     expect = np.array([1.0 / _i0_series(m * math.sqrt(b * b - (2 * math.pi * v / Nt) ** 2)) for v in n])
     assert np.allclose(window.deconv_factor(n, Nt, m, b), expect, rtol=1e-13)
+
+
+def test_untruncated_window_continuation():
+    """psi_full equals psi inside the support, is continuous through |u| = m
+    (both branches tend to b/pi) and is the sin form beyond."""
+    m, b = 4, window.kb_shape(64, 128)
+    u = np.linspace(-3.9, 3.9, 41)
+    assert np.allclose(window.psi_full(u, m, b), window.psi(u, m, b), rtol=1e-15)
+    for eps in (1e-8, 1e-10):   # deviation ~ b^2 2m eps / 6
+        assert window.psi_full(m - eps, m, b) == pytest.approx(b / np.pi, rel=1e-6)
+        assert window.psi_full(m + eps, m, b) == pytest.approx(b / np.pi, rel=1e-6)
+    x = 4.6
+    sp = math.sqrt(x * x - m * m)
+    assert window.psi_full(x, m, b) == pytest.approx(math.sin(b * sp) / (math.pi * sp), rel=1e-14)
+
+
+def test_dpsi_full_by_finite_differences():
+    m, b = 3, window.kb_shape(50, 100)
+    h = 1e-6
+    u = np.concatenate([np.linspace(-m - 0.95, m + 0.95, 53), [m + 1e-3, -m - 1e-3, m - 1e-3]])
+    fd = (window.psi_full(u + h, m, b) - window.psi_full(u - h, m, b)) / (2 * h)
+    an = window.dpsi_full(u, m, b)
+    assert np.max(np.abs(fd - an)) < 1e-6 * np.max(np.abs(window.psi_full(np.linspace(-m, m, 9), m, b)))
