@@ -37,6 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
 WORKLOADS = {
+    "accuracy": "accuracy",
     "batched": "batched",
     "3d": "3d",
     "3d_lean": "3d_lean",
@@ -220,7 +221,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2208_00049_gb300 import inputs
-    wl = inputs.workload(WORKLOADS[args.workload] if args.workload != "batched" else "3d")
+    wl = inputs.workload(WORKLOADS[args.workload] if args.workload not in ("batched", "accuracy") else "3d")
     vals = []
     det = None
     for _ in range(max(1, args.warmup)):
@@ -414,6 +415,48 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+def run_accuracy(args):
+    """Figs. 1-2 analogue on the GPU: relative errors (L2 and the paper's
+    infinity norm) of the direct and adjoint NFFT against the exact NDFT for
+    m = 2..8, 2D N = 128^2 with M = |I_N| random nodes, sigma = 2, complex64
+    and complex128, 2m points and the (2m+2)-point variant."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import ndft as ondft
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300 import inputs
+    from paper_2208_00049_gb300.nfft import Plan
+    N = (128, 128)
+    case = inputs.small_case(N, 128 * 128, seed=2208)
+    sel = np.random.default_rng(1).choice(case["M"], 1024, replace=False)
+    ex = ondft.ndft(case["k"][sel], case["f"])
+    nsel = np.random.default_rng(2).choice(int(np.prod(N)), 1024, replace=False)
+    idx = np.unravel_index(nsel, N)
+    n = np.stack([idx[d] - N[d] // 2 for d in range(2)], axis=1).astype(float)
+    ph = n @ case["k"].T
+    ph -= np.floor(ph)
+    exa = np.exp(2j * np.pi * ph) @ case["w"]
+    rows = []
+    for dt, name in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+        for wide in (False, True):
+            for m in range(2, 9):
+                flags = B.NFFT_FLAG_WIDE_WINDOW if wide else 0
+                plan = Plan(N, case["M"], sigma=2.0, m=m, dtype=dt, flags=flags)
+                plan.set_nodes(torch.from_numpy(case["k"]).cuda())
+                fh = plan.forward(torch.from_numpy(case["f"]).to(dt).cuda()).cpu().numpy()[sel]
+                y = plan.adjoint(torch.from_numpy(case["w"]).to(dt).cuda()).cpu().numpy()[idx]
+                plan.close()
+                rows.append({"dtype": name, "taps": "2m+2" if wide else "2m", "m": m,
+                             "fwd_l2": float(np.linalg.norm(fh - ex) / np.linalg.norm(ex)),
+                             "fwd_inf": float(np.max(np.abs(fh - ex)) / np.max(np.abs(ex))),
+                             "adj_l2": float(np.linalg.norm(y - exa) / np.linalg.norm(exa)),
+                             "adj_inf": float(np.max(np.abs(y - exa)) / np.max(np.abs(exa)))})
+    print(json.dumps({"metric": "NFFT relative error vs exact NDFT (1024 sampled outputs each way)",
+                      "config": {"workload": "2D N=128^2 M=16384 sigma=2 uniform nodes"}, "rows": rows}))
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -604,6 +647,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "accuracy":
+        run_accuracy(args)
     else:
         run_gpu(args)
 

@@ -69,6 +69,11 @@ extern "C" {
    kernels.  A comparison form: it stores and moves far more than the grid.
    NFFT_ERR_UNSUPPORTED when M (2m)^D >= 2^31 or D = 3 with m > 6. */
 #define NFFT_FLAG_FULL_MATRIX     0x4u
+/* (2m+2)^D footprint with the untruncated window (continued past |u| = m
+   by its sin form): the NFFT3 variant discussed in Sec. 3.7.5, slightly more
+   accurate than 2m points at the same m (Sec. 5.1).  Exclusive with
+   NFFT_FLAG_CLOSED_SUPPORT. */
+#define NFFT_FLAG_WIDE_WINDOW     0x8u
 
 typedef struct nfft_plan nfft_plan;
 

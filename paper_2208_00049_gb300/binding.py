@@ -26,6 +26,7 @@ NFFT_C128 = 1
 NFFT_FLAG_CLOSED_SUPPORT = 0x1
 NFFT_FLAG_COMPENSATED = 0x2
 NFFT_FLAG_FULL_MATRIX = 0x4
+NFFT_FLAG_WIDE_WINDOW = 0x8
 
 _p = ctypes.c_void_p
 _i = ctypes.c_int

@@ -439,7 +439,8 @@ int nfft_batch_create(nfft_batch** out, int D, int B, const int64_t* N, const in
   if (D < 1 || D > kMaxD || B < 1 || S < 1 || S > B || !N || !set_of || !M_set) return NFFT_ERR_INVALID_ARG;
   if (!(sigma > 1.0) || m < 1 || m > kMaxM) return NFFT_ERR_INVALID_ARG;
   if (dtype != NFFT_C64 && dtype != NFFT_C128) return NFFT_ERR_INVALID_ARG;
-  if (flags & ~(uint32_t)NFFT_FLAG_CLOSED_SUPPORT) return NFFT_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW)) return NFFT_ERR_INVALID_ARG;
+  if ((flags & NFFT_FLAG_CLOSED_SUPPORT) && (flags & NFFT_FLAG_WIDE_WINDOW)) return NFFT_ERR_INVALID_ARG;
   nfft_batch* b = new (std::nothrow) nfft_batch();
   if (!b) return NFFT_ERR_OOM;
   b->D = D;
@@ -451,8 +452,9 @@ int nfft_batch_create(nfft_batch** out, int D, int B, const int64_t* N, const in
   b->flags = flags;
   b->stream = (cudaStream_t)stream;
   const bool closed = (flags & NFFT_FLAG_CLOSED_SUPPORT) != 0;
-  b->K = closed ? 2 * m + 2 : 2 * m;
-  b->off = closed ? -m : -m + 1;
+  const bool wide = (flags & NFFT_FLAG_WIDE_WINDOW) != 0;
+  b->K = (closed || wide) ? 2 * m + 2 : 2 * m;
+  b->off = (closed || wide) ? -m : -m + 1;
   b->N.assign(N, N + (size_t)B * D);
   b->Nt.resize((size_t)B * D);
   b->set_of.assign(set_of, set_of + B);

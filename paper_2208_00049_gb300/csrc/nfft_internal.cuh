@@ -40,35 +40,49 @@ struct Geometry {
 };
 
 // Kaiser-Bessel window in grid units, scaled to 1 at u = 0:
-//   w(u) = [sinh(b s)/s] * m/sinh(b m),  s = sqrt(m^2 - u^2).
-// s^2 is formed as (m - u)(m + u) from the integer and fractional parts of
-// u so that it stays accurate near the support edges.  At s = 0 the value
-// is the limit b * m/sinh(b m).
+//   w(u) = [sinh(b s)/s] * m/sinh(b m),  s = sqrt(m^2 - u^2)     (|u| <= m)
+//   w(u) = [sin(b s')/s'] * m/sinh(b m), s' = sqrt(u^2 - m^2)    (|u| > m)
+// (the second line is the untruncated window past the support, used by the
+// (2m+2)-point footprint).  s^2 is formed as (m - u)(m + u) from the integer
+// and fractional parts of u so that it stays accurate near the support
+// edges.  At s = 0 both forms tend to b * m/sinh(b m).
 template <typename R>
 __device__ __forceinline__ R kb_window(R mm_u, R mp_u, R b, R norm) {
-  R s2 = mm_u * mp_u;
-  R s = sqrt(s2 > R(0) ? s2 : R(0));
-  R z = b * s;
-  R r = (z < R(1e-3)) ? b * (R(1) + z * z * R(1.0 / 6.0)) : sinh(z) / s;
+  const R s2 = mm_u * mp_u;
+  const R s = sqrt(s2 > R(0) ? s2 : -s2);
+  const R z = b * s;
+  R r;
+  if (s2 >= R(0))
+    r = (z < R(1e-3)) ? b * (R(1) + z * z * R(1.0 / 6.0)) : sinh(z) / s;
+  else
+    r = (z < R(1e-3)) ? b * (R(1) - z * z * R(1.0 / 6.0)) : sin(z) / s;
   return r * norm;
 }
 
 // Derivative of the scaled window with respect to u:
-//   w'(u) = -u (b s cosh(b s) - sinh(b s)) / s^3 * m/sinh(b m)
-// with the series b^3 (1/3 + z^2/30 + z^4/840 + z^6/45360) for small z = b s.
+//   |u| <= m: w'(u) = -u (b s cosh(b s) - sinh(b s)) / s^3 * m/sinh(b m)
+//   |u| > m:  w'(u) = +u (b s' cos(b s') - sin(b s')) / s'^3 * m/sinh(b m)
+// with the series b^3 (1/3 + z^2/30 + z^4/840 + z^6/45360) inside and
+// b^3 (-1/3 + z^2/30 - z^4/840 + z^6/45360) outside for small z = b s.
 template <typename R>
 __device__ __forceinline__ R kb_window_deriv(R u, R mm_u, R mp_u, R b, R norm, R zsmall) {
-  R s2 = mm_u * mp_u;
-  R s = sqrt(s2 > R(0) ? s2 : R(0));
-  R z = b * s;
+  const R s2 = mm_u * mp_u;
+  const R s = sqrt(s2 > R(0) ? s2 : -s2);
+  const R z = b * s;
+  const R z2 = z * z;
   R h;
-  if (z < zsmall) {
-    R z2 = z * z;
-    h = b * b * b * (R(1.0 / 3.0) + z2 * (R(1.0 / 30.0) + z2 * (R(1.0 / 840.0) + z2 * R(1.0 / 45360.0))));
-  } else {
-    h = (z * cosh(z) - sinh(z)) / (s * s * s);
+  if (s2 >= R(0)) {
+    if (z < zsmall)
+      h = b * b * b * (R(1.0 / 3.0) + z2 * (R(1.0 / 30.0) + z2 * (R(1.0 / 840.0) + z2 * R(1.0 / 45360.0))));
+    else
+      h = (z * cosh(z) - sinh(z)) / (s * s * s);
+    return -u * h * norm;
   }
-  return -u * h * norm;
+  if (z < zsmall)
+    h = b * b * b * (R(-1.0 / 3.0) + z2 * (R(1.0 / 30.0) + z2 * (R(-1.0 / 840.0) + z2 * R(1.0 / 45360.0))));
+  else
+    h = (z * cos(z) - sin(z)) / (s * s * s);
+  return u * h * norm;
 }
 
 // ---- launchers (one per translation unit) ------------------------------

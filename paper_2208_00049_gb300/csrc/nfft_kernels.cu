@@ -109,8 +109,8 @@ __global__ void build_poly_kernel(PolyArgs a, float* coef) {
     const double zeta = 0.5 * cos(M_PI * (j + 0.5) / Z);
     const double u = center + zeta;
     const double s2 = (m - u) * (m + u);
-    const double s = sqrt(s2 > 0.0 ? s2 : 0.0);
-    const double val = (s == 0.0) ? b * norm : sinh(b * s) / s * norm;
+    const double s = sqrt(s2 > 0.0 ? s2 : -s2);
+    const double val = (s == 0.0) ? b * norm : (s2 > 0.0 ? sinh(b * s) : sin(b * s)) / s * norm;
     double p = 1.0;
     for (int z = 0; z < Z; ++z) {
       V[j][z] = p;

@@ -435,8 +435,10 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
   if (!(sigma > 1.0) || m < 1 || m > kMaxM) return NFFT_ERR_INVALID_ARG;
   if (dtype != NFFT_C64 && dtype != NFFT_C128) return NFFT_ERR_INVALID_ARG;
   if (M < 0 || M >= ((int64_t)1 << 31)) return NFFT_ERR_INVALID_ARG;
-  if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_COMPENSATED | NFFT_FLAG_FULL_MATRIX))
+  if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_COMPENSATED | NFFT_FLAG_FULL_MATRIX |
+                          NFFT_FLAG_WIDE_WINDOW))
     return NFFT_ERR_INVALID_ARG;
+  if ((flags & NFFT_FLAG_CLOSED_SUPPORT) && (flags & NFFT_FLAG_WIDE_WINDOW)) return NFFT_ERR_INVALID_ARG;
   int64_t total = 1;
   for (int d = 0; d < D; ++d) {
     if (N[d] < 2 || N[d] > ((int64_t)1 << 28)) return NFFT_ERR_INVALID_ARG;
@@ -456,8 +458,9 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
   p->flags = flags;
   p->stream = (cudaStream_t)stream;
   const bool closed = (flags & NFFT_FLAG_CLOSED_SUPPORT) != 0;
-  p->K = closed ? 2 * m + 2 : 2 * m;
-  p->off = closed ? -m : -m + 1;
+  const bool wide = (flags & NFFT_FLAG_WIDE_WINDOW) != 0;
+  p->K = (closed || wide) ? 2 * m + 2 : 2 * m;
+  p->off = (closed || wide) ? -m : -m + 1;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     cudaGetLastError();
     delete p;
@@ -508,7 +511,7 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
     }
     s = cuda_status(p, launch_build_beta(D, Ni, Nti, m, p->b, p->beta64, p->beta32, p->stream));
   }
-  if (s == NFFT_OK && !closed) {
+  if (s == NFFT_OK && !closed && !wide) {
     PolyArgs pa{};
     pa.D = D;
     pa.K = p->K;

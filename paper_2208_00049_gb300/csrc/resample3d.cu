@@ -359,7 +359,7 @@ cudaError_t set_smem(K kern, size_t smem) {
 }  // namespace
 
 bool fast3d_supported(const Geometry& g, int cmax) {
-  if (g.D != 3 || g.K != kTaps || g.closed || g.off != -3) return false;
+  if (g.D != 3 || g.K != kTaps || g.closed || g.off != -3 || g.m != 4.0) return false;
   if (g.T[2] > kMaxTile2 || cmax > kItemCap) return false;
   for (int d = 0; d < 3; ++d)
     if (g.T[d] > g.Nt[d] - kTaps + 1 || g.L[d] > 255) return false;

@@ -320,3 +320,43 @@ def test_full_matrix_form_matches_oracle(N, M, m, dt):
     tol = TOL[dt] * (10 if dt == "c128" and m <= 3 else 1)
     assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, m), tol, "forward")
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, m), tol, "adjoint")
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("N,M,m", [((200,), 500, 3), ((40, 36), 2500, 4), ((16, 14, 18), 2000, 3), ((20, 18, 16), 3000, 4)])
+def test_wide_window_matches_oracle(N, M, m, dt):
+    """NFFT_FLAG_WIDE_WINDOW: (2m+2)^D taps of the untruncated window."""
+    from paper_2208_00049_gb300 import binding as B
+    case = inputs.small_case(N, M, seed=71, m=m)
+    fh, y = _run(case, dt, flags=B.NFFT_FLAG_WIDE_WINDOW)
+    tol = TOL[dt] * (10 if dt == "c128" and m <= 3 else 1)
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, m, wide=True), tol, "forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, m, wide=True), tol, "adjoint")
+
+
+def test_accuracy_study_against_ndft():
+    """Sec. 5.1 on the GPU path (complex128, 2D, M = |I_N|, sigma = 2): the
+    error against the exact NDFT decays exponentially in m and saturates by
+    m = 8; the (2m+2)-point variant beats 2m points and loses to m + 1."""
+    from paper_2208_00049_gb300 import binding as B
+    N = (40, 40)
+    M = 1600
+    case = inputs.small_case(N, M, seed=73)
+    ex = ondft.ndft(case["k"], case["f"])
+    exa = ondft.ndft_adjoint(case["k"], case["w"], N)
+    errs, errs_a, wide = {}, {}, {}
+    for m in range(2, 9):
+        c = dict(case, m=m)
+        fh, y = _run(c, "c128")
+        errs[m] = rel_l2(fh, ex)
+        errs_a[m] = rel_l2(y, exa)
+        if m <= 6:
+            fw, _ = _run(c, "c128", flags=B.NFFT_FLAG_WIDE_WINDOW)
+            wide[m] = rel_l2(fw, ex)
+    for e in (errs, errs_a):
+        for m in range(2, 7):
+            assert e[m + 1] < e[m] / 10
+        assert e[8] < 1e-12
+    for m in range(2, 6):
+        assert wide[m] < errs[m]
+        assert errs[m + 1] < wide[m]
