@@ -34,7 +34,6 @@ constexpr int kDeg = 8;             // polynomial degree 2m
 constexpr int kCoef = kDeg + 1;
 constexpr int kPitch = 18;          // shared row pitch (complex) along dim 2
 constexpr int kMaxTile2 = 9;        // L2 = T2 + 7 <= 16: two rows per warp step
-constexpr int kGatherWarps = 4;
 constexpr int kItemCap = 128;       // nodes per work item staged in shared memory
 
 // One staged node = 8 words {t0, t1, t2, a0 | a1 << 8 | a2 << 16, perm, re v, im v, 0}
@@ -167,7 +166,8 @@ __device__ __forceinline__ void load_tile(const Geometry& g, const int* start, c
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kGatherWarps)
+template <int GW>
+__global__ void __launch_bounds__(32 * GW)
     gather3d_m4_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na,
                        const float* __restrict__ poly, float2* __restrict__ fhat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -194,12 +194,12 @@ __global__ void __launch_bounds__(32 * kGatherWarps)
     for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
 
     __syncthreads();
-    load_tile(g, start, grid, tile, warp, lane, kGatherWarps, shift);
+    load_tile(g, start, grid, tile, warp, lane, GW, shift);
     stage_nodes(g, na, item, tc, ns, nullptr, threadIdx.x, blockDim.x);
     cp_async_wait_all();
     __syncthreads();
 
-    for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * kGatherWarps) {
+    for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * GW) {
       const int s = min(s0 + half, item.z - 1);  // a half without a node repeats the last one
       const float word = ns.w[s][lane & 7];
       const float tA = __shfl_sync(0xffffffffu, word, hbase + grp);
@@ -327,6 +327,23 @@ __global__ void __launch_bounds__(32 * W)
   }
 }
 
+int gather_warps() {
+  static int w = [] {
+    const char* e = getenv("NFFT_GB300_GATHER_WARPS");
+    const int v = e ? atoi(e) : 4;
+    return (v == 2 || v == 4 || v == 8) ? v : 4;
+  }();
+  return w;
+}
+
+void* gather_kernel_for(int w) {
+  switch (w) {
+    case 2: return (void*)gather3d_m4_kernel<2>;
+    case 8: return (void*)gather3d_m4_kernel<8>;
+    default: return (void*)gather3d_m4_kernel<4>;
+  }
+}
+
 int scatter_warps() {
   static int w = [] {
     const char* e = getenv("NFFT_GB300_SCATTER_WARPS");
@@ -368,8 +385,8 @@ bool fast3d_supported(const Geometry& g, int cmax) {
 
 int fast3d_ctas_per_sm(const Geometry& g, int kind) {
   const size_t smem = smem_bytes(g);
-  void* k = kind == 0 ? (void*)gather3d_m4_kernel : scatter_kernel_for(scatter_warps());
-  const int threads = kind == 0 ? 32 * kGatherWarps : 32 * scatter_warps();
+  void* k = kind == 0 ? gather_kernel_for(gather_warps()) : scatter_kernel_for(scatter_warps());
+  const int threads = kind == 0 ? 32 * gather_warps() : 32 * scatter_warps();
   if (set_smem(k, smem) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
@@ -379,10 +396,12 @@ int fast3d_ctas_per_sm(const Geometry& g, int kind) {
 cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na,
                                  const float* poly, void* fhat, int ctas, cudaStream_t s) {
   const size_t smem = smem_bytes(g);
-  cudaError_t e = set_smem(gather3d_m4_kernel, smem);
+  const int w = gather_warps();
+  void* k = gather_kernel_for(w);
+  cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
-  gather3d_m4_kernel<<<ctas, 32 * kGatherWarps, smem, s>>>(g, (const float2*)grid, na, poly,
-                                                          (float2*)fhat);
+  auto kern = reinterpret_cast<void (*)(Geometry, const float2*, NodeArrays, const float*, float2*)>(k);
+  kern<<<ctas, 32 * w, smem, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat);
   return cudaGetLastError();
 }
 
