@@ -256,7 +256,8 @@ def algorithmic_bytes(wl, kernel):
     nvals = 8 * int(np.prod(wl["N"]))
     if kernel in ("gather", "scatter"):
         return grid + M * (4 * D + 8)
-    if kernel == "deconv_pad":
+    if kernel in ("deconv_pad", "pad_fft", "fft_crop"):
+        # f read (or y written) once and the grid written (or read) once
         return grid + nvals
     if kernel == "crop_deconv":
         return 2 * nvals
@@ -348,12 +349,10 @@ def full_matrix_form(wl, steps, warmup, flush):
     h = plan.handle
 
     def step():
-        B.check(B.nfft_step_deconv_pad(h, f.data_ptr()))
-        B.check(B.nfft_step_fft(h, -1))
+        B.check(B.nfft_step_pad_fft(h, f.data_ptr()))
         B.check(B.nfft_step_gather(h, fh.data_ptr()))
         B.check(B.nfft_step_scatter(h, w.data_ptr()))
-        B.check(B.nfft_step_fft(h, +1))
-        B.check(B.nfft_step_crop_deconv(h, y.data_ptr()))
+        B.check(B.nfft_step_fft_crop(h, y.data_ptr()))
     ms = time_steps(step, steps, warmup, stream, flush)
     plan.close()
     nnz = wl["M"] * (2 * wl["m"]) ** len(wl["N"])
@@ -496,31 +495,30 @@ def run_gpu(args):
     info = plan.info()
 
     h = plan.handle
-    names = ["deconv_pad", "fft_fwd", "gather", "scatter", "fft_inv", "crop_deconv"]
+    paths = plan.paths()
+    # Algorithm 1 lines 1-6 | 7-9, Algorithm 2 lines 1-3 | 4-10
+    names = ["pad_fft", "gather", "scatter", "fft_crop"]
+    nev = len(names) + 1
 
     def step(evs):
         evs[0].record(stream)
-        B.check(B.nfft_step_deconv_pad(h, f_d.data_ptr()))
+        B.check(B.nfft_step_pad_fft(h, f_d.data_ptr()))
         evs[1].record(stream)
-        B.check(B.nfft_step_fft(h, -1))
-        evs[2].record(stream)
         B.check(B.nfft_step_gather(h, fhat_d.data_ptr()))
-        evs[3].record(stream)
+        evs[2].record(stream)
         B.check(B.nfft_step_scatter(h, w_d.data_ptr()))
+        evs[3].record(stream)
+        B.check(B.nfft_step_fft_crop(h, y_d.data_ptr()))
         evs[4].record(stream)
-        B.check(B.nfft_step_fft(h, +1))
-        evs[5].record(stream)
-        B.check(B.nfft_step_crop_deconv(h, y_d.data_ptr()))
-        evs[6].record(stream)
 
     for _ in range(args.warmup):
         flush.zero_()
-        step([torch.cuda.Event(enable_timing=True) for _ in range(7)])
+        step([torch.cuda.Event(enable_timing=True) for _ in range(nev)])
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    all_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    all_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             flush.zero_()
@@ -534,14 +532,14 @@ def run_gpu(args):
     per = {n: [] for n in names}
     steps_ms = []
     for evs in all_ev:
-        steps_ms.append(evs[0].elapsed_time(evs[6]))
+        steps_ms.append(evs[0].elapsed_time(evs[-1]))
         for j, n in enumerate(names):
             per[n].append(evs[j].elapsed_time(evs[j + 1]))
     agg = aggregate_replicas(sum(steps_ms), wl["M"], args.steps)
     ms_per_step = agg["ms_per_step"]
     value = agg["value"]
     mean = {n: statistics.mean(v) for n, v in per.items()}
-    conv_ms = mean["deconv_pad"] + mean["gather"] + mean["scatter"] + mean["crop_deconv"]
+    resample_ms = mean["gather"] + mean["scatter"]
 
     # roofline of the dominant kernel
     dom = "gather" if mean["gather"] >= mean["scatter"] else "scatter"
@@ -554,12 +552,25 @@ def run_gpu(args):
                 "traffic": traffic, "algorithmic_bytes": abytes}
     kernel_table = {}
     for n in names:
-        entry = {"ms": round(mean[n], 4)}
-        if n in ("deconv_pad", "gather", "scatter", "crop_deconv"):
-            ab = algorithmic_bytes(wl, n)
-            entry["GBps"] = round(ab / (mean[n] * 1e-3) / 1e9, 1)
-            entry["hbm_frac"] = round(ab / (mean[n] * 1e-3) / 1e9 / peak, 4)
-        kernel_table[n] = entry
+        ab = algorithmic_bytes(wl, n)
+        kernel_table[n] = {"ms": round(mean[n], 4), "GBps": round(ab / (mean[n] * 1e-3) / 1e9, 1),
+                           "hbm_frac": round(ab / (mean[n] * 1e-3) / 1e9 / peak, 4)}
+
+    # the same Algorithm 1 lines 1-6 / Algorithm 2 lines 4-10 as separate
+    # correction kernels around cuFFT (the form the pruned FFT replaces)
+    def lib_fwd():
+        B.check(B.nfft_step_deconv_pad(h, f_d.data_ptr()))
+        B.check(B.nfft_step_fft(h, -1))
+
+    def lib_adj():
+        B.check(B.nfft_step_fft(h, +1))
+        B.check(B.nfft_step_crop_deconv(h, y_d.data_ptr()))
+
+    nlib = min(20, max(3, args.steps // 4))
+    fft_forms = {"pruned_fft_used": paths["pruned_fft"],
+                 "pad_fft_ms": round(mean["pad_fft"], 4), "fft_crop_ms": round(mean["fft_crop"], 4),
+                 "library_pad_fft_ms": round(time_steps(lib_fwd, nlib, 2, stream, flush), 4),
+                 "library_fft_crop_ms": round(time_steps(lib_adj, nlib, 2, stream, flush), 4)}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -612,7 +623,9 @@ def run_gpu(args):
                "sample": det["sample"], "detail": det}
         accuracy["rel_l2_vs_ndft_48_sampled_nodes"] = ndft_sample_error(wl, fhat32)
 
-    launches_per_step = 4  # deconv_pad, gather, scatter, crop_deconv (cuFFT and memset not counted)
+    # pruned FFT: 3 + 3 line-DFT kernels; else deconv_pad and crop_deconv
+    # (cuFFT's kernels and the grid memset not counted); gather and scatter
+    launches_per_step = (8 if paths["pruned_fft"] else 4)
     plan.close()
     if rank == 0:
         line = {
@@ -623,9 +636,10 @@ def run_gpu(args):
             "config": {"workload": workload_desc(wl), "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "tile": list(info["tile"]), "work_items": info["n_items"]},
-            "nodes_per_s_excl_fft": world * wl["M"] / (conv_ms * 1e-3),
+            "nodes_per_s_resampling_only": world * wl["M"] / (resample_ms * 1e-3),
             "set_nodes_ms": round(set_nodes_ms, 3),
             "kernels": kernel_table,
+            "fft_forms": fft_forms,
             "roofline": roofline,
             "fp64_form": fp64,
             "full_matrix_form": full,

@@ -74,6 +74,10 @@ extern "C" {
    accurate than 2m points at the same m (Sec. 5.1).  Exclusive with
    NFFT_FLAG_CLOSED_SUPPORT. */
 #define NFFT_FLAG_WIDE_WINDOW     0x8u
+/* Run Algorithm 1 lines 1-6 and Algorithm 2 lines 4-10 as the separate
+   correction kernels around a full cuFFT transform even where the plan
+   qualifies for the pruned FFT (see nfft_step_pad_fft). */
+#define NFFT_FLAG_LIBRARY_FFT     0x10u
 
 typedef struct nfft_plan nfft_plan;
 
@@ -175,6 +179,30 @@ int nfft_step_scatter(nfft_plan *p, const void *fhat);
 /* Algorithm 2 lines 8-10: crop of the plan grid to I_N and resampling
  * correction into y. */
 int nfft_step_crop_deconv(nfft_plan *p, void *y);
+
+/* Algorithm 1 lines 1-6 in one call: correction, zero pad and forward FFT
+ * of f into the plan grid (the grid then holds ghat as after
+ * nfft_step_deconv_pad + nfft_step_fft(-1)).  For D = 3, complex64 and
+ * N~_d = 2 N_d = 256 (and without NFFT_FLAG_LIBRARY_FFT) this is the pruned
+ * FFT: three passes of 256-point line DFTs that read only the non-zero part
+ * of the padded grid, with the correction fused into the first pass and the
+ * fftshift of Sec. 3.5 applied as the exact phase i^l (N~ = 2N).  Otherwise
+ * it runs the two separate steps. */
+int nfft_step_pad_fft(nfft_plan *p, const void *f);
+
+/* Algorithm 2 lines 4-10 in one call: unnormalised inverse FFT of the plan
+ * grid, crop to I_N and correction into y.  Pruned as for nfft_step_pad_fft
+ * (each inverse pass computes only the N outputs that are kept; the plan
+ * grid is used as scratch and does not hold the full inverse FFT
+ * afterwards); otherwise nfft_step_fft(+1) + nfft_step_crop_deconv. */
+int nfft_step_fft_crop(nfft_plan *p, void *y);
+
+/* Which kernels the plan's transforms use: *fast_resample = 1 when the 3D
+ * m = 4 complex64 node-per-half-warp gather / plane-owned scatter kernels
+ * apply (set by nfft_plan_create and nfft_set_nodes), *pruned_fft = 1 when
+ * nfft_step_pad_fft / nfft_step_fft_crop run the pruned FFT.  Either
+ * pointer may be NULL. */
+int nfft_plan_paths(nfft_plan *p, int *fast_resample, int *pruned_fft);
 
 /* Node-gradient resampling on the current plan grid (which must hold
  * ghat = F D f): gk[j][d] = Re(conj(cot_j) d fhat_j / d k_{j,d}). */

@@ -27,6 +27,7 @@ NFFT_FLAG_CLOSED_SUPPORT = 0x1
 NFFT_FLAG_COMPENSATED = 0x2
 NFFT_FLAG_FULL_MATRIX = 0x4
 NFFT_FLAG_WIDE_WINDOW = 0x8
+NFFT_FLAG_LIBRARY_FFT = 0x10
 
 _p = ctypes.c_void_p
 _i = ctypes.c_int
@@ -51,6 +52,9 @@ SIGNATURES = {
     "nfft_step_gather": (_i, [_p, _p]),
     "nfft_step_scatter": (_i, [_p, _p]),
     "nfft_step_crop_deconv": (_i, [_p, _p]),
+    "nfft_step_pad_fft": (_i, [_p, _p]),
+    "nfft_step_fft_crop": (_i, [_p, _p]),
+    "nfft_plan_paths": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nfft_step_grad_gather": (_i, [_p, _p, _p]),
     "nfft_plan_autotune": (_i, [_p, _p, _i, _i64p]),
     "nfft_batch_create": (_i, [ctypes.POINTER(_p), _i, _i, _i64p, ctypes.POINTER(ctypes.c_int32), _i, _i64p,
@@ -184,6 +188,22 @@ def nfft_step_scatter(plan, fhat_ptr):
 
 def nfft_step_crop_deconv(plan, y_ptr):
     return lib().nfft_step_crop_deconv(_p(plan), _p(y_ptr))
+
+
+def nfft_step_pad_fft(plan, f_ptr):
+    return lib().nfft_step_pad_fft(_p(plan), _p(f_ptr))
+
+
+def nfft_step_fft_crop(plan, y_ptr):
+    return lib().nfft_step_fft_crop(_p(plan), _p(y_ptr))
+
+
+def nfft_plan_paths(plan):
+    """Returns (status, fast_resample, pruned_fft)."""
+    a = _i()
+    b = _i()
+    s = lib().nfft_plan_paths(_p(plan), ctypes.byref(a), ctypes.byref(b))
+    return s, bool(a.value), bool(b.value)
 
 
 def nfft_step_grad_gather(plan, cot_ptr, gk_ptr):

@@ -143,6 +143,15 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
                                   const float* poly, const void* fhat, int ctas, cudaStream_t s);
 
+// Pruned 3D FFT with the resampling correction fused in, N~_d = 2 N_d = 256,
+// complex64 (fft_pruned.cu).  `tw` holds the 256 twiddles exp(-2 pi i j/256)
+// (build_fft_twiddles); beta[d] are the FP32 correction vectors.
+bool pruned_fft_supported(int D, const int* N, const int* Nt);
+cudaError_t build_fft_twiddles(float2* tw, cudaStream_t s);
+cudaError_t launch_pruned_forward(const void* f, const float* const* beta, const float2* tw, void* grid,
+                                  cudaStream_t s);
+cudaError_t launch_pruned_adjoint(void* grid, const float* const* beta, const float2* tw, void* y, cudaStream_t s);
+
 // FULL precomputation: B as a CSR matrix, applied with cuSPARSE (nfft_full.cu)
 struct FullMatrix;
 int full_build(FullMatrix** out, const Geometry& g, int dtype, const NodeArrays& na, cudaStream_t s);

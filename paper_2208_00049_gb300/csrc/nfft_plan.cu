@@ -44,6 +44,8 @@ struct nfft_plan {
   bool fast3d = false;         // 3D m = 4 complex64 warp-per-node kernels
   FullMatrix* full = nullptr;  // NFFT_FLAG_FULL_MATRIX: B and B^T as CSR
   int fast_ctas[2] = {0, 0};
+  bool pruned = false;         // nfft_step_pad_fft / fft_crop use the pruned 3D FFT
+  float2* fft_tw = nullptr;    // its 256 twiddles
 
   void* grid = nullptr;
   double* beta64 = nullptr;
@@ -377,6 +379,40 @@ int run_scatter(nfft_plan* p, const void* fhat) {
   return cuda_status(p, e);
 }
 
+const float* const* beta32_dims(const nfft_plan* p, const float** out) {
+  int64_t off = 0;
+  for (int d = 0; d < p->D; ++d) {
+    out[d] = p->beta32 + off;
+    off += p->N[d];
+  }
+  return out;
+}
+
+// Algorithm 1 lines 1-6: pruned FFT where the plan qualifies, else the
+// correction kernel and cuFFT.
+int run_pad_fft(nfft_plan* p, const void* f) {
+  if (p->pruned) {
+    const float* beta[kMaxD];
+    return cuda_status(p, launch_pruned_forward(f, beta32_dims(p, beta), p->fft_tw, p->grid, p->stream));
+  }
+  int s = run_deconv_pad(p, f);
+  if (s != NFFT_OK) return s;
+  return run_fft(p, -1);
+}
+
+int run_crop_deconv(nfft_plan* p, void* y);
+
+// Algorithm 2 lines 4-10.
+int run_fft_crop(nfft_plan* p, void* y) {
+  if (p->pruned) {
+    const float* beta[kMaxD];
+    return cuda_status(p, launch_pruned_adjoint(p->grid, beta32_dims(p, beta), p->fft_tw, y, p->stream));
+  }
+  int s = run_fft(p, +1);
+  if (s != NFFT_OK) return s;
+  return run_crop_deconv(p, y);
+}
+
 int run_crop_deconv(nfft_plan* p, void* y) {
   DeconvArgs a = make_deconv(p);
   cudaError_t e = p->dtype == NFFT_C128 ? launch_crop_deconv<double>(a, p->grid, y, p->stream)
@@ -419,7 +455,7 @@ int nfft_plan_destroy(nfft_plan* p) {
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->fft_ok) cufftDestroy(p->fft);
   full_destroy(p->full);
-  void* bufs[] = {p->grid, p->beta64, p->beta32, p->poly, p->cell, p->frac, p->perm, p->key, p->rank,
+  void* bufs[] = {p->grid, p->fft_tw, p->beta64, p->beta32, p->poly, p->cell, p->frac, p->perm, p->key, p->rank,
                   p->tile_count, p->tile_offset, p->items, p->n_items,
                   p->stage[0], p->stage[1], p->stage[2]};
   for (void* b : bufs) dfree(b);
@@ -436,7 +472,7 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
   if (dtype != NFFT_C64 && dtype != NFFT_C128) return NFFT_ERR_INVALID_ARG;
   if (M < 0 || M >= ((int64_t)1 << 31)) return NFFT_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_COMPENSATED | NFFT_FLAG_FULL_MATRIX |
-                          NFFT_FLAG_WIDE_WINDOW))
+                          NFFT_FLAG_WIDE_WINDOW | NFFT_FLAG_LIBRARY_FFT))
     return NFFT_ERR_INVALID_ARG;
   if ((flags & NFFT_FLAG_CLOSED_SUPPORT) && (flags & NFFT_FLAG_WIDE_WINDOW)) return NFFT_ERR_INVALID_ARG;
   int64_t total = 1;
@@ -521,6 +557,18 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
     for (int d = 0; d < D; ++d) pa.b[d] = p->b[d];
     s = cuda_status(p, launch_build_poly(pa, p->poly, p->stream));
   }
+  if (s == NFFT_OK && dtype == NFFT_C64 && !(flags & NFFT_FLAG_LIBRARY_FFT)) {
+    int Ni[kMaxD], Nti[kMaxD];
+    for (int d = 0; d < D; ++d) {
+      Ni[d] = (int)N[d];
+      Nti[d] = (int)p->Nt[d];
+    }
+    if (pruned_fft_supported(D, Ni, Nti)) {
+      s = dalloc(p, &p->fft_tw, sizeof(float2) * 256);
+      if (s == NFFT_OK) s = cuda_status(p, build_fft_twiddles(p->fft_tw, p->stream));
+      p->pruned = s == NFFT_OK;
+    }
+  }
   if (s == NFFT_OK) s = cuda_status(p, cudaMemsetAsync(p->n_items, 0, sizeof(int), p->stream));
   if (s != NFFT_OK) {
     nfft_plan_destroy(p);
@@ -574,8 +622,7 @@ int nfft_forward(nfft_plan* p, const void* f, void* fhat) {
   OutputBinding ob;
   if ((s = device_input(p, 0, f, (size_t)prod_N(p) * cplx_size(p), &fd)) != NFFT_OK) return s;
   if ((s = device_output(p, 1, fhat, (size_t)p->M * cplx_size(p), &ob)) != NFFT_OK) return s;
-  if ((s = run_deconv_pad(p, fd)) != NFFT_OK) return s;
-  if ((s = run_fft(p, -1)) != NFFT_OK) return s;
+  if ((s = run_pad_fft(p, fd)) != NFFT_OK) return s;
   if ((s = run_gather(p, ob.dev)) != NFFT_OK) return s;
   return finish_output(p, ob);
 }
@@ -591,8 +638,7 @@ int nfft_adjoint(nfft_plan* p, const void* fhat, void* y) {
   if ((s = device_input(p, 0, fhat, (size_t)p->M * cplx_size(p), &fd)) != NFFT_OK) return s;
   if ((s = device_output(p, 1, y, (size_t)prod_N(p) * cplx_size(p), &ob)) != NFFT_OK) return s;
   if ((s = run_scatter(p, fd)) != NFFT_OK) return s;
-  if ((s = run_fft(p, +1)) != NFFT_OK) return s;
-  if ((s = run_crop_deconv(p, ob.dev)) != NFFT_OK) return s;
+  if ((s = run_fft_crop(p, ob.dev)) != NFFT_OK) return s;
   return finish_output(p, ob);
 }
 
@@ -608,8 +654,7 @@ int nfft_grad(nfft_plan* p, const void* f, const void* cot, void* gk) {
   if ((s = device_input(p, 0, f, (size_t)prod_N(p) * cplx_size(p), &fd)) != NFFT_OK) return s;
   if ((s = device_input(p, 2, cot, (size_t)p->M * cplx_size(p), &cd)) != NFFT_OK) return s;
   if ((s = device_output(p, 1, gk, (size_t)(p->M * p->D) * real_size(p), &ob)) != NFFT_OK) return s;
-  if ((s = run_deconv_pad(p, fd)) != NFFT_OK) return s;
-  if ((s = run_fft(p, -1)) != NFFT_OK) return s;
+  if ((s = run_pad_fft(p, fd)) != NFFT_OK) return s;
   if ((s = run_grad_gather(p, cd, ob.dev)) != NFFT_OK) return s;
   return finish_output(p, ob);
 }
@@ -796,6 +841,29 @@ int nfft_step_crop_deconv(nfft_plan* p, void* y) {
   if (!y) return NFFT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
   return run_crop_deconv(p, y);
+}
+
+int nfft_step_pad_fft(nfft_plan* p, const void* f) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!f) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  return run_pad_fft(p, f);
+}
+
+int nfft_step_fft_crop(nfft_plan* p, void* y) {
+  int s;
+  if (!ready(p, &s)) return s;
+  if (!y) return NFFT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  return run_fft_crop(p, y);
+}
+
+int nfft_plan_paths(nfft_plan* p, int* fast_resample, int* pruned_fft) {
+  if (!p) return NFFT_ERR_INVALID_ARG;
+  if (fast_resample) *fast_resample = p->fast3d ? 1 : 0;
+  if (pruned_fft) *pruned_fft = p->pruned ? 1 : 0;
+  return NFFT_OK;
 }
 
 int nfft_step_grad_gather(nfft_plan* p, const void* cot, void* gk) {

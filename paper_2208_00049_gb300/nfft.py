@@ -173,6 +173,23 @@ class Plan:
         B.check(B.nfft_step_crop_deconv(self.handle, _ptr(out)), "nfft_step_crop_deconv")
         return out
 
+    def step_pad_fft(self, f):
+        """Algorithm 1 lines 1-6 (the pruned FFT where the plan qualifies)."""
+        self._check_tensor(f, self.N, self.dtype, "f")
+        B.check(B.nfft_step_pad_fft(self.handle, _ptr(f)), "nfft_step_pad_fft")
+
+    def step_fft_crop(self, out):
+        """Algorithm 2 lines 4-10 (the pruned FFT where the plan qualifies)."""
+        self._check_tensor(out, self.N, self.dtype, "out")
+        B.check(B.nfft_step_fft_crop(self.handle, _ptr(out)), "nfft_step_fft_crop")
+        return out
+
+    def paths(self):
+        """{'fast_resample': bool, 'pruned_fft': bool} for this plan."""
+        s, fast, pruned = B.nfft_plan_paths(self.handle)
+        B.check(s, "nfft_plan_paths")
+        return {"fast_resample": fast, "pruned_fft": pruned}
+
     def step_grad_gather(self, cot, out):
         self._check_tensor(cot, (self.M,), self.dtype, "cot")
         self._check_tensor(out, (self.M, self.D), self.real_dtype, "out")

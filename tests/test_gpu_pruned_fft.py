@@ -1,0 +1,125 @@
+"""GPU parity of the pruned 3D FFT (N~_d = 2 N_d = 256, complex64) against the
+FP64 oracle: the fused steps Algorithm 1 lines 1-6 and Algorithm 2 lines
+4-10 element by element on the full 256^3 grid / 128^3 output, the whole
+transforms and the node gradient through them, and the selection rule."""
+import numpy as np
+import pytest
+
+from oracle import nfft as onfft
+from paper_2208_00049_gb300 import inputs
+
+from gpu_helpers import assert_close, cdtype, rel_l2, require_gpu, to_dev, tol_for, tol_max_for
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N3 = (128, 128, 128)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _plan(N, M, dt="c64", flags=0, sigma=2.0, m=4):
+    from paper_2208_00049_gb300.nfft import Plan
+    return Plan(N, M, sigma=sigma, m=m, dtype=cdtype(dt), flags=flags)
+
+
+def _peak(p):
+    # the library scales the window to 1 at u = 0 and the correction by
+    # prod_d psi_d(0) to match
+    return float(np.prod([float(onfft.psi(0.0, p.m, b)) for b in p.b]))
+
+
+def test_pruned_path_selection():
+    from paper_2208_00049_gb300 import binding as B
+    cases = [
+        ((128, 128, 128), "c64", 0, 2.0, True),
+        ((128, 128, 128), "c64", B.NFFT_FLAG_LIBRARY_FFT, 2.0, False),
+        ((128, 128, 128), "c128", 0, 2.0, False),
+        ((128, 128, 64), "c64", 0, 2.0, False),
+        ((128, 128, 128), "c64", 0, 1.5, False),
+        ((128, 128), "c64", 0, 2.0, False),
+    ]
+    for N, dt, flags, sigma, want in cases:
+        plan = _plan(N, 8, dt, flags, sigma)
+        assert plan.paths()["pruned_fft"] is want, (N, dt, flags, sigma)
+        plan.close()
+
+
+def test_pad_fft_matches_oracle():
+    """Algorithm 1 lines 1-6 on the full grid: correction, zero pad, FFT."""
+    rng = np.random.default_rng(2208)
+    f = inputs.complex_normal(rng, N3)
+    p = onfft.Params(N3, 2.0, 4)
+    plan = _plan(N3, 8)
+    assert plan.paths()["pruned_fft"]
+    plan.step_pad_fft(to_dev(f, torch.complex64))
+    got = plan.grid_tensor().cpu().numpy().astype(np.complex128) / _peak(p)
+    want = onfft.fft_forward(onfft.correction_pad(p, f))
+    assert_close(got, want, tol_for(N3, 2.0, 4, "c64"), "pad_fft", tol_max_for(N3, 2.0, 4, "c64"))
+    plan.close()
+
+
+def test_fft_crop_matches_oracle():
+    """Algorithm 2 lines 4-10: inverse FFT of an arbitrary grid, crop, correction."""
+    rng = np.random.default_rng(49)
+    p = onfft.Params(N3, 2.0, 4)
+    G = inputs.complex_normal(rng, p.Nt)
+    plan = _plan(N3, 8)
+    plan.grid_tensor().copy_(torch.from_numpy(G.astype(np.complex64)))
+    y = torch.empty(N3, dtype=torch.complex64, device="cuda")
+    plan.step_fft_crop(y)
+    got = y.cpu().numpy().astype(np.complex128) / _peak(p)
+    want = onfft.crop_correction(p, onfft.fft_adjoint(G))
+    assert_close(got, want, tol_for(N3, 2.0, 4, "c64"), "fft_crop", tol_max_for(N3, 2.0, 4, "c64"))
+    plan.close()
+
+
+def test_pruned_and_library_fft_agree():
+    """Both FP32 forms of the same steps agree to FP32 rounding."""
+    from paper_2208_00049_gb300 import binding as B
+    rng = np.random.default_rng(7)
+    f = to_dev(inputs.complex_normal(rng, N3), torch.complex64)
+    grids = []
+    for flags in (0, B.NFFT_FLAG_LIBRARY_FFT):
+        plan = _plan(N3, 8, flags=flags)
+        plan.step_pad_fft(f)
+        grids.append(plan.grid_tensor().cpu().numpy())
+        plan.close()
+    assert rel_l2(grids[0], grids[1]) <= 2e-6
+
+
+@pytest.mark.parametrize("M", [1, 20000])
+def test_transforms_through_pruned_fft(M):
+    """nfft_forward / nfft_adjoint at N = 128^3 (pruned path) against the oracle."""
+    rng = np.random.default_rng(1000 + M)
+    k = inputs.uniform_nodes(rng, M, 3)
+    f = inputs.complex_normal(rng, N3)
+    w = inputs.complex_normal(rng, (M,))
+    plan = _plan(N3, M)
+    assert plan.paths()["pruned_fft"]
+    plan.set_nodes(to_dev(k, torch.float64))
+    fh = plan.forward(to_dev(f, torch.complex64)).cpu().numpy()
+    y = plan.adjoint(to_dev(w, torch.complex64)).cpu().numpy()
+    plan.close()
+    tol, tmax = tol_for(N3, 2.0, 4, "c64"), tol_max_for(N3, 2.0, 4, "c64")
+    assert_close(fh, onfft.forward(k, f, 2.0, 4), tol, "forward", tmax)
+    assert_close(y, onfft.adjoint(k, w, N3, 2.0, 4), tol, "adjoint", tmax)
+
+
+def test_grad_through_pruned_fft():
+    """nfft_grad (ghat from the pruned FFT) against the oracle's node gradient."""
+    M = 3000
+    rng = np.random.default_rng(77)
+    k = inputs.uniform_nodes(rng, M, 3)
+    f = inputs.complex_normal(rng, N3)
+    cot = inputs.complex_normal(rng, (M,))
+    plan = _plan(N3, M)
+    plan.set_nodes(to_dev(k, torch.float64))
+    gk = plan.grad(to_dev(f, torch.complex64), to_dev(cot, torch.complex64)).cpu().numpy()
+    plan.close()
+    want = onfft.node_grad(k, f, cot, 2.0, 4)
+    # the complex64 node-gradient tolerance of the other gradient tests
+    assert_close(gk, want, 1e-4, "grad")
