@@ -14,17 +14,25 @@
 // the correction and writes y.  HBM traffic: 352 MB per direction at N = 128
 // against about 950 MB for a separate correction pass plus a full 3D FFT.
 //
-// A 256-point line DFT is 16 x 16: thread n2 of the line's 16 takes the
-// 16-point DFT over n1 of x[16 n1 + n2], multiplies by exp(-2 pi i n2 k1/256),
-// and after a transpose thread k1 takes the 16-point DFT over n2, giving
-// X[k1 + 16 k2].  The 16-point DFTs are 4 x 4 in registers with constant
-// twiddles; the 16 x 16 inter-stage twiddles come from a table built in FP64
-// on the device.
+// A 256-point line DFT is 16 x 16: thread r of the line's 16 takes the
+// 16-point DFT over n1 of x[16 n1 + r], multiplies by exp(-2 pi i r k1/256),
+// and after a transpose in shared memory thread k1 takes the 16-point DFT
+// over n2, giving X[k1 + 16 k2].  The 16-point DFTs are 4 x 4 in registers
+// with constant twiddles.
 //
-// Latency, not bandwidth, limits passes like these: every pass loads all of a
-// CTA's lines with fully unrolled loads before the first shared-memory store,
-// the transpose buffer aliases the staging buffer (about 19 KB per CTA), and
-// registers are capped so that 8 CTAs share an SM.
+// Thread layouts make every global access coalesced without staging: in a row
+// pass (line contiguous) thread (line, r) loads x[16 n1 + r], 16 lanes reading
+// 128 consecutive bytes; in a column pass 16 adjacent lines (columns) are
+// handled together and thread (line, r) loads row 16 n1 + r of its column, a
+// half-warp again reading 128 consecutive bytes.  Stage-2 thread k1 holds
+// X[k1 + 16 k2], k2 = 0..15, and stores them in the same pattern.  One
+// shared-memory transpose and one barrier per pass.
+//
+// The phases fold into the inter-stage twiddles: output n = k1 + 16 k2 has
+// i^n = i^k1 (constant per stage-2 thread) and input n = 16 n1 + r has
+// (-i)^n = (-i)^r (constant per stage-1 thread), so the tables are
+//   forward  W256^(r k1) i^k1,   inverse  conj(W256^(r k1)) (-i)^r,
+// built in FP64 on the device.
 #include "nfft_internal.cuh"
 
 namespace nfftgb {
@@ -32,21 +40,28 @@ namespace {
 
 constexpr int kLen = 256;
 constexpr int kHalf = 128;
-constexpr int kLines = 8;                 // lines per CTA
-constexpr int kThreads = 16 * kLines;     // 16 threads per line
-constexpr int kSweep = kThreads / kLines; // rows of the column block per CTA-wide load
-constexpr int kBufPitch = kLen + 2;       // line pitch (complex): column staging conflict-free
-constexpr int kTPitch = 17;               // padded pitch of the 16 x 16 transpose
-constexpr int kMinCtas = 8;               // CTAs per SM the register cap allows
+#ifndef NFFT_PRUNED_LINES
+#define NFFT_PRUNED_LINES 16
+#endif
+#ifndef NFFT_PRUNED_MIN_CTAS
+#define NFFT_PRUNED_MIN_CTAS 4
+#endif
+constexpr int kLines = NFFT_PRUNED_LINES;     // lines per CTA
+constexpr int kThreads = 16 * kLines;         // 16 threads per line
+constexpr int kMinCtas = NFFT_PRUNED_MIN_CTAS;  // CTAs per SM the register cap allows
+static_assert(kLines == 8 || kLines == 16, "lines per CTA");
 
-struct FftSmem {
-  union {
-    float2 buf[kLines][kBufPitch];        // the lines (staging, input and output)
-    float2 T[kLines][16][kTPitch];        // the 16 x 16 transposes between the stages
-  } u;
-  float2 tw[16][16];                      // tw[k1][r] = W256^(r k1)
-};
-static_assert(sizeof(FftSmem) <= 48 * 1024, "static shared-memory launch");
+// Transpose buffers.  Row passes: [line][a][b], pitch 17 along a.  Column
+// passes: [a][b][line] (lines fastest, 8 complex of padding per a when
+// kLines = 8 so that the two r of a half-warp fall in different banks).
+constexpr int kRowT = kLines * 16 * 17;
+constexpr int kColPad = kLines == 8 ? 8 : 0;
+constexpr int kColT = 16 * (16 * kLines + kColPad);
+constexpr int kTSize = kRowT > kColT ? kRowT : kColT;
+static_assert(kTSize * 8 <= 48 * 1024, "static shared-memory launch");
+
+__device__ __forceinline__ int row_t(int line, int a, int b) { return line * (16 * 17) + a * 17 + b; }
+__device__ __forceinline__ int col_t(int line, int a, int b) { return a * (16 * kLines + kColPad) + b * kLines + line; }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -54,12 +69,7 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 conj_if(float2 w, bool c) { return c ? make_float2(w.x, -w.y) : w; }
-
-// a * i^q, branch-free (q mod 4)
-__device__ __forceinline__ float2 mul_ipow(float2 a, int q) {
-  float2 v = (q & 1) ? make_float2(-a.y, a.x) : a;
-  return (q & 2) ? make_float2(-v.x, -v.y) : v;
-}
+__device__ __forceinline__ float2 cscale(float2 a, float b) { return make_float2(a.x * b, a.y * b); }
 
 // W16^k = exp(-2 pi i k/16) for the products n2 k1 of the 4 x 4 split
 // (k in {1, 2, 3, 4, 6, 9}); cos(pi/8), sin(pi/8) and sqrt(1/2).
@@ -90,7 +100,11 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
 
 template <bool INV, int K>
 __device__ __forceinline__ void tw16(float2& a) {
-  a = cmul(a, conj_if(w16<K>(), INV));
+  if constexpr (K == 4) {
+    a = INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);  // * -+i
+  } else {
+    a = cmul(a, conj_if(w16<K>(), INV));
+  }
 }
 
 // 16-point DFT in registers, in place with the output permuted:
@@ -117,146 +131,101 @@ __device__ __forceinline__ void dft16(float2* x) {
 // X[k] of dft16's output: x[4 (k & 3) + (k >> 2)]
 __device__ __forceinline__ constexpr int perm16(int k) { return 4 * (k & 3) + (k >> 2); }
 
-// 256-point DFT of the kLines lines staged in s.u.buf, in place.  Thread
-// (line, r): r = n2 in the first stage, r = k1 in the second.  NIN = number
-// of leading inputs that can be non-zero (128 for the zero-padded forward).
-template <bool INV, int NIN>
-__device__ __forceinline__ void line_dft256(FftSmem& s, int line, int r) {
-  float2 x[16];
-#pragma unroll
-  for (int n1 = 0; n1 < 16; ++n1) x[n1] = (16 * n1 < NIN) ? s.u.buf[line][16 * n1 + r] : make_float2(0.f, 0.f);
+// The 256-point line DFT around the loads and stores: on entry x[n1] =
+// x_line[16 n1 + r] (thread (line, r)), on return x[perm16(k2)] =
+// X_line[r + 16 k2] (thread (line, k1 = r)), phases included.  COL selects
+// the transpose layout.  One barrier.
+template <bool INV, bool COL>
+__device__ __forceinline__ void line_dft256(float2* x, float2* T, const float2* __restrict__ tw, int line, int r) {
   dft16<INV>(x);
+  const float2* twr = tw + (INV ? kLen : 0) + r;
 #pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) x[perm16(k1)] = cmul(x[perm16(k1)], conj_if(s.tw[k1][r], INV));
-  __syncthreads();  // every line read before the transpose overwrites it
-#pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) s.u.T[line][k1][r] = x[perm16(k1)];
+  for (int k1 = 0; k1 < 16; ++k1) {
+    const float2 v = cmul(x[perm16(k1)], __ldg(twr + 16 * k1));
+    T[COL ? col_t(line, k1, r) : row_t(line, k1, r)] = v;
+  }
   __syncthreads();
 #pragma unroll
-  for (int n2 = 0; n2 < 16; ++n2) x[n2] = s.u.T[line][r][n2];
+  for (int n2 = 0; n2 < 16; ++n2) x[n2] = T[COL ? col_t(line, r, n2) : row_t(line, r, n2)];
   dft16<INV>(x);
-  __syncthreads();  // every transpose read before the lines are written back
-#pragma unroll
-  for (int k2 = 0; k2 < 16; ++k2) s.u.buf[line][r + 16 * k2] = x[perm16(k2)];
-  __syncthreads();
-}
-
-__device__ __forceinline__ void load_twiddles(FftSmem& s, const float2* tw) {
-  for (int j = threadIdx.x; j < kLen; j += blockDim.x) (&s.tw[0][0])[j] = tw[j];
 }
 
 // Pass A (forward): rows (i0, i1) of f times the correction, DFT along dim 2,
-// post-phase i^l, into the grid rows (i0, i1, :).
+// into the grid rows (i0, i1, :).
 __global__ void __launch_bounds__(kThreads, kMinCtas)
     fwd_rows_kernel(const float2* __restrict__ f, const float* __restrict__ beta0, const float* __restrict__ beta1,
                     const float* __restrict__ beta2, const float2* __restrict__ tw, float2* __restrict__ grid) {
-  __shared__ FftSmem s;
-  const int t = threadIdx.x;
-  const int row0 = blockIdx.x * kLines;
-  float2 v[kLines];
+  __shared__ float2 T[kTSize];
+  const int t = threadIdx.x, line = t >> 4, r = t & 15;
+  const int row = blockIdx.x * kLines + line, i0 = row / kHalf, i1 = row - i0 * kHalf;
+  const float2* src = f + (int64_t)row * kHalf + r;
+  float2 x[16];
 #pragma unroll
-  for (int line = 0; line < kLines; ++line) v[line] = f[(int64_t)(row0 + line) * kHalf + t];
-  load_twiddles(s, tw);
-  const float b2 = beta2[t];
+  for (int n1 = 0; n1 < 8; ++n1) x[n1] = src[16 * n1];
+  const float b01 = beta0[i0] * beta1[i1];
 #pragma unroll
-  for (int line = 0; line < kLines; ++line) {
-    const int row = row0 + line, i0 = row / kHalf, i1 = row - i0 * kHalf;
-    const float b = beta0[i0] * beta1[i1] * b2;
-    s.u.buf[line][t] = make_float2(v[line].x * b, v[line].y * b);
-  }
-  __syncthreads();
-  line_dft256<false, kHalf>(s, t >> 4, t & 15);
+  for (int n1 = 0; n1 < 8; ++n1) x[n1] = cscale(x[n1], b01 * beta2[16 * n1 + r]);
 #pragma unroll
-  for (int line = 0; line < kLines; ++line) {
-    const int row = row0 + line, i0 = row / kHalf, i1 = row - i0 * kHalf;
-    float2* dst = grid + ((int64_t)i0 * kLen + i1) * kLen;
+  for (int n1 = 8; n1 < 16; ++n1) x[n1] = make_float2(0.f, 0.f);
+  line_dft256<false, false>(x, T, tw, line, r);
+  float2* dst = grid + ((int64_t)i0 * kLen + i1) * kLen + r;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int l = t + h * kThreads;
-      dst[l] = mul_ipow(s.u.buf[line][l], l);
-    }
-  }
+  for (int k2 = 0; k2 < 16; ++k2) dst[16 * k2] = x[perm16(k2)];
 }
 
 // Passes B and C (forward): kLines adjacent columns (element stride S, first
-// element at base + j) read N inputs, write N~ outputs in place with the
-// post-phase i^l.  Passes C' and B' (adjoint): read N~ inputs with the
-// pre-phase (-i)^l, write the N outputs of the inverse DFT in place.
+// element at base + line) read N inputs, write N~ outputs in place.  Passes
+// C' and B' (adjoint): read N~ inputs, write the N outputs of the inverse DFT
+// in place.
 template <bool INV>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
     cols_kernel(float2* __restrict__ grid, int64_t outer_stride, int64_t S, const float2* __restrict__ tw) {
-  __shared__ FftSmem s;
-  constexpr int NIN = INV ? kLen : kHalf;
-  constexpr int NOUT = INV ? kHalf : kLen;
-  const int t = threadIdx.x;
+  __shared__ float2 T[kTSize];
+  constexpr int NIN1 = (INV ? kLen : kHalf) / 16;   // stage-1 inputs per thread
+  constexpr int NOUT2 = (INV ? kHalf : kLen) / 16;  // stage-2 outputs per thread
+  const int t = threadIdx.x, line = t % kLines, r = t / kLines;
   constexpr int blocks_per_outer = kLen / kLines;
   const int outer = blockIdx.x / blocks_per_outer;
   const int jb = (blockIdx.x - outer * blocks_per_outer) * kLines;
-  float2* base = grid + outer * outer_stride + jb;
-  const int j = t % kLines, n0 = t / kLines;
-  float2 v[NIN / kSweep];
+  float2* col = grid + outer * outer_stride + jb + line;
+  float2 x[16];
 #pragma unroll
-  for (int i = 0; i < NIN / kSweep; ++i) v[i] = base[(n0 + kSweep * i) * S + j];
-  load_twiddles(s, tw);
+  for (int n1 = 0; n1 < 16; ++n1) x[n1] = n1 < NIN1 ? col[(16 * n1 + r) * S] : make_float2(0.f, 0.f);
+  line_dft256<INV, true>(x, T, tw, line, r);
 #pragma unroll
-  for (int i = 0; i < NIN / kSweep; ++i) {
-    const int n = n0 + kSweep * i;
-    s.u.buf[j][n] = INV ? mul_ipow(v[i], 3 * n) : v[i];  // (-i)^n = i^(3n)
-  }
-  __syncthreads();
-  line_dft256<INV, NIN>(s, t >> 4, t & 15);
-#pragma unroll
-  for (int i = 0; i < NOUT / kSweep; ++i) {
-    const int n = n0 + kSweep * i;
-    const float2 o = s.u.buf[j][n];
-    base[n * S + j] = INV ? o : mul_ipow(o, n);
-  }
+  for (int k2 = 0; k2 < NOUT2; ++k2) col[(r + 16 * k2) * S] = x[perm16(k2)];
 }
 
-// Pass A' (adjoint): rows (i0, i1) of the grid, pre-phase, inverse DFT along
-// dim 2, the N outputs times the correction into y.
+// Pass A' (adjoint): rows (i0, i1) of the grid, inverse DFT along dim 2, the
+// N outputs times the correction into y.
 __global__ void __launch_bounds__(kThreads, kMinCtas)
     adj_rows_kernel(const float2* __restrict__ grid, const float* __restrict__ beta0, const float* __restrict__ beta1,
                     const float* __restrict__ beta2, const float2* __restrict__ tw, float2* __restrict__ y) {
-  __shared__ FftSmem s;
-  const int t = threadIdx.x;
-  const int row0 = blockIdx.x * kLines;
-  float2 v[2 * kLines];
+  __shared__ float2 T[kTSize];
+  const int t = threadIdx.x, line = t >> 4, r = t & 15;
+  const int row = blockIdx.x * kLines + line, i0 = row / kHalf, i1 = row - i0 * kHalf;
+  const float2* src = grid + ((int64_t)i0 * kLen + i1) * kLen + r;
+  float2 x[16];
 #pragma unroll
-  for (int line = 0; line < kLines; ++line) {
-    const int row = row0 + line, i0 = row / kHalf, i1 = row - i0 * kHalf;
-    const float2* src = grid + ((int64_t)i0 * kLen + i1) * kLen;
-    v[2 * line] = src[t];
-    v[2 * line + 1] = src[t + kThreads];
-  }
-  load_twiddles(s, tw);
+  for (int n1 = 0; n1 < 16; ++n1) x[n1] = src[16 * n1];
+  line_dft256<true, false>(x, T, tw, line, r);
+  const float b01 = beta0[i0] * beta1[i1];
+  float2* dst = y + (int64_t)row * kHalf + r;
 #pragma unroll
-  for (int line = 0; line < kLines; ++line) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int l = t + h * kThreads;
-      s.u.buf[line][l] = mul_ipow(v[2 * line + h], 3 * l);
-    }
-  }
-  __syncthreads();
-  line_dft256<true, kLen>(s, t >> 4, t & 15);
-  const float b2 = beta2[t];
-#pragma unroll
-  for (int line = 0; line < kLines; ++line) {
-    const int row = row0 + line, i0 = row / kHalf, i1 = row - i0 * kHalf;
-    const float b = beta0[i0] * beta1[i1] * b2;
-    const float2 o = s.u.buf[line][t];
-    y[(int64_t)row * kHalf + t] = make_float2(o.x * b, o.y * b);
-  }
+  for (int k2 = 0; k2 < 8; ++k2) dst[16 * k2] = cscale(x[perm16(k2)], b01 * beta2[r + 16 * k2]);
 }
 
-// tw[16 k1 + r] = exp(-2 pi i r k1/256), in FP64 then rounded
+// tw[16 k1 + r]       = exp(-2 pi i r k1/256) i^k1      (forward)
+// tw[256 + 16 k1 + r] = exp(+2 pi i r k1/256) (-i)^r    (inverse)
+// in FP64, then rounded.
 __global__ void build_twiddles_kernel(float2* tw) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < kLen) {
-    const int k1 = j >> 4, r = j & 15;
-    const double a = 2.0 * M_PI * (double)(r * k1) / (double)kLen;
-    tw[j] = make_float2((float)cos(a), (float)-sin(a));
+  if (j < 2 * kLen) {
+    const int inv = j >= kLen, e = j & (kLen - 1), k1 = e >> 4, r = e & 15;
+    const double turn = 2.0 * M_PI / (double)kLen;
+    const double a = inv ? turn * (double)(r * k1) - 0.5 * M_PI * (double)r
+                         : -turn * (double)(r * k1) + 0.5 * M_PI * (double)k1;
+    tw[j] = make_float2((float)cos(a), (float)sin(a));
   }
 }
 
@@ -270,7 +239,8 @@ bool pruned_fft_supported(int D, const int* N, const int* Nt) {
 }
 
 cudaError_t build_fft_twiddles(float2* tw, cudaStream_t s) {
-  build_twiddles_kernel<<<1, kLen, 0, s>>>(tw);
+  static_assert(kPrunedFftTwiddles == 2 * kLen, "twiddle table size");
+  build_twiddles_kernel<<<2, kLen, 0, s>>>(tw);
   return cudaGetLastError();
 }
 

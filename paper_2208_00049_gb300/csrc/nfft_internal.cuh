@@ -144,8 +144,9 @@ cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArray
                                   const float* poly, const void* fhat, int ctas, cudaStream_t s);
 
 // Pruned 3D FFT with the resampling correction fused in, N~_d = 2 N_d = 256,
-// complex64 (fft_pruned.cu).  `tw` holds the 256 twiddles exp(-2 pi i j/256)
-// (build_fft_twiddles); beta[d] are the FP32 correction vectors.
+// complex64 (fft_pruned.cu).  `tw` holds kPrunedFftTwiddles inter-stage
+// twiddles (build_fft_twiddles); beta[d] are the FP32 correction vectors.
+constexpr int kPrunedFftTwiddles = 512;
 bool pruned_fft_supported(int D, const int* N, const int* Nt);
 cudaError_t build_fft_twiddles(float2* tw, cudaStream_t s);
 cudaError_t launch_pruned_forward(const void* f, const float* const* beta, const float2* tw, void* grid,

@@ -564,7 +564,7 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
       Nti[d] = (int)p->Nt[d];
     }
     if (pruned_fft_supported(D, Ni, Nti)) {
-      s = dalloc(p, &p->fft_tw, sizeof(float2) * 256);
+      s = dalloc(p, &p->fft_tw, sizeof(float2) * kPrunedFftTwiddles);
       if (s == NFFT_OK) s = cuda_status(p, build_fft_twiddles(p->fft_tw, p->stream));
       p->pruned = s == NFFT_OK;
     }
