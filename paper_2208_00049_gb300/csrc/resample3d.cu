@@ -23,6 +23,7 @@
 //    added to the grid with vector global reductions;
 //  * the node records of a work item are staged in shared memory with the tile.
 #include <stdlib.h>
+#include <string.h>
 
 #include "nfft_internal.cuh"
 
@@ -327,6 +328,196 @@ __global__ void __launch_bounds__(32 * W)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-accumulating scatter.  Thread (r1, c) of the CTA's 16 x 16 owns
+// the region line (., r1, c) of the tile + halo in registers (acc[r0],
+// r0 < L0 <= 16): a node at offset (a0, a1, a2) adds
+//   v w1[r1 - a1] w2[c - a2] * w0[i0]   to acc[a0 + i0],  i0 = 0..7,
+// so the accumulation costs 8 packed FMAs per thread and node and no shared
+// memory traffic.  Register indices must be static, so the nodes of a work
+// item are counting-sorted by (a0, a1): each a0 bin runs a loop specialised
+// to its a0, and a warp, which owns rows r1 = 2w, 2w + 1, visits only the
+// contiguous run of nodes whose a1 puts one of its rows in the footprint.
+// Per work item:
+//  1. stage the node records and count them per (a0, a1) key;
+//  2. scan the counts (one warp);
+//  3. evaluate the 24 window values of every node once (POLYNOMIAL form),
+//     storing at the node's sorted slot w0 as packed pairs and w1, w2
+//     shifted to their region rows (row_d[r] = w_d[r - a_d], zero elsewhere);
+//  4. every warp runs over its node runs;
+//  5. the region is added to the grid with vector global reductions.
+constexpr int kRegAccLines = 16;                         // acc[r0], L0 <= 16
+constexpr int kRegAccThreads = 256;                      // 16 x 16 (r1, c)
+constexpr int kRegAccA = 9;                              // a_d < T_d <= 9
+constexpr int kRegAccKeys = kRegAccA * kRegAccA;         // (a0, a1)
+
+struct RegAccStage {
+  float4 rec[kItemCap][2];               // {t0, t1, t2, pk}, {re v, im v, key, rank}
+  float2 v[kItemCap];                    // by slot
+  f32x2 w0p[kItemCap][kTaps];            // (w0, w0) pairs, by slot
+  float row1[kItemCap][kRegAccLines];    // w1 shifted to region rows, by slot
+  float row2[kItemCap][kRegAccLines];    // w2 shifted to region columns, by slot
+  int count[kRegAccKeys];
+  int start[kRegAccKeys + 1];
+};
+
+template <int A0>
+__device__ __forceinline__ void regacc_bin(const RegAccStage& st, int lo, int hi, int r1, int c, f32x2* acc) {
+  const int s0 = st.start[A0 * kRegAccA + lo], s1 = st.start[A0 * kRegAccA + hi + 1];
+  for (int s = s0; s < s1; ++s) {
+    const float p = st.row1[s][r1] * st.row2[s][c];
+    const f32x2 vp = mul2(*reinterpret_cast<const f32x2*>(&st.v[s]), pack2(p, p));
+    const float4* wq = reinterpret_cast<const float4*>(&st.w0p[s][0]);
+#pragma unroll
+    for (int q = 0; q < kTaps / 2; ++q) {
+      const float4 x = wq[q];
+      acc[A0 + 2 * q] = fma2(vp, pack2(x.x, x.y), acc[A0 + 2 * q]);
+      acc[A0 + 2 * q + 1] = fma2(vp, pack2(x.z, x.w), acc[A0 + 2 * q + 1]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRegAccThreads, 3)
+    scatter3d_m4_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na,
+                               const float* __restrict__ poly, const float2* __restrict__ fhat) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RegAccStage& st = *reinterpret_cast<RegAccStage*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r1 = tid >> 4, c = tid & 15;
+  // a1 run of this warp: rows 2w, 2w + 1 lie in [a1, a1 + 8)
+  const int lo = max(0, 2 * warp - (kTaps - 1)), hi = min(kRegAccA - 1, 2 * warp + 1);
+  // weight evaluation: thread (grp, k), k = 8 d + tap, grp = 0..9
+  const int grp = tid / 24, k = tid - 24 * (tid / 24);
+  const int de = min(k >> 3, 2), tap = k & 7;
+  float coef[kCoef];
+  load_coef(poly, de, tap, coef);
+  const int nitems = *na.n_items;
+  const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+  const int64_t M = g.M;
+  const float* frac = reinterpret_cast<const float*>(na.frac);
+  for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;
+
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 item = na.items[it];
+    int tc[3], start[3];
+    tile_origin(g, item.x, tc);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
+    const int count = item.z;
+
+    __syncthreads();  // previous item done; counts cleared
+    for (int i = tid; i < count; i += kRegAccThreads) {
+      const int q = item.y + i;
+      int a[3];
+      float t[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        a[d] = na.cell[d * M + q] - tc[d] * g.T[d];
+        t[d] = frac[d * M + q];
+      }
+      const float2 v = fhat[na.perm[q]];
+      const int key = a[0] * kRegAccA + a[1];
+      const int rank = atomicAdd(&st.count[key], 1);
+      st.rec[i][0] = make_float4(t[0], t[1], t[2], __int_as_float(a[0] | (a[1] << 8) | (a[2] << 16)));
+      st.rec[i][1] = make_float4(v.x, v.y, __int_as_float(key), __int_as_float(rank));
+    }
+    {
+      float4* z1 = reinterpret_cast<float4*>(&st.row1[0][0]);
+      float4* z2 = reinterpret_cast<float4*>(&st.row2[0][0]);
+      for (int e = tid; e < count * (kRegAccLines / 4); e += kRegAccThreads) {
+        z1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        z2[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // exclusive scan of the 81 counts: lane owns keys 3 lane .. 3 lane + 2
+      int cv[3], sum = 0;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int key = 3 * lane + u;
+        cv[u] = key < kRegAccKeys ? st.count[key] : 0;
+        sum += cv[u];
+      }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int run = incl - sum;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int key = 3 * lane + u;
+        if (key <= kRegAccKeys) st.start[key] = run;
+        run += cv[u];
+      }
+    }
+    __syncthreads();
+    if (grp < 10) {
+      for (int s = grp; s < count; s += 10) {
+        const float4 r0 = st.rec[s][0];
+        const float4 rv = st.rec[s][1];
+        const int pk = __float_as_int(r0.w);
+        const int q = st.start[__float_as_int(rv.z)] + __float_as_int(rv.w);
+        const float t = de == 0 ? r0.x : (de == 1 ? r0.y : r0.z);
+        const float w = horner(coef, t - 0.5f);
+        if (de == 0) {
+          st.w0p[q][tap] = pack2(w, w);
+          if (tap == 0) st.v[q] = make_float2(rv.x, rv.y);
+        } else if (de == 1) {
+          st.row1[q][((pk >> 8) & 0xff) + tap] = w;
+        } else {
+          st.row2[q][(pk >> 16) + tap] = w;
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;  // for the next item
+
+    f32x2 acc[kRegAccLines];
+#pragma unroll
+    for (int r = 0; r < kRegAccLines; ++r) acc[r] = pack2(0.f, 0.f);
+    regacc_bin<0>(st, lo, hi, r1, c, acc);
+    regacc_bin<1>(st, lo, hi, r1, c, acc);
+    regacc_bin<2>(st, lo, hi, r1, c, acc);
+    regacc_bin<3>(st, lo, hi, r1, c, acc);
+    regacc_bin<4>(st, lo, hi, r1, c, acc);
+    regacc_bin<5>(st, lo, hi, r1, c, acc);
+    regacc_bin<6>(st, lo, hi, r1, c, acc);
+    regacc_bin<7>(st, lo, hi, r1, c, acc);
+    regacc_bin<8>(st, lo, hi, r1, c, acc);
+
+    // add the region to the grid (periodic wrap only here)
+    if (r1 < L1 && c < L2) {
+      const int g1 = wrap1(start[1] + r1, g.Nt[1]);
+      const int g2 = wrap1(start[2] + c, g.Nt[2]);
+#pragma unroll
+      for (int r = 0; r < kRegAccLines; ++r) {
+        if (r < L0) {
+          const int g0 = wrap1(start[0] + r, g.Nt[0]);
+          atomicAdd(grid + ((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + g2, unpack2(acc[r]));
+        }
+      }
+    }
+  }
+}
+
+bool regacc_supported(const Geometry& g) {
+  return g.T[0] <= 9 && g.T[1] <= 9 && g.T[2] <= 9;
+}
+
+// Scatter form: NFFT_GB300_SCATTER=smem selects the shared-accumulator
+// kernel below, anything else the register-accumulating one (where the tile
+// allows it).
+bool use_regacc(const Geometry& g) {
+  static int smem_form = [] {
+    const char* e = getenv("NFFT_GB300_SCATTER");
+    return (e && strcmp(e, "smem") == 0) ? 1 : 0;
+  }();
+  return !smem_form && regacc_supported(g);
+}
+
 int gather_warps() {
   static int w = [] {
     const char* e = getenv("NFFT_GB300_GATHER_WARPS");
@@ -384,6 +575,14 @@ bool fast3d_supported(const Geometry& g, int cmax) {
 }
 
 int fast3d_ctas_per_sm(const Geometry& g, int kind) {
+  if (kind == 1 && use_regacc(g)) {
+    const size_t smem = sizeof(RegAccStage);
+    void* k = (void*)scatter3d_m4_regacc_kernel;
+    if (set_smem(k, smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
+    return n;
+  }
   const size_t smem = smem_bytes(g);
   void* k = kind == 0 ? gather_kernel_for(gather_warps()) : scatter_kernel_for(scatter_warps());
   const int threads = kind == 0 ? 32 * gather_warps() : 32 * scatter_warps();
@@ -407,6 +606,13 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
 
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
                                   const float* poly, const void* fhat, int ctas, cudaStream_t s) {
+  if (use_regacc(g)) {
+    const size_t smem = sizeof(RegAccStage);
+    cudaError_t e = set_smem(scatter3d_m4_regacc_kernel, smem);
+    if (e != cudaSuccess) return e;
+    scatter3d_m4_regacc_kernel<<<ctas, kRegAccThreads, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
+    return cudaGetLastError();
+  }
   const size_t smem = smem_bytes(g);
   const int w = scatter_warps();
   void* k = scatter_kernel_for(w);
