@@ -329,25 +329,27 @@ __global__ void __launch_bounds__(32 * W)
 }
 
 // ---------------------------------------------------------------------------
-// Register-accumulating scatter.  Thread (r1, c) of the CTA's 16 x 16 owns
-// the region line (., r1, c) of the tile + halo in registers (acc[r0],
-// r0 < L0 <= 16): a node at offset (a0, a1, a2) adds
-//   v w1[r1 - a1] w2[c - a2] * w0[i0]   to acc[a0 + i0],  i0 = 0..7,
-// so the accumulation costs 8 packed FMAs per thread and node and no shared
-// memory traffic.  Register indices must be static, so the nodes of a work
-// item are counting-sorted by (a0, a1): each a0 bin runs a loop specialised
-// to its a0, and a warp, which owns rows r1 = 2w, 2w + 1, visits only the
-// contiguous run of nodes whose a1 puts one of its rows in the footprint.
+// Register-accumulating scatter.  Each thread owns CPT region lines
+// (., r1, c) of the tile + halo in registers (acc[h][r0], r0 < L0 <= 16): a
+// node at offset (a0, a1, a2) adds
+//   v w1[r1 - a1] w2[c - a2] * w0[i0]   to acc[h][a0 + i0],  i0 = 0..7,
+// so the accumulation costs 8 CPT packed FMAs per thread and node and no
+// shared-memory traffic.  Register indices must be static, so the nodes of a
+// work item are counting-sorted by (a0, a1): each a0 bin runs a loop
+// specialised to its a0, and a warp, which owns 2 CPT consecutive rows r1,
+// visits only the contiguous run of nodes whose a1 puts one of its rows in
+// the footprint.  Thread layout: 16/CPT threads per row r1, thread cc of a
+// row owning columns c = cc + (16/CPT) h, h < CPT.
 // Per work item:
 //  1. stage the node records and count them per (a0, a1) key;
 //  2. scan the counts (one warp);
 //  3. evaluate the 24 window values of every node once (POLYNOMIAL form),
 //     storing at the node's sorted slot w0 as packed pairs and w1, w2
-//     shifted to their region rows (row_d[r] = w_d[r - a_d], zero elsewhere);
+//     shifted to their region rows (row_d[r] = w_d[r - a_d], zero elsewhere;
+//     row2 in the thread-column order cc CPT + h);
 //  4. every warp runs over its node runs;
 //  5. the region is added to the grid with vector global reductions.
 constexpr int kRegAccLines = 16;                         // acc[r0], L0 <= 16
-constexpr int kRegAccThreads = 256;                      // 16 x 16 (r1, c)
 constexpr int kRegAccA = 9;                              // a_d < T_d <= 9
 constexpr int kRegAccKeys = kRegAccA * kRegAccA;         // (a0, a1)
 
@@ -361,41 +363,91 @@ struct RegAccStage {
   int start[kRegAccKeys + 1];
 };
 
-template <int A0>
-__device__ __forceinline__ void regacc_bin(const RegAccStage& st, int lo, int hi, int r1, int c, f32x2* acc) {
-  const int s0 = st.start[A0 * kRegAccA + lo], s1 = st.start[A0 * kRegAccA + hi + 1];
-  for (int s = s0; s < s1; ++s) {
-    const float p = st.row1[s][r1] * st.row2[s][c];
-    const f32x2 vp = mul2(*reinterpret_cast<const f32x2*>(&st.v[s]), pack2(p, p));
-    const float4* wq = reinterpret_cast<const float4*>(&st.w0p[s][0]);
+template <int CPT>
+struct RegAccLayout {
+  static constexpr int kThreads = 256 / CPT;
+  static constexpr int kPerRow = 16 / CPT;   // threads per row r1
+  static constexpr int kRowsPerWarp = 32 / kPerRow;
+};
+
+template <int A0, int CPT>
+__device__ __forceinline__ void regacc_node(const RegAccStage& st, int s, int r1, int cc,
+                                            f32x2 (&acc)[CPT][kRegAccLines]) {
+  const float w1 = st.row1[s][r1];
+  float w2[CPT];
+  if constexpr (CPT == 1) {
+    w2[0] = st.row2[s][cc];
+  } else {
+    const float2 q = *reinterpret_cast<const float2*>(&st.row2[s][2 * cc]);
+    w2[0] = q.x;
+    w2[1] = q.y;
+  }
+  const f32x2 v = *reinterpret_cast<const f32x2*>(&st.v[s]);
+  f32x2 vp[CPT];
 #pragma unroll
-    for (int q = 0; q < kTaps / 2; ++q) {
-      const float4 x = wq[q];
-      acc[A0 + 2 * q] = fma2(vp, pack2(x.x, x.y), acc[A0 + 2 * q]);
-      acc[A0 + 2 * q + 1] = fma2(vp, pack2(x.z, x.w), acc[A0 + 2 * q + 1]);
+  for (int h = 0; h < CPT; ++h) {
+    const float p = w1 * w2[h];
+    vp[h] = mul2(v, pack2(p, p));
+  }
+  const float4* wq = reinterpret_cast<const float4*>(&st.w0p[s][0]);
+#pragma unroll
+  for (int q = 0; q < kTaps / 2; ++q) {
+    const float4 x = wq[q];
+    const f32x2 wa = pack2(x.x, x.y), wb = pack2(x.z, x.w);
+#pragma unroll
+    for (int h = 0; h < CPT; ++h) {
+      acc[h][A0 + 2 * q] = fma2(vp[h], wa, acc[h][A0 + 2 * q]);
+      acc[h][A0 + 2 * q + 1] = fma2(vp[h], wb, acc[h][A0 + 2 * q + 1]);
     }
   }
 }
 
-__global__ void __launch_bounds__(kRegAccThreads, 3)
+template <int A0, int CPT>
+__device__ __forceinline__ void regacc_bin(const RegAccStage& st, int lo, int hi, int r1, int cc,
+                                           f32x2 (&acc)[CPT][kRegAccLines]) {
+  const int s0 = st.start[A0 * kRegAccA + lo], s1 = st.start[A0 * kRegAccA + hi + 1];
+  int s = s0;
+  for (; s + 1 < s1; s += 2) {
+    regacc_node<A0, CPT>(st, s, r1, cc, acc);
+    regacc_node<A0, CPT>(st, s + 1, r1, cc, acc);
+  }
+  if (s < s1) regacc_node<A0, CPT>(st, s, r1, cc, acc);
+}
+
+template <int CPT, int MINCTAS>
+__global__ void __launch_bounds__(RegAccLayout<CPT>::kThreads, MINCTAS)
     scatter3d_m4_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na,
                                const float* __restrict__ poly, const float2* __restrict__ fhat) {
+  using Lay = RegAccLayout<CPT>;
+  constexpr int kThreads = Lay::kThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RegAccStage& st = *reinterpret_cast<RegAccStage*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int r1 = tid >> 4, c = tid & 15;
-  // a1 run of this warp: rows 2w, 2w + 1 lie in [a1, a1 + 8)
-  const int lo = max(0, 2 * warp - (kTaps - 1)), hi = min(kRegAccA - 1, 2 * warp + 1);
-  // weight evaluation: thread (grp, k), k = 8 d + tap, grp = 0..9
-  const int grp = tid / 24, k = tid - 24 * (tid / 24);
-  const int de = min(k >> 3, 2), tap = k & 7;
-  float coef[kCoef];
-  load_coef(poly, de, tap, coef);
+  const int r1 = tid / Lay::kPerRow, cc = tid % Lay::kPerRow;
+  // a1 run of this warp: one of rows R w .. R w + R - 1 lies in [a1, a1 + 8)
+  const int R = Lay::kRowsPerWarp;
+  const int lo = max(0, R * warp - (kTaps - 1)), hi = min(kRegAccA - 1, R * warp + R - 1);
+  // weight evaluation: warp w takes dimension w mod 3 (warp-uniform), the
+  // wgrp warps of one dimension splitting the nodes; lane & 3 owns taps
+  // 2 (lane & 3) and 2 (lane & 3) + 1, their coefficients as packed pairs
+  constexpr int kWarps = kThreads / 32;
+  const int wdim = warp < 3 * (kWarps / 3) + (kWarps % 3) ? warp % 3 : -1;
+  const int wgi = warp / 3;
+  const int wgrp = kWarps / 3 + ((warp % 3) < (kWarps % 3) ? 1 : 0);
+  f32x2 cpair[kCoef];
+  {
+    float ca[kCoef], cb[kCoef];
+    const int d = wdim < 0 ? 0 : wdim, tp = lane & 3;
+    load_coef(poly, d, 2 * tp, ca);
+    load_coef(poly, d, 2 * tp + 1, cb);
+#pragma unroll
+    for (int e = 0; e < kCoef; ++e) cpair[e] = pack2(ca[e], cb[e]);
+  }
   const int nitems = *na.n_items;
   const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
   const int64_t M = g.M;
   const float* frac = reinterpret_cast<const float*>(na.frac);
-  for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;
+  for (int e = tid; e < kRegAccKeys; e += kThreads) st.count[e] = 0;
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 item = na.items[it];
@@ -406,7 +458,7 @@ __global__ void __launch_bounds__(kRegAccThreads, 3)
     const int count = item.z;
 
     __syncthreads();  // previous item done; counts cleared
-    for (int i = tid; i < count; i += kRegAccThreads) {
+    for (int i = tid; i < count; i += kThreads) {
       const int q = item.y + i;
       int a[3];
       float t[3];
@@ -424,7 +476,7 @@ __global__ void __launch_bounds__(kRegAccThreads, 3)
     {
       float4* z1 = reinterpret_cast<float4*>(&st.row1[0][0]);
       float4* z2 = reinterpret_cast<float4*>(&st.row2[0][0]);
-      for (int e = tid; e < count * (kRegAccLines / 4); e += kRegAccThreads) {
+      for (int e = tid; e < count * (kRegAccLines / 4); e += kThreads) {
         z1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         z2[e] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -454,52 +506,91 @@ __global__ void __launch_bounds__(kRegAccThreads, 3)
       }
     }
     __syncthreads();
-    if (grp < 10) {
-      for (int s = grp; s < count; s += 10) {
+    if (wdim >= 0) {
+      // warp (wdim, wgi): lane (j, tp) evaluates taps 2 tp, 2 tp + 1 of
+      // dimension wdim for nodes s = 8 (wgi + wgrp it) + j
+      const int j = lane >> 2, tp = lane & 3;
+      for (int s = 8 * wgi + j; s < count; s += 8 * wgrp) {
         const float4 r0 = st.rec[s][0];
         const float4 rv = st.rec[s][1];
         const int pk = __float_as_int(r0.w);
         const int q = st.start[__float_as_int(rv.z)] + __float_as_int(rv.w);
-        const float t = de == 0 ? r0.x : (de == 1 ? r0.y : r0.z);
-        const float w = horner(coef, t - 0.5f);
-        if (de == 0) {
-          st.w0p[q][tap] = pack2(w, w);
-          if (tap == 0) st.v[q] = make_float2(rv.x, rv.y);
-        } else if (de == 1) {
-          st.row1[q][((pk >> 8) & 0xff) + tap] = w;
+        const float t = wdim == 0 ? r0.x : (wdim == 1 ? r0.y : r0.z);
+        const float z = t - 0.5f;
+        const f32x2 zz = pack2(z, z);
+        f32x2 pw = cpair[kDeg];
+#pragma unroll
+        for (int e = kDeg - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[e]);
+        const float2 w = unpack2(pw);  // taps 2 tp, 2 tp + 1
+        if (wdim == 0) {
+          *reinterpret_cast<float4*>(&st.w0p[q][2 * tp]) = make_float4(w.x, w.x, w.y, w.y);
+          if (tp == 0) st.v[q] = make_float2(rv.x, rv.y);
+        } else if (wdim == 1) {
+          const int r = ((pk >> 8) & 0xff) + 2 * tp;
+          st.row1[q][r] = w.x;
+          st.row1[q][r + 1] = w.y;
         } else {
-          st.row2[q][(pk >> 16) + tap] = w;
+          const int c0 = (pk >> 16) + 2 * tp, c1 = c0 + 1;
+          st.row2[q][(c0 % Lay::kPerRow) * CPT + c0 / Lay::kPerRow] = w.x;
+          st.row2[q][(c1 % Lay::kPerRow) * CPT + c1 / Lay::kPerRow] = w.y;
         }
       }
     }
     __syncthreads();
-    for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;  // for the next item
+    for (int e = tid; e < kRegAccKeys; e += kThreads) st.count[e] = 0;  // for the next item
 
-    f32x2 acc[kRegAccLines];
+    f32x2 acc[CPT][kRegAccLines];
 #pragma unroll
-    for (int r = 0; r < kRegAccLines; ++r) acc[r] = pack2(0.f, 0.f);
-    regacc_bin<0>(st, lo, hi, r1, c, acc);
-    regacc_bin<1>(st, lo, hi, r1, c, acc);
-    regacc_bin<2>(st, lo, hi, r1, c, acc);
-    regacc_bin<3>(st, lo, hi, r1, c, acc);
-    regacc_bin<4>(st, lo, hi, r1, c, acc);
-    regacc_bin<5>(st, lo, hi, r1, c, acc);
-    regacc_bin<6>(st, lo, hi, r1, c, acc);
-    regacc_bin<7>(st, lo, hi, r1, c, acc);
-    regacc_bin<8>(st, lo, hi, r1, c, acc);
+    for (int h = 0; h < CPT; ++h)
+#pragma unroll
+      for (int r = 0; r < kRegAccLines; ++r) acc[h][r] = pack2(0.f, 0.f);
+    regacc_bin<0, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<1, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<2, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<3, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<4, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<5, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<6, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<7, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<8, CPT>(st, lo, hi, r1, cc, acc);
 
     // add the region to the grid (periodic wrap only here)
-    if (r1 < L1 && c < L2) {
-      const int g1 = wrap1(start[1] + r1, g.Nt[1]);
-      const int g2 = wrap1(start[2] + c, g.Nt[2]);
 #pragma unroll
-      for (int r = 0; r < kRegAccLines; ++r) {
-        if (r < L0) {
-          const int g0 = wrap1(start[0] + r, g.Nt[0]);
-          atomicAdd(grid + ((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + g2, unpack2(acc[r]));
+    for (int h = 0; h < CPT; ++h) {
+      const int c = cc + Lay::kPerRow * h;
+      if (r1 < L1 && c < L2) {
+        const int g1 = wrap1(start[1] + r1, g.Nt[1]);
+        const int g2 = wrap1(start[2] + c, g.Nt[2]);
+#pragma unroll
+        for (int r = 0; r < kRegAccLines; ++r) {
+          if (r < L0) {
+            const int g0 = wrap1(start[0] + r, g.Nt[0]);
+            atomicAdd(grid + ((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + g2, unpack2(acc[h][r]));
+          }
         }
       }
     }
+  }
+}
+
+// Variant (columns per thread, CTAs per SM the register cap targets):
+// NFFT_GB300_SCATTER_CPT = 1 (1, 3), 2 (2, 5), 24 (2, 4; default).  At the
+// 3D 128^3 workload: 691, 670 and 619 us.
+int regacc_variant() {
+  static int v = [] {
+    const char* e = getenv("NFFT_GB300_SCATTER_CPT");
+    const int x = e ? atoi(e) : 24;
+    return (x == 1 || x == 2 || x == 24) ? x : 24;
+  }();
+  return v;
+}
+int regacc_cpt() { return regacc_variant() == 1 ? 1 : 2; }
+
+void* regacc_kernel_for(int) {
+  switch (regacc_variant()) {
+    case 1: return (void*)scatter3d_m4_regacc_kernel<1, 3>;
+    case 24: return (void*)scatter3d_m4_regacc_kernel<2, 4>;
+    default: return (void*)scatter3d_m4_regacc_kernel<2, 5>;
   }
 }
 
@@ -577,10 +668,11 @@ bool fast3d_supported(const Geometry& g, int cmax) {
 int fast3d_ctas_per_sm(const Geometry& g, int kind) {
   if (kind == 1 && use_regacc(g)) {
     const size_t smem = sizeof(RegAccStage);
-    void* k = (void*)scatter3d_m4_regacc_kernel;
+    const int cpt = regacc_cpt();
+    void* k = regacc_kernel_for(cpt);
     if (set_smem(k, smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256 / cpt, smem) != cudaSuccess) return 0;
     return n;
   }
   const size_t smem = smem_bytes(g);
@@ -608,9 +700,12 @@ cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArray
                                   const float* poly, const void* fhat, int ctas, cudaStream_t s) {
   if (use_regacc(g)) {
     const size_t smem = sizeof(RegAccStage);
-    cudaError_t e = set_smem(scatter3d_m4_regacc_kernel, smem);
+    const int cpt = regacc_cpt();
+    void* k = regacc_kernel_for(cpt);
+    cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
-    scatter3d_m4_regacc_kernel<<<ctas, kRegAccThreads, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
+    auto kern = reinterpret_cast<void (*)(Geometry, float2*, NodeArrays, const float*, const float2*)>(k);
+    kern<<<ctas, 256 / cpt, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
     return cudaGetLastError();
   }
   const size_t smem = smem_bytes(g);
