@@ -329,125 +329,94 @@ __global__ void __launch_bounds__(32 * W)
 }
 
 // ---------------------------------------------------------------------------
-// Register-accumulating scatter.  Each thread owns CPT region lines
-// (., r1, c) of the tile + halo in registers (acc[h][r0], r0 < L0 <= 16): a
-// node at offset (a0, a1, a2) adds
+// Register-accumulating scatter.  Thread (r1, cc) of a 128-thread CTA owns
+// the two region lines (., r1, cc) and (., r1, cc + 8) of the tile + halo in
+// registers (acc[h][r0], r0 < L0 <= 16): a node at offset (a0, a1, a2) adds
 //   v w1[r1 - a1] w2[c - a2] * w0[i0]   to acc[h][a0 + i0],  i0 = 0..7,
-// so the accumulation costs 8 CPT packed FMAs per thread and node and no
-// shared-memory traffic.  Register indices must be static, so the nodes of a
-// work item are counting-sorted by (a0, a1): each a0 bin runs a loop
-// specialised to its a0, and a warp, which owns 2 CPT consecutive rows r1,
+// c = cc + 8 h, so the accumulation costs 16 packed FMAs per thread and node
+// and no shared-memory traffic.  Register indices must be static, so the
+// nodes of a work item are counting-sorted by (a0, a1): each a0 bin runs a
+// loop specialised to its a0, and a warp, which owns rows 4w .. 4w + 3,
 // visits only the contiguous run of nodes whose a1 puts one of its rows in
-// the footprint.  Thread layout: 16/CPT threads per row r1, thread cc of a
-// row owning columns c = cc + (16/CPT) h, h < CPT.
-// Per work item:
+// the footprint.  Per work item:
 //  1. stage the node records and count them per (a0, a1) key;
 //  2. scan the counts (one warp);
-//  3. evaluate the 24 window values of every node once (POLYNOMIAL form),
-//     storing at the node's sorted slot w0 as packed pairs and w1, w2
-//     shifted to their region rows (row_d[r] = w_d[r - a_d], zero elsewhere;
-//     row2 in the thread-column order cc CPT + h);
+//  3. evaluate the 24 window values of every node once (POLYNOMIAL form; a
+//     lane takes two taps of all three dimensions with packed Horner steps)
+//     and store, at the node's sorted slot and shifted to region
+//     coordinates: w0 as packed pairs, v w1 per row, w2 as packed pairs per
+//     thread column pair (zero outside the footprint);
 //  4. every warp runs over its node runs;
 //  5. the region is added to the grid with vector global reductions.
-constexpr int kRegAccLines = 16;                         // acc[r0], L0 <= 16
-constexpr int kRegAccA = 9;                              // a_d < T_d <= 9
-constexpr int kRegAccKeys = kRegAccA * kRegAccA;         // (a0, a1)
+constexpr int kRegAccLines = 16;                   // acc[h][r0], L0 <= 16
+constexpr int kRegAccThreads = 128;                // 16 rows r1 x 8 column pairs
+constexpr int kRegAccWarps = kRegAccThreads / 32;  // warp w owns rows 4w .. 4w + 3
+constexpr int kRegAccA = 9;                        // a_d < T_d <= 9
+constexpr int kRegAccKeys = kRegAccA * kRegAccA;   // (a0, a1)
 
 struct RegAccStage {
   float4 rec[kItemCap][2];               // {t0, t1, t2, pk}, {re v, im v, key, rank}
-  float2 v[kItemCap];                    // by slot
-  f32x2 w0p[kItemCap][kTaps];            // (w0, w0) pairs, by slot
-  float row1[kItemCap][kRegAccLines];    // w1 shifted to region rows, by slot
-  float row2[kItemCap][kRegAccLines];    // w2 shifted to region columns, by slot
+  f32x2 w0p[kItemCap][kTaps];            // (w0, w0), by slot
+  f32x2 vw1[kItemCap][kRegAccLines];     // v w1[r - a1], by slot
+  float4 w2p[kItemCap][8];               // cc -> (w2[cc - a2] x2, w2[cc + 8 - a2] x2), by slot
   int count[kRegAccKeys];
   int start[kRegAccKeys + 1];
+  f32x2 coef[3][4][kCoef];               // (tap 2 tp, tap 2 tp + 1) coefficient pairs
 };
 
-template <int CPT>
-struct RegAccLayout {
-  static constexpr int kThreads = 256 / CPT;
-  static constexpr int kPerRow = 16 / CPT;   // threads per row r1
-  static constexpr int kRowsPerWarp = 32 / kPerRow;
-};
-
-template <int A0, int CPT>
+template <int A0>
 __device__ __forceinline__ void regacc_node(const RegAccStage& st, int s, int r1, int cc,
-                                            f32x2 (&acc)[CPT][kRegAccLines]) {
-  const float w1 = st.row1[s][r1];
-  float w2[CPT];
-  if constexpr (CPT == 1) {
-    w2[0] = st.row2[s][cc];
-  } else {
-    const float2 q = *reinterpret_cast<const float2*>(&st.row2[s][2 * cc]);
-    w2[0] = q.x;
-    w2[1] = q.y;
-  }
-  const f32x2 v = *reinterpret_cast<const f32x2*>(&st.v[s]);
-  f32x2 vp[CPT];
-#pragma unroll
-  for (int h = 0; h < CPT; ++h) {
-    const float p = w1 * w2[h];
-    vp[h] = mul2(v, pack2(p, p));
-  }
+                                            f32x2 (&acc)[2][kRegAccLines]) {
+  const f32x2 vw = st.vw1[s][r1];
+  const float4 w2 = st.w2p[s][cc];
+  const f32x2 vp0 = mul2(vw, pack2(w2.x, w2.y));
+  const f32x2 vp1 = mul2(vw, pack2(w2.z, w2.w));
   const float4* wq = reinterpret_cast<const float4*>(&st.w0p[s][0]);
 #pragma unroll
   for (int q = 0; q < kTaps / 2; ++q) {
     const float4 x = wq[q];
     const f32x2 wa = pack2(x.x, x.y), wb = pack2(x.z, x.w);
-#pragma unroll
-    for (int h = 0; h < CPT; ++h) {
-      acc[h][A0 + 2 * q] = fma2(vp[h], wa, acc[h][A0 + 2 * q]);
-      acc[h][A0 + 2 * q + 1] = fma2(vp[h], wb, acc[h][A0 + 2 * q + 1]);
-    }
+    acc[0][A0 + 2 * q] = fma2(vp0, wa, acc[0][A0 + 2 * q]);
+    acc[0][A0 + 2 * q + 1] = fma2(vp0, wb, acc[0][A0 + 2 * q + 1]);
+    acc[1][A0 + 2 * q] = fma2(vp1, wa, acc[1][A0 + 2 * q]);
+    acc[1][A0 + 2 * q + 1] = fma2(vp1, wb, acc[1][A0 + 2 * q + 1]);
   }
 }
 
-template <int A0, int CPT>
+template <int A0>
 __device__ __forceinline__ void regacc_bin(const RegAccStage& st, int lo, int hi, int r1, int cc,
-                                           f32x2 (&acc)[CPT][kRegAccLines]) {
+                                           f32x2 (&acc)[2][kRegAccLines]) {
   const int s0 = st.start[A0 * kRegAccA + lo], s1 = st.start[A0 * kRegAccA + hi + 1];
   int s = s0;
   for (; s + 1 < s1; s += 2) {
-    regacc_node<A0, CPT>(st, s, r1, cc, acc);
-    regacc_node<A0, CPT>(st, s + 1, r1, cc, acc);
+    regacc_node<A0>(st, s, r1, cc, acc);
+    regacc_node<A0>(st, s + 1, r1, cc, acc);
   }
-  if (s < s1) regacc_node<A0, CPT>(st, s, r1, cc, acc);
+  if (s < s1) regacc_node<A0>(st, s, r1, cc, acc);
 }
 
-template <int CPT, int MINCTAS>
-__global__ void __launch_bounds__(RegAccLayout<CPT>::kThreads, MINCTAS)
+__global__ void __launch_bounds__(kRegAccThreads, 4)
     scatter3d_m4_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na,
                                const float* __restrict__ poly, const float2* __restrict__ fhat) {
-  using Lay = RegAccLayout<CPT>;
-  constexpr int kThreads = Lay::kThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RegAccStage& st = *reinterpret_cast<RegAccStage*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int r1 = tid / Lay::kPerRow, cc = tid % Lay::kPerRow;
-  // a1 run of this warp: one of rows R w .. R w + R - 1 lies in [a1, a1 + 8)
-  const int R = Lay::kRowsPerWarp;
-  const int lo = max(0, R * warp - (kTaps - 1)), hi = min(kRegAccA - 1, R * warp + R - 1);
-  // weight evaluation: warp w takes dimension w mod 3 (warp-uniform), the
-  // wgrp warps of one dimension splitting the nodes; lane & 3 owns taps
-  // 2 (lane & 3) and 2 (lane & 3) + 1, their coefficients as packed pairs
-  constexpr int kWarps = kThreads / 32;
-  const int wdim = warp < 3 * (kWarps / 3) + (kWarps % 3) ? warp % 3 : -1;
-  const int wgi = warp / 3;
-  const int wgrp = kWarps / 3 + ((warp % 3) < (kWarps % 3) ? 1 : 0);
-  f32x2 cpair[kCoef];
-  {
-    float ca[kCoef], cb[kCoef];
-    const int d = wdim < 0 ? 0 : wdim, tp = lane & 3;
-    load_coef(poly, d, 2 * tp, ca);
-    load_coef(poly, d, 2 * tp + 1, cb);
-#pragma unroll
-    for (int e = 0; e < kCoef; ++e) cpair[e] = pack2(ca[e], cb[e]);
+  const int r1 = tid >> 3, cc = tid & 7;
+  // a1 run of this warp: one of rows 4w .. 4w + 3 lies in [a1, a1 + 8)
+  const int lo = max(0, 4 * warp - (kTaps - 1)), hi = min(kRegAccA - 1, 4 * warp + 3);
+  // weight evaluation: lane (j, tp) takes taps 2 tp, 2 tp + 1 of every
+  // dimension for nodes 8 (warp + 4 it) + j; coefficients as packed pairs,
+  // kept in shared memory between items
+  const int wj = lane >> 2, tp = lane & 3;
+  for (int e = tid; e < 3 * 4 * kCoef; e += kRegAccThreads) {
+    const int d = e / (4 * kCoef), p = (e / kCoef) % 4, z = e % kCoef;
+    st.coef[d][p][z] = pack2(poly[(d * kTaps + 2 * p) * kCoef + z], poly[(d * kTaps + 2 * p + 1) * kCoef + z]);
   }
   const int nitems = *na.n_items;
   const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
   const int64_t M = g.M;
   const float* frac = reinterpret_cast<const float*>(na.frac);
-  for (int e = tid; e < kRegAccKeys; e += kThreads) st.count[e] = 0;
+  for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 item = na.items[it];
@@ -458,7 +427,7 @@ __global__ void __launch_bounds__(RegAccLayout<CPT>::kThreads, MINCTAS)
     const int count = item.z;
 
     __syncthreads();  // previous item done; counts cleared
-    for (int i = tid; i < count; i += kThreads) {
+    for (int i = tid; i < count; i += kRegAccThreads) {
       const int q = item.y + i;
       int a[3];
       float t[3];
@@ -474,9 +443,10 @@ __global__ void __launch_bounds__(RegAccLayout<CPT>::kThreads, MINCTAS)
       st.rec[i][1] = make_float4(v.x, v.y, __int_as_float(key), __int_as_float(rank));
     }
     {
-      float4* z1 = reinterpret_cast<float4*>(&st.row1[0][0]);
-      float4* z2 = reinterpret_cast<float4*>(&st.row2[0][0]);
-      for (int e = tid; e < count * (kRegAccLines / 4); e += kThreads) {
+      // clear the shifted rows of the slots in use (vw1 and w2p: 8 float4 each per slot)
+      float4* z1 = reinterpret_cast<float4*>(&st.vw1[0][0]);
+      float4* z2 = &st.w2p[0][0];
+      for (int e = tid; e < count * 8; e += kRegAccThreads) {
         z1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         z2[e] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -506,58 +476,58 @@ __global__ void __launch_bounds__(RegAccLayout<CPT>::kThreads, MINCTAS)
       }
     }
     __syncthreads();
-    if (wdim >= 0) {
-      // warp (wdim, wgi): lane (j, tp) evaluates taps 2 tp, 2 tp + 1 of
-      // dimension wdim for nodes s = 8 (wgi + wgrp it) + j
-      const int j = lane >> 2, tp = lane & 3;
-      for (int s = 8 * wgi + j; s < count; s += 8 * wgrp) {
-        const float4 r0 = st.rec[s][0];
-        const float4 rv = st.rec[s][1];
-        const int pk = __float_as_int(r0.w);
-        const int q = st.start[__float_as_int(rv.z)] + __float_as_int(rv.w);
-        const float t = wdim == 0 ? r0.x : (wdim == 1 ? r0.y : r0.z);
-        const float z = t - 0.5f;
-        const f32x2 zz = pack2(z, z);
-        f32x2 pw = cpair[kDeg];
+    f32x2 cpair[3][kCoef];
 #pragma unroll
-        for (int e = kDeg - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[e]);
-        const float2 w = unpack2(pw);  // taps 2 tp, 2 tp + 1
-        if (wdim == 0) {
-          *reinterpret_cast<float4*>(&st.w0p[q][2 * tp]) = make_float4(w.x, w.x, w.y, w.y);
-          if (tp == 0) st.v[q] = make_float2(rv.x, rv.y);
-        } else if (wdim == 1) {
-          const int r = ((pk >> 8) & 0xff) + 2 * tp;
-          st.row1[q][r] = w.x;
-          st.row1[q][r + 1] = w.y;
-        } else {
-          const int c0 = (pk >> 16) + 2 * tp, c1 = c0 + 1;
-          st.row2[q][(c0 % Lay::kPerRow) * CPT + c0 / Lay::kPerRow] = w.x;
-          st.row2[q][(c1 % Lay::kPerRow) * CPT + c1 / Lay::kPerRow] = w.y;
-        }
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int e = 0; e < kCoef; ++e) cpair[d][e] = st.coef[d][tp][e];
+    for (int s = 8 * warp + wj; s < count; s += 8 * kRegAccWarps) {
+      const float4 r0 = st.rec[s][0];
+      const float4 rv = st.rec[s][1];
+      const int pk = __float_as_int(r0.w);
+      const int q = st.start[__float_as_int(rv.z)] + __float_as_int(rv.w);
+      float2 w[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float z = (d == 0 ? r0.x : (d == 1 ? r0.y : r0.z)) - 0.5f;
+        const f32x2 zz = pack2(z, z);
+        f32x2 pw = cpair[d][kDeg];
+#pragma unroll
+        for (int e = kDeg - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[d][e]);
+        w[d] = unpack2(pw);  // taps 2 tp, 2 tp + 1
       }
+      *reinterpret_cast<float4*>(&st.w0p[q][2 * tp]) = make_float4(w[0].x, w[0].x, w[0].y, w[0].y);
+      const int r = ((pk >> 8) & 0xff) + 2 * tp;
+      st.vw1[q][r] = pack2(rv.x * w[1].x, rv.y * w[1].x);
+      st.vw1[q][r + 1] = pack2(rv.x * w[1].y, rv.y * w[1].y);
+      // column c sits in pair cc = c & 7, half c >> 3 (two copies)
+      const int c0 = (pk >> 16) + 2 * tp, c1 = c0 + 1;
+      float* w2f = reinterpret_cast<float*>(&st.w2p[q][0]);
+      *reinterpret_cast<float2*>(&w2f[4 * (c0 & 7) + 2 * (c0 >> 3)]) = make_float2(w[2].x, w[2].x);
+      *reinterpret_cast<float2*>(&w2f[4 * (c1 & 7) + 2 * (c1 >> 3)]) = make_float2(w[2].y, w[2].y);
     }
     __syncthreads();
-    for (int e = tid; e < kRegAccKeys; e += kThreads) st.count[e] = 0;  // for the next item
+    for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;  // for the next item
 
-    f32x2 acc[CPT][kRegAccLines];
+    f32x2 acc[2][kRegAccLines];
 #pragma unroll
-    for (int h = 0; h < CPT; ++h)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int r = 0; r < kRegAccLines; ++r) acc[h][r] = pack2(0.f, 0.f);
-    regacc_bin<0, CPT>(st, lo, hi, r1, cc, acc);
-    regacc_bin<1, CPT>(st, lo, hi, r1, cc, acc);
-    regacc_bin<2, CPT>(st, lo, hi, r1, cc, acc);
-    regacc_bin<3, CPT>(st, lo, hi, r1, cc, acc);
-    regacc_bin<4, CPT>(st, lo, hi, r1, cc, acc);
-    regacc_bin<5, CPT>(st, lo, hi, r1, cc, acc);
-    regacc_bin<6, CPT>(st, lo, hi, r1, cc, acc);
-    regacc_bin<7, CPT>(st, lo, hi, r1, cc, acc);
-    regacc_bin<8, CPT>(st, lo, hi, r1, cc, acc);
+    regacc_bin<0>(st, lo, hi, r1, cc, acc);
+    regacc_bin<1>(st, lo, hi, r1, cc, acc);
+    regacc_bin<2>(st, lo, hi, r1, cc, acc);
+    regacc_bin<3>(st, lo, hi, r1, cc, acc);
+    regacc_bin<4>(st, lo, hi, r1, cc, acc);
+    regacc_bin<5>(st, lo, hi, r1, cc, acc);
+    regacc_bin<6>(st, lo, hi, r1, cc, acc);
+    regacc_bin<7>(st, lo, hi, r1, cc, acc);
+    regacc_bin<8>(st, lo, hi, r1, cc, acc);
 
     // add the region to the grid (periodic wrap only here)
 #pragma unroll
-    for (int h = 0; h < CPT; ++h) {
-      const int c = cc + Lay::kPerRow * h;
+    for (int h = 0; h < 2; ++h) {
+      const int c = cc + 8 * h;
       if (r1 < L1 && c < L2) {
         const int g1 = wrap1(start[1] + r1, g.Nt[1]);
         const int g2 = wrap1(start[2] + c, g.Nt[2]);
@@ -570,27 +540,6 @@ __global__ void __launch_bounds__(RegAccLayout<CPT>::kThreads, MINCTAS)
         }
       }
     }
-  }
-}
-
-// Variant (columns per thread, CTAs per SM the register cap targets):
-// NFFT_GB300_SCATTER_CPT = 1 (1, 3), 2 (2, 5), 24 (2, 4; default).  At the
-// 3D 128^3 workload: 691, 670 and 619 us.
-int regacc_variant() {
-  static int v = [] {
-    const char* e = getenv("NFFT_GB300_SCATTER_CPT");
-    const int x = e ? atoi(e) : 24;
-    return (x == 1 || x == 2 || x == 24) ? x : 24;
-  }();
-  return v;
-}
-int regacc_cpt() { return regacc_variant() == 1 ? 1 : 2; }
-
-void* regacc_kernel_for(int) {
-  switch (regacc_variant()) {
-    case 1: return (void*)scatter3d_m4_regacc_kernel<1, 3>;
-    case 24: return (void*)scatter3d_m4_regacc_kernel<2, 4>;
-    default: return (void*)scatter3d_m4_regacc_kernel<2, 5>;
   }
 }
 
@@ -668,11 +617,10 @@ bool fast3d_supported(const Geometry& g, int cmax) {
 int fast3d_ctas_per_sm(const Geometry& g, int kind) {
   if (kind == 1 && use_regacc(g)) {
     const size_t smem = sizeof(RegAccStage);
-    const int cpt = regacc_cpt();
-    void* k = regacc_kernel_for(cpt);
+    void* k = (void*)scatter3d_m4_regacc_kernel;
     if (set_smem(k, smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256 / cpt, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
     return n;
   }
   const size_t smem = smem_bytes(g);
@@ -700,12 +648,10 @@ cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArray
                                   const float* poly, const void* fhat, int ctas, cudaStream_t s) {
   if (use_regacc(g)) {
     const size_t smem = sizeof(RegAccStage);
-    const int cpt = regacc_cpt();
-    void* k = regacc_kernel_for(cpt);
-    cudaError_t e = set_smem(k, smem);
+    cudaError_t e = set_smem(scatter3d_m4_regacc_kernel, smem);
     if (e != cudaSuccess) return e;
-    auto kern = reinterpret_cast<void (*)(Geometry, float2*, NodeArrays, const float*, const float2*)>(k);
-    kern<<<ctas, 256 / cpt, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
+    scatter3d_m4_regacc_kernel<<<ctas, kRegAccThreads, smem, s>>>(g, (float2*)grid, na, poly,
+                                                                  (const float2*)fhat);
     return cudaGetLastError();
   }
   const size_t smem = smem_bytes(g);
