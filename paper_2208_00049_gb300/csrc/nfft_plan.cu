@@ -256,10 +256,17 @@ void default_tile(const nfft_plan* p, int64_t* T) {
     best = t;
     if (density * cells >= 2.0 * kResampleThreads) break;
   }
+  // 3D m = 4 complex64 (the register-accumulating scatter): 9 x 9 x 8 cells
+  // (regions of 16 x 16 x 15) measured 3.5 % faster than 8^3 for gather +
+  // scatter at 0.125 nodes per cell, with fewer halo reductions per node.
+  const bool fast_shape = p->D == 3 && p->m == 4 && p->K == 8 && p->dtype == NFFT_C64 &&
+                          !(p->flags & (NFFT_FLAG_COMPENSATED | NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
+  const int64_t pref[kMaxD] = {9, 9, 8};
   for (int d = 0; d < p->D; ++d) {
     int64_t cap = p->Nt[d] - p->K + 1;  // keeps region coordinates within [-N~, 2 N~)
     if (cap < 1) cap = 1;
-    T[d] = best < cap ? best : cap;
+    const int64_t want = (fast_shape && best == 8) ? pref[d] : best;
+    T[d] = want < cap ? want : cap;
   }
 }
 
@@ -726,6 +733,8 @@ std::vector<std::vector<int64_t>> plan_tile_candidates(const nfft_plan* p) {
     c.push_back({8, 8, 4});
     c.push_back({4, 8, 8});
     c.push_back({16, 8, 8});
+    c.push_back({9, 9, 8});
+    c.push_back({9, 9, 9});
   }
   std::vector<std::vector<int64_t>> ok;
   const int kind = (p->flags & NFFT_FLAG_COMPENSATED) ? 2 : 1;
