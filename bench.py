@@ -39,6 +39,7 @@ PROFILE_DIR = os.path.join(ROOT, "profiles")
 WORKLOADS = {
     "accuracy": "accuracy",
     "batched": "batched",
+    "tiles": "tiles",
     "3d": "3d",
     "3d_lean": "3d_lean",
     "2d_c64": "2d_c64",
@@ -456,6 +457,60 @@ def run_accuracy(args):
                       "config": {"workload": "2D N=128^2 M=16384 sigma=2 uniform nodes"}, "rows": rows}))
 
 
+def run_tiles(args):
+    """Tile-shape sweep (the GPU analogue of the block-size study of Sec. 5.2):
+    gather and scatter time per tile shape across dimension, m, sigma and node
+    density, including a clustered (non-uniform) node set."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300 import inputs
+    from paper_2208_00049_gb300.nfft import Plan
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(2208)
+    t3 = [(4, 4, 4), (8, 8, 8), (9, 9, 8), (9, 9, 9), (8, 8, 4), (4, 8, 8), (6, 8, 8), (16, 8, 8), (16, 16, 16)]
+    n3 = 128 ** 3
+    clustered = inputs.wrap_half(0.12 * rng.standard_normal((n3, 3)))
+    cases = [
+        ("3d sigma=2 m=4 uniform M=|I_N|/4", (128,) * 3, 2.0, 4, inputs.uniform_nodes(rng, n3 // 4, 3), t3),
+        ("3d sigma=2 m=4 uniform M=|I_N|", (128,) * 3, 2.0, 4, inputs.uniform_nodes(rng, n3, 3), t3),
+        ("3d sigma=2 m=4 uniform M=2|I_N|", (128,) * 3, 2.0, 4, inputs.uniform_nodes(rng, 2 * n3, 3), t3),
+        ("3d sigma=2 m=4 clustered (normal, sd 0.12) M=|I_N|", (128,) * 3, 2.0, 4, clustered, t3),
+        ("3d sigma=1.25 m=6 uniform M=|I_N|", (128,) * 3, 1.25, 6, inputs.uniform_nodes(rng, n3, 3),
+         [(4, 4, 4), (8, 8, 8), (8, 8, 4), (16, 8, 8)]),
+        ("2d sigma=2 m=4 uniform M=|I_N|", (256, 256), 2.0, 4, inputs.uniform_nodes(rng, 256 * 256, 2),
+         [(8, 8), (16, 16), (32, 32), (64, 64), (16, 32), (32, 16)]),
+    ]
+    rows = []
+    for name, N, sigma, m, k, tiles in cases:
+        M = k.shape[0]
+        plan = Plan(N, M, sigma=sigma, m=m, dtype=torch.complex64)
+        kd = torch.from_numpy(k).cuda()
+        w = torch.ones(M, dtype=torch.complex64, device="cuda")
+        fh = torch.empty(M, dtype=torch.complex64, device="cuda")
+        f = torch.ones(N, dtype=torch.complex64, device="cuda")
+        h = plan.handle
+        for tile in tiles:
+            try:
+                plan.set_tile(tile)
+                plan.set_nodes(kd)
+            except Exception as exc:  # tile not admissible for this plan
+                rows.append({"case": name, "tile": list(tile), "unavailable": str(exc)})
+                continue
+            B.check(B.nfft_step_pad_fft(h, f.data_ptr()))
+            tg = time_steps(lambda: B.check(B.nfft_step_gather(h, fh.data_ptr())), 10, 2, stream, flush)
+            ts = time_steps(lambda: B.check(B.nfft_step_scatter(h, w.data_ptr())), 10, 2, stream, flush)
+            rows.append({"case": name, "M": M, "tile": list(tile), "gather_ms": round(tg, 4),
+                         "scatter_ms": round(ts, 4), "nodes_per_s": M / ((tg + ts) * 1e-3),
+                         "fast_resample": plan.paths()["fast_resample"]})
+        plan.close()
+    print(json.dumps({"metric": "gather + scatter time per tile shape", "unit": "ms",
+                      "data": "synthetic (seeded PCG64)", "rows": rows}))
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -663,6 +718,8 @@ def main():
         run_batched(args)
     elif args.workload == "accuracy":
         run_accuracy(args)
+    elif args.workload == "tiles":
+        run_tiles(args)
     else:
         run_gpu(args)
 
