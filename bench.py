@@ -480,7 +480,7 @@ def run_tiles(args):
         ("3d sigma=2 m=4 uniform M=2|I_N|", (128,) * 3, 2.0, 4, inputs.uniform_nodes(rng, 2 * n3, 3), t3),
         ("3d sigma=2 m=4 clustered (normal, sd 0.12) M=|I_N|", (128,) * 3, 2.0, 4, clustered, t3),
         ("3d sigma=1.25 m=6 uniform M=|I_N|", (128,) * 3, 1.25, 6, inputs.uniform_nodes(rng, n3, 3),
-         [(4, 4, 4), (8, 8, 8), (8, 8, 4), (16, 8, 8)]),
+         [(4, 4, 4), (5, 5, 5), (5, 5, 4), (4, 5, 5), (8, 8, 8), (8, 8, 4), (16, 8, 8)]),
         ("2d sigma=2 m=4 uniform M=|I_N|", (256, 256), 2.0, 4, inputs.uniform_nodes(rng, 256 * 256, 2),
          [(8, 8), (16, 16), (32, 32), (64, 64), (16, 32), (32, 16)]),
     ]
@@ -505,7 +505,8 @@ def run_tiles(args):
             ts = time_steps(lambda: B.check(B.nfft_step_scatter(h, w.data_ptr())), 10, 2, stream, flush)
             rows.append({"case": name, "M": M, "tile": list(tile), "gather_ms": round(tg, 4),
                          "scatter_ms": round(ts, 4), "nodes_per_s": M / ((tg + ts) * 1e-3),
-                         "fast_resample": plan.paths()["fast_resample"]})
+                         "fast_gather": plan.paths()["fast_gather"],
+                         "fast_scatter": plan.paths()["fast_scatter"]})
         plan.close()
     print(json.dumps({"metric": "gather + scatter time per tile shape", "unit": "ms",
                       "data": "synthetic (seeded PCG64)", "rows": rows}))

@@ -197,11 +197,12 @@ int nfft_step_pad_fft(nfft_plan *p, const void *f);
  * afterwards); otherwise nfft_step_fft(+1) + nfft_step_crop_deconv. */
 int nfft_step_fft_crop(nfft_plan *p, void *y);
 
-/* Which kernels the plan's transforms use: *fast_resample = 1 when the 3D
- * m = 4 complex64 node-per-half-warp gather / plane-owned scatter kernels
- * apply (set by nfft_plan_create and nfft_set_nodes), *pruned_fft = 1 when
- * nfft_step_pad_fft / nfft_step_fft_crop run the pruned FFT.  Either
- * pointer may be NULL. */
+/* Which kernels the plan's transforms use (set by nfft_plan_create and
+ * nfft_plan_set_tile): *fast_resample bit 0 = the 3D m = 4 complex64
+ * node-per-half-warp gather, bit 1 = the 3D m = 4 or 6 complex64
+ * register-accumulating scatter (tiles of at most 17 - 2m cells per
+ * dimension); *pruned_fft = 1 when nfft_step_pad_fft / nfft_step_fft_crop
+ * run the pruned FFT.  Either pointer may be NULL. */
 int nfft_plan_paths(nfft_plan *p, int *fast_resample, int *pruned_fft);
 
 /* Node-gradient resampling on the current plan grid (which must hold

@@ -199,11 +199,11 @@ def nfft_step_fft_crop(plan, y_ptr):
 
 
 def nfft_plan_paths(plan):
-    """Returns (status, fast_resample, pruned_fft)."""
+    """Returns (status, fast_gather, fast_scatter, pruned_fft)."""
     a = _i()
     b = _i()
     s = lib().nfft_plan_paths(_p(plan), ctypes.byref(a), ctypes.byref(b))
-    return s, bool(a.value), bool(b.value)
+    return s, bool(a.value & 1), bool(a.value & 2), bool(b.value)
 
 
 def nfft_step_grad_gather(plan, cot_ptr, gk_ptr):

@@ -137,6 +137,9 @@ int resample_ctas_per_sm(const Geometry& g, int kind);
 // 3D, m = 4, complex64 warp-per-node kernels (resample3d.cu); `poly` holds
 // the FP32 polynomial window coefficients [3][8][9] (launch_build_poly).
 bool fast3d_supported(const Geometry& g, int cmax);
+// 3D complex64 register-accumulating scatter, m = 4 or 6 (any tile of at
+// most 17 - 2m cells per dimension); kind 1 of the two functions below.
+bool fast_scatter_supported(const Geometry& g, int cmax);
 int fast3d_ctas_per_sm(const Geometry& g, int kind);  // kind 0 gather, 1 scatter
 cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na,
                                  const float* poly, void* fhat, int ctas, cudaStream_t s);

@@ -329,19 +329,21 @@ __global__ void __launch_bounds__(32 * W)
 }
 
 // ---------------------------------------------------------------------------
-// Register-accumulating scatter.  Thread (r1, cc) of a 128-thread CTA owns
-// the two region lines (., r1, cc) and (., r1, cc + 8) of the tile + halo in
-// registers (acc[h][r0], r0 < L0 <= 16): a node at offset (a0, a1, a2) adds
-//   v w1[r1 - a1] w2[c - a2] * w0[i0]   to acc[h][a0 + i0],  i0 = 0..7,
-// c = cc + 8 h, so the accumulation costs 16 packed FMAs per thread and node
+// Register-accumulating scatter, K = 2m taps per dimension (m = 4 and 6).
+// Thread (r1, cc) of a 128-thread CTA owns the two region lines (., r1, cc)
+// and (., r1, cc + 8) of the tile + halo in registers (acc[h][r0],
+// r0 < L0 <= 16): a node at offset (a0, a1, a2) adds
+//   v w1[r1 - a1] w2[c - a2] * w0[i0]   to acc[h][a0 + i0],  i0 = 0..K-1,
+// c = cc + 8 h, so the accumulation costs 2K packed FMAs per thread and node
 // and no shared-memory traffic.  Register indices must be static, so the
 // nodes of a work item are counting-sorted by (a0, a1): each a0 bin runs a
 // loop specialised to its a0, and a warp, which owns rows 4w .. 4w + 3,
 // visits only the contiguous run of nodes whose a1 puts one of its rows in
-// the footprint.  Per work item:
+// the footprint.  Tiles are at most 17 - K cells per dimension (regions of
+// at most 16).  Per work item:
 //  1. stage the node records and count them per (a0, a1) key;
 //  2. scan the counts (one warp);
-//  3. evaluate the 24 window values of every node once (POLYNOMIAL form; a
+//  3. evaluate the 3K window values of every node once (POLYNOMIAL form; a
 //     lane takes two taps of all three dimensions with packed Horner steps)
 //     and store, at the node's sorted slot and shifted to region
 //     coordinates: w0 as packed pairs, v w1 per row, w2 as packed pairs per
@@ -354,18 +356,20 @@ constexpr int kRegAccWarps = kRegAccThreads / 32;  // warp w owns rows 4w .. 4w 
 constexpr int kRegAccA = 9;                        // a_d < T_d <= 9
 constexpr int kRegAccKeys = kRegAccA * kRegAccA;   // (a0, a1)
 
+template <int K>
 struct RegAccStage {
+  static constexpr int kPairs = K / 2;   // tap pairs per dimension
   float4 rec[kItemCap][2];               // {t0, t1, t2, pk}, {re v, im v, key, rank}
-  f32x2 w0p[kItemCap][kTaps];            // (w0, w0), by slot
+  f32x2 w0p[kItemCap][K];                // (w0, w0), by slot
   f32x2 vw1[kItemCap][kRegAccLines];     // v w1[r - a1], by slot
   float4 w2p[kItemCap][8];               // cc -> (w2[cc - a2] x2, w2[cc + 8 - a2] x2), by slot
   int count[kRegAccKeys];
   int start[kRegAccKeys + 1];
-  f32x2 coef[3][4][kCoef];               // (tap 2 tp, tap 2 tp + 1) coefficient pairs
+  f32x2 coef[3][kPairs][K + 1];          // (tap 2 tp, tap 2 tp + 1) coefficient pairs, degree K
 };
 
-template <int A0>
-__device__ __forceinline__ void regacc_node(const RegAccStage& st, int s, int r1, int cc,
+template <int A0, int K>
+__device__ __forceinline__ void regacc_node(const RegAccStage<K>& st, int s, int r1, int cc,
                                             f32x2 (&acc)[2][kRegAccLines]) {
   const f32x2 vw = st.vw1[s][r1];
   const float4 w2 = st.w2p[s][cc];
@@ -373,7 +377,7 @@ __device__ __forceinline__ void regacc_node(const RegAccStage& st, int s, int r1
   const f32x2 vp1 = mul2(vw, pack2(w2.z, w2.w));
   const float4* wq = reinterpret_cast<const float4*>(&st.w0p[s][0]);
 #pragma unroll
-  for (int q = 0; q < kTaps / 2; ++q) {
+  for (int q = 0; q < K / 2; ++q) {
     const float4 x = wq[q];
     const f32x2 wa = pack2(x.x, x.y), wb = pack2(x.z, x.w);
     acc[0][A0 + 2 * q] = fma2(vp0, wa, acc[0][A0 + 2 * q]);
@@ -383,34 +387,40 @@ __device__ __forceinline__ void regacc_node(const RegAccStage& st, int s, int r1
   }
 }
 
-template <int A0>
-__device__ __forceinline__ void regacc_bin(const RegAccStage& st, int lo, int hi, int r1, int cc,
+template <int A0, int K>
+__device__ __forceinline__ void regacc_bin(const RegAccStage<K>& st, int lo, int hi, int r1, int cc,
                                            f32x2 (&acc)[2][kRegAccLines]) {
-  const int s0 = st.start[A0 * kRegAccA + lo], s1 = st.start[A0 * kRegAccA + hi + 1];
-  int s = s0;
-  for (; s + 1 < s1; s += 2) {
-    regacc_node<A0>(st, s, r1, cc, acc);
-    regacc_node<A0>(st, s + 1, r1, cc, acc);
+  if constexpr (A0 + K <= kRegAccLines) {  // a0 < T0 <= 17 - K
+    const int s0 = st.start[A0 * kRegAccA + lo], s1 = st.start[A0 * kRegAccA + hi + 1];
+    int s = s0;
+    for (; s + 1 < s1; s += 2) {
+      regacc_node<A0, K>(st, s, r1, cc, acc);
+      regacc_node<A0, K>(st, s + 1, r1, cc, acc);
+    }
+    if (s < s1) regacc_node<A0, K>(st, s, r1, cc, acc);
   }
-  if (s < s1) regacc_node<A0>(st, s, r1, cc, acc);
 }
 
+template <int K>
 __global__ void __launch_bounds__(kRegAccThreads, 4)
-    scatter3d_m4_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na,
-                               const float* __restrict__ poly, const float2* __restrict__ fhat) {
+    scatter3d_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na,
+                            const float* __restrict__ poly, const float2* __restrict__ fhat) {
+  using Stage = RegAccStage<K>;
+  constexpr int P = Stage::kPairs;
+  constexpr int kPerIter = 32 / P;  // nodes per warp and weight iteration
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  RegAccStage& st = *reinterpret_cast<RegAccStage*>(smem_raw);
+  Stage& st = *reinterpret_cast<Stage*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r1 = tid >> 3, cc = tid & 7;
-  // a1 run of this warp: one of rows 4w .. 4w + 3 lies in [a1, a1 + 8)
-  const int lo = max(0, 4 * warp - (kTaps - 1)), hi = min(kRegAccA - 1, 4 * warp + 3);
-  // weight evaluation: lane (j, tp) takes taps 2 tp, 2 tp + 1 of every
-  // dimension for nodes 8 (warp + 4 it) + j; coefficients as packed pairs,
-  // kept in shared memory between items
-  const int wj = lane >> 2, tp = lane & 3;
-  for (int e = tid; e < 3 * 4 * kCoef; e += kRegAccThreads) {
-    const int d = e / (4 * kCoef), p = (e / kCoef) % 4, z = e % kCoef;
-    st.coef[d][p][z] = pack2(poly[(d * kTaps + 2 * p) * kCoef + z], poly[(d * kTaps + 2 * p + 1) * kCoef + z]);
+  // a1 run of this warp: one of rows 4w .. 4w + 3 lies in [a1, a1 + K)
+  const int lo = max(0, 4 * warp - (K - 1)), hi = min(kRegAccA - 1, 4 * warp + 3);
+  // weight evaluation: lane (wj, tp) takes taps 2 tp, 2 tp + 1 of every
+  // dimension for nodes kPerIter (warp + 4 it) + wj; coefficients as packed
+  // pairs, kept in shared memory between items
+  const int wj = lane / P, tp = lane - P * (lane / P);
+  for (int e = tid; e < 3 * P * (K + 1); e += kRegAccThreads) {
+    const int d = e / (P * (K + 1)), pp = (e / (K + 1)) % P, z = e % (K + 1);
+    st.coef[d][pp][z] = pack2(poly[(d * K + 2 * pp) * (K + 1) + z], poly[(d * K + 2 * pp + 1) * (K + 1) + z]);
   }
   const int nitems = *na.n_items;
   const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
@@ -476,35 +486,37 @@ __global__ void __launch_bounds__(kRegAccThreads, 4)
       }
     }
     __syncthreads();
-    f32x2 cpair[3][kCoef];
+    if (wj < kPerIter) {
+      f32x2 cpair[3][K + 1];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+      for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int e = 0; e < kCoef; ++e) cpair[d][e] = st.coef[d][tp][e];
-    for (int s = 8 * warp + wj; s < count; s += 8 * kRegAccWarps) {
-      const float4 r0 = st.rec[s][0];
-      const float4 rv = st.rec[s][1];
-      const int pk = __float_as_int(r0.w);
-      const int q = st.start[__float_as_int(rv.z)] + __float_as_int(rv.w);
-      float2 w[3];
+        for (int e = 0; e <= K; ++e) cpair[d][e] = st.coef[d][tp][e];
+      for (int s = kPerIter * warp + wj; s < count; s += kPerIter * kRegAccWarps) {
+        const float4 r0 = st.rec[s][0];
+        const float4 rv = st.rec[s][1];
+        const int pk = __float_as_int(r0.w);
+        const int q = st.start[__float_as_int(rv.z)] + __float_as_int(rv.w);
+        float2 w[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const float z = (d == 0 ? r0.x : (d == 1 ? r0.y : r0.z)) - 0.5f;
-        const f32x2 zz = pack2(z, z);
-        f32x2 pw = cpair[d][kDeg];
+        for (int d = 0; d < 3; ++d) {
+          const float z = (d == 0 ? r0.x : (d == 1 ? r0.y : r0.z)) - 0.5f;
+          const f32x2 zz = pack2(z, z);
+          f32x2 pw = cpair[d][K];
 #pragma unroll
-        for (int e = kDeg - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[d][e]);
-        w[d] = unpack2(pw);  // taps 2 tp, 2 tp + 1
+          for (int e = K - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[d][e]);
+          w[d] = unpack2(pw);  // taps 2 tp, 2 tp + 1
+        }
+        *reinterpret_cast<float4*>(&st.w0p[q][2 * tp]) = make_float4(w[0].x, w[0].x, w[0].y, w[0].y);
+        const int r = ((pk >> 8) & 0xff) + 2 * tp;
+        st.vw1[q][r] = pack2(rv.x * w[1].x, rv.y * w[1].x);
+        st.vw1[q][r + 1] = pack2(rv.x * w[1].y, rv.y * w[1].y);
+        // column c sits in pair cc = c & 7, half c >> 3 (two copies)
+        const int c0 = (pk >> 16) + 2 * tp, c1 = c0 + 1;
+        float* w2f = reinterpret_cast<float*>(&st.w2p[q][0]);
+        *reinterpret_cast<float2*>(&w2f[4 * (c0 & 7) + 2 * (c0 >> 3)]) = make_float2(w[2].x, w[2].x);
+        *reinterpret_cast<float2*>(&w2f[4 * (c1 & 7) + 2 * (c1 >> 3)]) = make_float2(w[2].y, w[2].y);
       }
-      *reinterpret_cast<float4*>(&st.w0p[q][2 * tp]) = make_float4(w[0].x, w[0].x, w[0].y, w[0].y);
-      const int r = ((pk >> 8) & 0xff) + 2 * tp;
-      st.vw1[q][r] = pack2(rv.x * w[1].x, rv.y * w[1].x);
-      st.vw1[q][r + 1] = pack2(rv.x * w[1].y, rv.y * w[1].y);
-      // column c sits in pair cc = c & 7, half c >> 3 (two copies)
-      const int c0 = (pk >> 16) + 2 * tp, c1 = c0 + 1;
-      float* w2f = reinterpret_cast<float*>(&st.w2p[q][0]);
-      *reinterpret_cast<float2*>(&w2f[4 * (c0 & 7) + 2 * (c0 >> 3)]) = make_float2(w[2].x, w[2].x);
-      *reinterpret_cast<float2*>(&w2f[4 * (c1 & 7) + 2 * (c1 >> 3)]) = make_float2(w[2].y, w[2].y);
     }
     __syncthreads();
     for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;  // for the next item
@@ -514,15 +526,15 @@ __global__ void __launch_bounds__(kRegAccThreads, 4)
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int r = 0; r < kRegAccLines; ++r) acc[h][r] = pack2(0.f, 0.f);
-    regacc_bin<0>(st, lo, hi, r1, cc, acc);
-    regacc_bin<1>(st, lo, hi, r1, cc, acc);
-    regacc_bin<2>(st, lo, hi, r1, cc, acc);
-    regacc_bin<3>(st, lo, hi, r1, cc, acc);
-    regacc_bin<4>(st, lo, hi, r1, cc, acc);
-    regacc_bin<5>(st, lo, hi, r1, cc, acc);
-    regacc_bin<6>(st, lo, hi, r1, cc, acc);
-    regacc_bin<7>(st, lo, hi, r1, cc, acc);
-    regacc_bin<8>(st, lo, hi, r1, cc, acc);
+    regacc_bin<0, K>(st, lo, hi, r1, cc, acc);
+    regacc_bin<1, K>(st, lo, hi, r1, cc, acc);
+    regacc_bin<2, K>(st, lo, hi, r1, cc, acc);
+    regacc_bin<3, K>(st, lo, hi, r1, cc, acc);
+    regacc_bin<4, K>(st, lo, hi, r1, cc, acc);
+    regacc_bin<5, K>(st, lo, hi, r1, cc, acc);
+    regacc_bin<6, K>(st, lo, hi, r1, cc, acc);
+    regacc_bin<7, K>(st, lo, hi, r1, cc, acc);
+    regacc_bin<8, K>(st, lo, hi, r1, cc, acc);
 
     // add the region to the grid (periodic wrap only here)
 #pragma unroll
@@ -544,7 +556,10 @@ __global__ void __launch_bounds__(kRegAccThreads, 4)
 }
 
 bool regacc_supported(const Geometry& g) {
-  return g.T[0] <= 9 && g.T[1] <= 9 && g.T[2] <= 9;
+  if (g.D != 3 || g.closed || (g.K != 8 && g.K != 12) || g.m != 0.5 * g.K || g.off != 1 - g.K / 2) return false;
+  for (int d = 0; d < 3; ++d)
+    if (g.T[d] > kRegAccLines + 1 - g.K || g.T[d] > g.Nt[d] - g.K + 1) return false;
+  return true;
 }
 
 // Scatter form: NFFT_GB300_SCATTER=smem selects the shared-accumulator
@@ -555,8 +570,20 @@ bool use_regacc(const Geometry& g) {
     const char* e = getenv("NFFT_GB300_SCATTER");
     return (e && strcmp(e, "smem") == 0) ? 1 : 0;
   }();
-  return !smem_form && regacc_supported(g);
+  // the shared-accumulator form exists for K = 8 only
+  return regacc_supported(g) && (!smem_form || g.K != kTaps);
 }
+
+}  // namespace
+
+bool fast_scatter_supported(const Geometry& g, int cmax) { return cmax <= kItemCap && use_regacc(g); }
+
+namespace {
+
+void* regacc_kernel(int K) {
+  return K == 12 ? (void*)scatter3d_regacc_kernel<12> : (void*)scatter3d_regacc_kernel<8>;
+}
+size_t regacc_smem(int K) { return K == 12 ? sizeof(RegAccStage<12>) : sizeof(RegAccStage<8>); }
 
 int gather_warps() {
   static int w = [] {
@@ -616,8 +643,8 @@ bool fast3d_supported(const Geometry& g, int cmax) {
 
 int fast3d_ctas_per_sm(const Geometry& g, int kind) {
   if (kind == 1 && use_regacc(g)) {
-    const size_t smem = sizeof(RegAccStage);
-    void* k = (void*)scatter3d_m4_regacc_kernel;
+    const size_t smem = regacc_smem(g.K);
+    void* k = regacc_kernel(g.K);
     if (set_smem(k, smem) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
@@ -647,11 +674,12 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
                                   const float* poly, const void* fhat, int ctas, cudaStream_t s) {
   if (use_regacc(g)) {
-    const size_t smem = sizeof(RegAccStage);
-    cudaError_t e = set_smem(scatter3d_m4_regacc_kernel, smem);
+    const size_t smem = regacc_smem(g.K);
+    void* k = regacc_kernel(g.K);
+    cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
-    scatter3d_m4_regacc_kernel<<<ctas, kRegAccThreads, smem, s>>>(g, (float2*)grid, na, poly,
-                                                                  (const float2*)fhat);
+    auto kern = reinterpret_cast<void (*)(Geometry, float2*, NodeArrays, const float*, const float2*)>(k);
+    kern<<<ctas, kRegAccThreads, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
     return cudaGetLastError();
   }
   const size_t smem = smem_bytes(g);

@@ -185,10 +185,11 @@ class Plan:
         return out
 
     def paths(self):
-        """{'fast_resample': bool, 'pruned_fft': bool} for this plan."""
-        s, fast, pruned = B.nfft_plan_paths(self.handle)
+        """{'fast_gather', 'fast_scatter', 'pruned_fft'}: which specialised
+        kernels this plan's transforms run."""
+        s, fg, fs, pruned = B.nfft_plan_paths(self.handle)
         B.check(s, "nfft_plan_paths")
-        return {"fast_resample": fast, "pruned_fft": pruned}
+        return {"fast_gather": fg, "fast_scatter": fs, "pruned_fft": pruned}
 
     def step_grad_gather(self, cot, out):
         self._check_tensor(cot, (self.M,), self.dtype, "cot")

@@ -280,6 +280,41 @@ def test_fast3d_m4_tile_shapes(tile):
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), 1e-5, "adjoint")
 
 
+@pytest.mark.parametrize("sigma", [2.0, 1.25])
+@pytest.mark.parametrize("tile", [(5, 5, 5), (3, 4, 5), (5, 5, 1), (2, 5, 3)])
+def test_fast_scatter_m6_tile_shapes(sigma, tile):
+    """3D, m = 6, complex64: the register-accumulating scatter (tiles of at
+    most 5 cells per dimension) against the oracle, sigma = 2 and the lean
+    sigma = 1.25."""
+    from paper_2208_00049_gb300.nfft import Plan
+    N = (20, 18, 24)
+    case = inputs.small_case(N, 5000, seed=37, sigma=sigma, m=6)
+    plan = Plan(N, case["M"], sigma=sigma, m=6, dtype=torch.complex64)
+    plan.set_tile(tile)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    assert plan.paths()["fast_scatter"]
+    y = plan.adjoint(to_dev(case["w"], torch.complex64)).cpu().numpy()
+    plan.close()
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, sigma, 6), tol_for(N, sigma, 6, "c64"), "adjoint",
+                 tol_max_for(N, sigma, 6, "c64"))
+
+
+def test_fast_scatter_m6_hot_tile():
+    """m = 6: work items split at the per-item cap, nodes on the boundary."""
+    from paper_2208_00049_gb300.nfft import Plan
+    N = (16, 16, 16)
+    case = inputs.small_case(N, 6000, seed=41, m=6)
+    case["k"][:4000] = 0.02 * case["k"][:4000]
+    case["k"][4000:4500, 1] = -0.5
+    plan = Plan(N, case["M"], sigma=2.0, m=6, dtype=torch.complex64)
+    plan.set_tile((5, 5, 5))
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    assert plan.paths()["fast_scatter"]
+    y = plan.adjoint(to_dev(case["w"], torch.complex64)).cpu().numpy()
+    plan.close()
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 6), 1e-5, "adjoint")
+
+
 def test_fast3d_m4_hot_tile_and_boundaries():
     """Many nodes in one tile (work items split at the per-item cap) and nodes
     on the periodic boundary of the 3D grid."""
