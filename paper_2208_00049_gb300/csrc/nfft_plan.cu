@@ -263,12 +263,13 @@ void default_tile(const nfft_plan* p, int64_t* T) {
   const bool fast_shape = p->D == 3 && p->m == 4 && p->K == 8 && p->dtype == NFFT_C64 &&
                           !(p->flags & (NFFT_FLAG_COMPENSATED | NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
   const int64_t pref[kMaxD] = {9, 9, 8};
-  // 3D m = 6 complex64: the register-accumulating scatter needs tiles of at
-  // most 5 cells per dimension; 5 x 5 x 4 measured best for gather + scatter
-  // at the sigma = 1.25 lean variant (4.97 ms against 18.7 ms at 8^3)
+  // 3D m = 6 complex64: the K = 12 gather and the register-accumulating
+  // scatter need tiles of at most 5 cells per dimension; 5^3 measured best
+  // for gather + scatter at the sigma = 1.25 lean variant (2.50 ms against
+  // 18.9 ms for the generic kernels at 8^3)
   const bool m6_shape = p->D == 3 && p->m == 6 && p->K == 12 && p->dtype == NFFT_C64 &&
                         !(p->flags & (NFFT_FLAG_COMPENSATED | NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
-  const int64_t pref6[kMaxD] = {5, 5, 4};
+  const int64_t pref6[kMaxD] = {5, 5, 5};
   for (int d = 0; d < p->D; ++d) {
     int64_t cap = p->Nt[d] - p->K + 1;  // keeps region coordinates within [-N~, 2 N~)
     if (cap < 1) cap = 1;

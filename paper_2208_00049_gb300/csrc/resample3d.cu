@@ -329,6 +329,150 @@ __global__ void __launch_bounds__(32 * W)
 }
 
 // ---------------------------------------------------------------------------
+// Gather for m = 6 (K = 12 taps per dimension), complex64: the tile + halo
+// (L_d = T_d + 11 <= 16 per dimension, row pitch L2) in shared memory, one
+// node per half-warp.  Lane i2 (< 12; lanes 12..15 repeat tap 11 with weight
+// 0) runs over the 12 x 12 (i0, i1) taps of its column: a half-warp load
+// reads 12 consecutive complex of one row, one shared wavefront per half.
+// The 36 window values of every node are evaluated once per work item
+// (POLYNOMIAL form, packed Horner, two taps per lane) into shared memory:
+// w0 and w1 as packed pairs, w2 zero-padded to 16.
+constexpr int kG12Taps = 12;
+constexpr int kG12Warps = 8;
+constexpr int kG12Threads = 32 * kG12Warps;
+
+struct G12Weights {
+  f32x2 w0p[kItemCap][kG12Taps];
+  f32x2 w1p[kItemCap][kG12Taps];
+  float w2[kItemCap][16];
+  f32x2 coef[3][kG12Taps / 2][kG12Taps + 1];
+};
+
+__device__ __forceinline__ size_t g12_tile_offset() { return sizeof(NodeStage) + sizeof(G12Weights); }
+
+__global__ void __launch_bounds__(kG12Threads)
+    gather3d_k12_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na,
+                        const float* __restrict__ poly, float2* __restrict__ fhat) {
+  constexpr int K = kG12Taps, P = K / 2, kPerIter = 32 / P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  NodeStage& ns = *reinterpret_cast<NodeStage*>(smem_raw);
+  G12Weights& wt = *reinterpret_cast<G12Weights*>(smem_raw + sizeof(NodeStage));
+  float2* tile = reinterpret_cast<float2*>(smem_raw + g12_tile_offset());
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = lane >> 4, i2 = lane & 15, i2c = min(i2, K - 1);
+  const int L1 = g.L[1], L2 = g.L[2];
+  const int pitch = L2, plane = L1 * pitch;
+  // weight lanes: (wj, tp) = two taps of every dimension of node kPerIter (warp + it W) + wj
+  const int wj = lane / P, tp = lane - P * (lane / P);
+  for (int e = tid; e < 3 * P * (K + 1); e += kG12Threads) {
+    const int d = e / (P * (K + 1)), pp = (e / (K + 1)) % P, z = e % (K + 1);
+    wt.coef[d][pp][z] = pack2(poly[(d * K + 2 * pp) * (K + 1) + z], poly[(d * K + 2 * pp + 1) * (K + 1) + z]);
+  }
+  const int nitems = *na.n_items;
+
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 item = na.items[it];
+    int tc[3], start[3];
+    tile_origin(g, item.x, tc);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
+    const int count = item.z;
+
+    __syncthreads();  // previous item's tile, records and weights no longer read
+    {
+      const int rows = g.L[0] * L1;
+      for (int e = tid; e < rows * L2; e += kG12Threads) {
+        const int r = e / L2, c = e - r * L2;
+        const int r0 = r / L1, r1 = r - r0 * L1;
+        const int g0 = wrap1(start[0] + r0, g.Nt[0]);
+        const int g1 = wrap1(start[1] + r1, g.Nt[1]);
+        const int g2 = wrap1(start[2] + c, g.Nt[2]);
+        cp_async8(tile + r * pitch + c, grid + ((int64_t)g0 * g.Nt[1] + g1) * g.Nt[2] + g2);
+      }
+    }
+    stage_nodes(g, na, item, tc, ns, nullptr, tid, kG12Threads);
+    __syncthreads();  // records visible (the tile copies are waited for below)
+    if (wj < kPerIter) {
+      f32x2 cpair[3][K + 1];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int e = 0; e <= K; ++e) cpair[d][e] = wt.coef[d][tp][e];
+      for (int s = kPerIter * warp + wj; s < count; s += kPerIter * kG12Warps) {
+        const float4 r0 = *reinterpret_cast<const float4*>(&ns.w[s][0]);
+        float2 w[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float z = (d == 0 ? r0.x : (d == 1 ? r0.y : r0.z)) - 0.5f;
+          const f32x2 zz = pack2(z, z);
+          f32x2 pw = cpair[d][K];
+#pragma unroll
+          for (int e = K - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[d][e]);
+          w[d] = unpack2(pw);  // taps 2 tp, 2 tp + 1
+        }
+        *reinterpret_cast<float4*>(&wt.w0p[s][2 * tp]) = make_float4(w[0].x, w[0].x, w[0].y, w[0].y);
+        *reinterpret_cast<float4*>(&wt.w1p[s][2 * tp]) = make_float4(w[1].x, w[1].x, w[1].y, w[1].y);
+        *reinterpret_cast<float2*>(&wt.w2[s][2 * tp]) = w[2];
+        if (tp == 0) *reinterpret_cast<float4*>(&wt.w2[s][K]) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    for (int s0 = 2 * warp; s0 < count; s0 += 2 * kG12Warps) {
+      const int s = min(s0 + half, count - 1);  // a half without a node repeats the last one
+      const int pk = __float_as_int(ns.w[s][3]);
+      const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
+      const float w2 = wt.w2[s][i2];
+      const f32x2* col = reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1) * pitch + a2 + i2c);
+      f32x2 w1[K];
+      const float4* w1q = reinterpret_cast<const float4*>(&wt.w1p[s][0]);
+#pragma unroll
+      for (int q = 0; q < K / 2; ++q) {
+        const float4 x = w1q[q];
+        w1[2 * q] = pack2(x.x, x.y);
+        w1[2 * q + 1] = pack2(x.z, x.w);
+      }
+      const float4* w0q = reinterpret_cast<const float4*>(&wt.w0p[s][0]);
+      f32x2 acc = pack2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < K / 2; ++q) {
+        const float4 x = w0q[q];
+        const f32x2 w0a = pack2(x.x, x.y), w0b = pack2(x.z, x.w);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const f32x2* pl = col + (2 * q + h) * plane;
+          f32x2 sum = mul2(pl[0], w1[0]);
+#pragma unroll
+          for (int i1 = 1; i1 < K; ++i1) sum = fma2(pl[i1 * pitch], w1[i1], sum);
+          acc = fma2(sum, h == 0 ? w0a : w0b, acc);
+        }
+      }
+      float2 r = unpack2(acc);
+      r.x *= w2;
+      r.y *= w2;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
+        r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+      }
+      if (i2 == 0 && s0 + half < count) fhat[__float_as_int(ns.w[s][4])] = r;
+    }
+  }
+}
+
+size_t g12_smem_bytes(const Geometry& g) {
+  return sizeof(NodeStage) + sizeof(G12Weights) + (size_t)g.L[0] * g.L[1] * g.L[2] * sizeof(float2);
+}
+
+bool g12_supported(const Geometry& g, int cmax) {
+  if (g.D != 3 || g.K != kG12Taps || g.closed || g.off != -5 || g.m != 6.0 || cmax > kItemCap) return false;
+  for (int d = 0; d < 3; ++d)
+    if (g.L[d] > 16 || g.T[d] > g.Nt[d] - kG12Taps + 1) return false;
+  return g12_smem_bytes(g) <= 200 * 1024;
+}
+
+// ---------------------------------------------------------------------------
 // Register-accumulating scatter, K = 2m taps per dimension (m = 4 and 6).
 // Thread (r1, cc) of a 128-thread CTA owns the two region lines (., r1, cc)
 // and (., r1, cc + 8) of the tile + halo in registers (acc[h][r0],
@@ -634,6 +778,7 @@ cudaError_t set_smem(K kern, size_t smem) {
 }  // namespace
 
 bool fast3d_supported(const Geometry& g, int cmax) {
+  if (g.K == kG12Taps) return g12_supported(g, cmax);
   if (g.D != 3 || g.K != kTaps || g.closed || g.off != -3 || g.m != 4.0) return false;
   if (g.T[2] > kMaxTile2 || cmax > kItemCap) return false;
   for (int d = 0; d < 3; ++d)
@@ -650,6 +795,15 @@ int fast3d_ctas_per_sm(const Geometry& g, int kind) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
     return n;
   }
+  if (kind == 0 && g.K == kG12Taps) {
+    const size_t smem = g12_smem_bytes(g);
+    if (set_smem(gather3d_k12_kernel, smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather3d_k12_kernel, kG12Threads, smem) != cudaSuccess)
+      return 0;
+    return n;
+  }
+  if (g.K != kTaps) return 0;
   const size_t smem = smem_bytes(g);
   void* k = kind == 0 ? gather_kernel_for(gather_warps()) : scatter_kernel_for(scatter_warps());
   const int threads = kind == 0 ? 32 * gather_warps() : 32 * scatter_warps();
@@ -661,6 +815,13 @@ int fast3d_ctas_per_sm(const Geometry& g, int kind) {
 
 cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na,
                                  const float* poly, void* fhat, int ctas, cudaStream_t s) {
+  if (g.K == kG12Taps) {
+    const size_t smem = g12_smem_bytes(g);
+    cudaError_t e = set_smem(gather3d_k12_kernel, smem);
+    if (e != cudaSuccess) return e;
+    gather3d_k12_kernel<<<ctas, kG12Threads, smem, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat);
+    return cudaGetLastError();
+  }
   const size_t smem = smem_bytes(g);
   const int w = gather_warps();
   void* k = gather_kernel_for(w);

@@ -282,24 +282,26 @@ def test_fast3d_m4_tile_shapes(tile):
 
 @pytest.mark.parametrize("sigma", [2.0, 1.25])
 @pytest.mark.parametrize("tile", [(5, 5, 5), (3, 4, 5), (5, 5, 1), (2, 5, 3)])
-def test_fast_scatter_m6_tile_shapes(sigma, tile):
-    """3D, m = 6, complex64: the register-accumulating scatter (tiles of at
-    most 5 cells per dimension) against the oracle, sigma = 2 and the lean
-    sigma = 1.25."""
+def test_fast_m6_tile_shapes(sigma, tile):
+    """3D, m = 6, complex64: the K = 12 gather and the register-accumulating
+    scatter (tiles of at most 5 cells per dimension) against the oracle,
+    sigma = 2 and the lean sigma = 1.25."""
     from paper_2208_00049_gb300.nfft import Plan
     N = (20, 18, 24)
     case = inputs.small_case(N, 5000, seed=37, sigma=sigma, m=6)
     plan = Plan(N, case["M"], sigma=sigma, m=6, dtype=torch.complex64)
     plan.set_tile(tile)
     plan.set_nodes(to_dev(case["k"], torch.float64))
-    assert plan.paths()["fast_scatter"]
+    assert plan.paths()["fast_scatter"] and plan.paths()["fast_gather"]
+    fh = plan.forward(to_dev(case["f"], torch.complex64)).cpu().numpy()
     y = plan.adjoint(to_dev(case["w"], torch.complex64)).cpu().numpy()
     plan.close()
-    assert_close(y, onfft.adjoint(case["k"], case["w"], N, sigma, 6), tol_for(N, sigma, 6, "c64"), "adjoint",
-                 tol_max_for(N, sigma, 6, "c64"))
+    tol, tmax = tol_for(N, sigma, 6, "c64"), tol_max_for(N, sigma, 6, "c64")
+    assert_close(fh, onfft.forward(case["k"], case["f"], sigma, 6), tol, "forward", tmax)
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, sigma, 6), tol, "adjoint", tmax)
 
 
-def test_fast_scatter_m6_hot_tile():
+def test_fast_m6_hot_tile():
     """m = 6: work items split at the per-item cap, nodes on the boundary."""
     from paper_2208_00049_gb300.nfft import Plan
     N = (16, 16, 16)
@@ -309,9 +311,11 @@ def test_fast_scatter_m6_hot_tile():
     plan = Plan(N, case["M"], sigma=2.0, m=6, dtype=torch.complex64)
     plan.set_tile((5, 5, 5))
     plan.set_nodes(to_dev(case["k"], torch.float64))
-    assert plan.paths()["fast_scatter"]
+    assert plan.paths()["fast_scatter"] and plan.paths()["fast_gather"]
+    fh = plan.forward(to_dev(case["f"], torch.complex64)).cpu().numpy()
     y = plan.adjoint(to_dev(case["w"], torch.complex64)).cpu().numpy()
     plan.close()
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 6), 1e-5, "forward")
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 6), 1e-5, "adjoint")
 
 
