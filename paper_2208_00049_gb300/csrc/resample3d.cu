@@ -350,7 +350,7 @@ struct G12Weights {
 
 __device__ __forceinline__ size_t g12_tile_offset() { return sizeof(NodeStage) + sizeof(G12Weights); }
 
-__global__ void __launch_bounds__(kG12Threads)
+__global__ void __launch_bounds__(kG12Threads, 3)
     gather3d_k12_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na,
                         const float* __restrict__ poly, float2* __restrict__ fhat) {
   constexpr int K = kG12Taps, P = K / 2, kPerIter = 32 / P;
@@ -393,27 +393,27 @@ __global__ void __launch_bounds__(kG12Threads)
     stage_nodes(g, na, item, tc, ns, nullptr, tid, kG12Threads);
     __syncthreads();  // records visible (the tile copies are waited for below)
     if (wj < kPerIter) {
-      f32x2 cpair[3][K + 1];
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
+      for (int d = 0; d < 3; ++d) {  // one dimension's coefficients in registers at a time
+        f32x2 cpair[K + 1];
 #pragma unroll
-        for (int e = 0; e <= K; ++e) cpair[d][e] = wt.coef[d][tp][e];
-      for (int s = kPerIter * warp + wj; s < count; s += kPerIter * kG12Warps) {
-        const float4 r0 = *reinterpret_cast<const float4*>(&ns.w[s][0]);
-        float2 w[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const float z = (d == 0 ? r0.x : (d == 1 ? r0.y : r0.z)) - 0.5f;
+        for (int e = 0; e <= K; ++e) cpair[e] = wt.coef[d][tp][e];
+        for (int s = kPerIter * warp + wj; s < count; s += kPerIter * kG12Warps) {
+          const float z = ns.w[s][d] - 0.5f;
           const f32x2 zz = pack2(z, z);
-          f32x2 pw = cpair[d][K];
+          f32x2 pw = cpair[K];
 #pragma unroll
-          for (int e = K - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[d][e]);
-          w[d] = unpack2(pw);  // taps 2 tp, 2 tp + 1
+          for (int e = K - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[e]);
+          const float2 w = unpack2(pw);  // taps 2 tp, 2 tp + 1
+          if (d == 0) {
+            *reinterpret_cast<float4*>(&wt.w0p[s][2 * tp]) = make_float4(w.x, w.x, w.y, w.y);
+          } else if (d == 1) {
+            *reinterpret_cast<float4*>(&wt.w1p[s][2 * tp]) = make_float4(w.x, w.x, w.y, w.y);
+          } else {
+            *reinterpret_cast<float2*>(&wt.w2[s][2 * tp]) = w;
+            if (tp == 0) *reinterpret_cast<float4*>(&wt.w2[s][K]) = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
-        *reinterpret_cast<float4*>(&wt.w0p[s][2 * tp]) = make_float4(w[0].x, w[0].x, w[0].y, w[0].y);
-        *reinterpret_cast<float4*>(&wt.w1p[s][2 * tp]) = make_float4(w[1].x, w[1].x, w[1].y, w[1].y);
-        *reinterpret_cast<float2*>(&wt.w2[s][2 * tp]) = w[2];
-        if (tp == 0) *reinterpret_cast<float4*>(&wt.w2[s][K]) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     cp_async_wait_all();
