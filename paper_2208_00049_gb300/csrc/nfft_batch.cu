@@ -76,6 +76,8 @@ struct nfft_batch {
   int* item_off = nullptr;
   int64_t items_cap = 0;
   int ctas[2] = {0, 0};
+  bool fast_scatter = false;  // 2D m = 4 complex64 register-accumulating scatter
+  int fast_ctas = 0;
 
   bool has_nodes = false;
   bool graph_mode = false;
@@ -212,6 +214,13 @@ int configure(nfft_batch* b) {
     if (per <= 0) return NFFT_ERR_UNSUPPORTED;
     b->ctas[kind] = per * b->sms;
   }
+  b->fast_scatter = b->D == 2 && b->dtype == NFFT_C64 && !(b->flags & NFFT_FLAG_COMPENSATED);
+  for (int p = 0; p < b->B && b->fast_scatter; ++p) b->fast_scatter = scatter2d_supported(b->probs_host[p].g);
+  if (b->fast_scatter) {
+    const int per = scatter2d_ctas_per_sm();
+    b->fast_scatter = per > 0;
+    b->fast_ctas = per * b->sms;
+  }
   for (int k = 0; k < 2; ++k) {
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
     b->graph[k] = nullptr;
@@ -320,7 +329,9 @@ int enqueue_forward(nfft_batch* b, const void* f, void* fhat, cudaStream_t st) {
 int enqueue_adjoint(nfft_batch* b, const void* fhat, void* y, cudaStream_t st) {
   const Geometry gm = max_geometry(b);
   B_CK(b, cudaMemsetAsync(b->grid, 0, (size_t)b->grid_total * csize(b->dtype), st));
-  cudaError_t e = b->dtype == NFFT_C128
+  cudaError_t e = b->fast_scatter
+                      ? launch_scatter2d_fast_batch(b->probs, b->grid, batch_nodes(b), fhat, b->fast_ctas, st)
+                  : b->dtype == NFFT_C128
                       ? launch_scatter_batch<double>(b->probs, gm, b->grid, batch_nodes(b), fhat, b->ctas[1], st)
                       : launch_scatter_batch<float>(b->probs, gm, b->grid, batch_nodes(b), fhat, b->ctas[1], st);
   B_CK(b, e);
@@ -399,6 +410,8 @@ std::vector<std::vector<int64_t>> tile_candidates(int D, int K, int dtype) {
     for (int64_t t : {8, 16, 32, 64}) c.push_back({t, t, 1});
     c.push_back({16, 32, 1});
     c.push_back({32, 16, 1});
+    c.push_back({9, 25, 1});
+    c.push_back({8, 25, 1});
   } else {
     for (int64_t t : {4, 8, 16}) c.push_back({t, t, t});
     c.push_back({8, 8, 4});

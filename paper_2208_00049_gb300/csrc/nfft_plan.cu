@@ -270,12 +270,18 @@ void default_tile(const nfft_plan* p, int64_t* T) {
   const bool m6_shape = p->D == 3 && p->m == 6 && p->K == 12 && p->dtype == NFFT_C64 &&
                         !(p->flags & (NFFT_FLAG_COMPENSATED | NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
   const int64_t pref6[kMaxD] = {5, 5, 5};
+  // 2D m = 4 complex64: the register-accumulating scatter holds regions of
+  // at most 16 x 32 cells
+  const bool m4_2d = p->D == 2 && p->m == 4 && p->K == 8 && p->dtype == NFFT_C64 &&
+                     !(p->flags & (NFFT_FLAG_COMPENSATED | NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
+  const int64_t pref2[kMaxD] = {9, 25, 1};
   for (int d = 0; d < p->D; ++d) {
     int64_t cap = p->Nt[d] - p->K + 1;  // keeps region coordinates within [-N~, 2 N~)
     if (cap < 1) cap = 1;
     int64_t want = best;
     if (fast_shape && best == 8) want = pref[d];
     if (m6_shape && best >= 4) want = pref6[d];
+    if (m4_2d && best >= 8) want = pref2[d];
     T[d] = want < cap ? want : cap;
   }
 }
@@ -317,8 +323,9 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
     p->fast3d = per_sm > 0;
     p->fast_ctas[0] = per_sm * p->sms;
   }
+  if (p->D == 2) p->fast_scatter = plain_c64 && scatter2d_supported(g);
   if (p->fast_scatter) {
-    const int per_sm = fast3d_ctas_per_sm(g, 1);
+    const int per_sm = p->D == 2 ? scatter2d_ctas_per_sm() : fast3d_ctas_per_sm(g, 1);
     p->fast_scatter = per_sm > 0;
     p->fast_ctas[1] = per_sm * p->sms;
   }
@@ -390,7 +397,9 @@ int run_scatter(nfft_plan* p, const void* fhat) {
   NodeArrays na = node_arrays(p);
   const int comp = (p->flags & NFFT_FLAG_COMPENSATED) && p->dtype == NFFT_C64 ? 1 : 0;
   cudaError_t e =
-      p->fast_scatter ? launch_scatter3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[1], p->stream)
+      p->fast_scatter
+          ? (p->D == 2 ? launch_scatter2d_fast(g, p->grid, na, fhat, p->fast_ctas[1], p->stream)
+                       : launch_scatter3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[1], p->stream))
       : p->dtype == NFFT_C128
           ? launch_scatter<double>(g, p->grid, na, fhat, 0, p->ctas[1], p->stream)
           : launch_scatter<float>(g, p->grid, na, fhat, comp, p->ctas[comp ? 2 : 1], p->stream);
@@ -739,6 +748,8 @@ std::vector<std::vector<int64_t>> plan_tile_candidates(const nfft_plan* p) {
     for (int64_t t : {8, 16, 32, 64}) c.push_back({t, t, 1});
     c.push_back({16, 32, 1});
     c.push_back({32, 16, 1});
+    c.push_back({9, 25, 1});
+    c.push_back({8, 25, 1});
   } else {
     for (int64_t t : {4, 8, 16}) c.push_back({t, t, t});
     c.push_back({8, 8, 4});

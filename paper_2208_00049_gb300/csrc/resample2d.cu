@@ -1,0 +1,179 @@
+// 2D register-accumulating scatter for m = 4 (8 taps per dimension),
+// complex64, for single plans and for batches.
+//
+// Same computation as the generic scatter (Eq. SumOverNodeAdjoint, Eq.
+// InnerTensorStructure, Algorithm 4) with the tile + halo region held in
+// registers: lane c of a warp owns the region column (., c), c < L1 <= 32,
+// as 16 packed complex accumulators acc[r0] (r0 < L0 <= 16).  A node at tile
+// offset (a0, a1) adds  v w1[c - a1] * w0[i0]  to acc[a0 + i0], i0 = 0..7:
+// 8 packed FMAs per lane and node, no shared-memory accumulation.  Register
+// indices must be static, so each staged chunk of 32 nodes is binned by a0
+// with warp ballots and every bin runs a loop specialised to its a0.
+//
+// Each warp works on its own work items (no block-wide barriers): per chunk
+// of 32 nodes, lane i loads node i (cells, fractions, value), evaluates its
+// 16 window values (the direct Kaiser-Bessel form of the generic kernels),
+// and writes them at its bin slot in the warp's stage; the warp then runs
+// over the bins.  After the item's last chunk the region is added to the grid
+// with vector global reductions (periodic wrap only there).
+#include "packed_f32x2.cuh"
+#include "resample.cuh"
+
+namespace nfftgb {
+namespace {
+
+constexpr int k2Taps = 8;
+constexpr int k2Lines = 16;                 // acc[r0], L0 <= 16
+constexpr int k2Cols = 32;                  // one region column per lane, L1 <= 32
+constexpr int k2Warps = 4;                  // independent warps per CTA
+constexpr int k2Threads = 32 * k2Warps;
+constexpr int k2Bins = 9;                   // a0 < T0 <= 9
+
+struct Stage2d {
+  f32x2 w0p[32][k2Taps];  // (w0, w0) pairs, by slot
+  float w1[32][k2Taps];
+  f32x2 v[32];
+  int a1[32];
+};
+
+template <int A0>
+__device__ __forceinline__ void scatter2d_bin(const Stage2d& st, int s0, int s1, int lane,
+                                              f32x2 (&acc)[k2Lines]) {
+  if constexpr (A0 + k2Taps <= k2Lines) {
+    for (int s = s0; s < s1; ++s) {
+      const int i1 = lane - st.a1[s];
+      const float wv = st.w1[s][i1 & (k2Taps - 1)];
+      const float p = (unsigned)i1 < (unsigned)k2Taps ? wv : 0.f;
+      const f32x2 vp = mul2(st.v[s], pack2(p, p));
+      const float4* wq = reinterpret_cast<const float4*>(&st.w0p[s][0]);
+#pragma unroll
+      for (int q = 0; q < k2Taps / 2; ++q) {
+        const float4 x = wq[q];
+        acc[A0 + 2 * q] = fma2(vp, pack2(x.x, x.y), acc[A0 + 2 * q]);
+        acc[A0 + 2 * q + 1] = fma2(vp, pack2(x.z, x.w), acc[A0 + 2 * q + 1]);
+      }
+    }
+  }
+}
+
+// One work item of one problem, by one warp.
+__device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __restrict__ grid,
+                                               const int* __restrict__ cell, const float* __restrict__ frac,
+                                               const int* __restrict__ perm, const float2* __restrict__ fhat,
+                                               const int4& item, Stage2d& st, int lane) {
+  const int64_t M = g.M;
+  int tc[2];
+  tile_coords<2>(g, item.x, tc);
+  const int start0 = tc[0] * g.T[0] + g.off, start1 = tc[1] * g.T[1] + g.off;
+  const unsigned lt = (1u << lane) - 1u;
+  f32x2 acc[k2Lines];
+#pragma unroll
+  for (int r = 0; r < k2Lines; ++r) acc[r] = pack2(0.f, 0.f);
+
+  for (int base = 0; base < item.z; base += 32) {
+    const bool valid = base + lane < item.z;
+    const int q = item.y + base + lane;
+    const int a0 = valid ? cell[q] - tc[0] * g.T[0] : -1;
+    // counting sort of the chunk by a0 (ballots): bin starts bs[], own slot
+    int bs[k2Bins + 1];
+    int slot = 0, run = 0;
+#pragma unroll
+    for (int b = 0; b < k2Bins; ++b) {
+      const unsigned m = __ballot_sync(0xffffffffu, a0 == b);
+      bs[b] = run;
+      if (a0 == b) slot = run + __popc(m & lt);
+      run += __popc(m);
+    }
+    bs[k2Bins] = run;
+    __syncwarp();  // the previous chunk's stage is no longer read
+    if (valid) {
+      // window values straight into the node's slot (one tap at a time)
+      const float t0 = frac[q], t1 = frac[M + q];
+      const float b0 = (float)g.b[0], n0 = (float)g.norm[0], b1 = (float)g.b[1], n1 = (float)g.norm[1];
+#pragma unroll 2
+      for (int i = 0; i < k2Taps; ++i) {
+        const float w = kb_window<float>((float)(4 + g.off + i) - t0, (float)(4 - g.off - i) + t0, b0, n0);
+        st.w0p[slot][i] = pack2(w, w);
+        st.w1[slot][i] = kb_window<float>((float)(4 + g.off + i) - t1, (float)(4 - g.off - i) + t1, b1, n1);
+      }
+      const float2 v = fhat[perm[q]];
+      st.v[slot] = pack2(v.x, v.y);
+      st.a1[slot] = cell[M + q] - tc[1] * g.T[1];
+    }
+    __syncwarp();
+    scatter2d_bin<0>(st, bs[0], bs[1], lane, acc);
+    scatter2d_bin<1>(st, bs[1], bs[2], lane, acc);
+    scatter2d_bin<2>(st, bs[2], bs[3], lane, acc);
+    scatter2d_bin<3>(st, bs[3], bs[4], lane, acc);
+    scatter2d_bin<4>(st, bs[4], bs[5], lane, acc);
+    scatter2d_bin<5>(st, bs[5], bs[6], lane, acc);
+    scatter2d_bin<6>(st, bs[6], bs[7], lane, acc);
+    scatter2d_bin<7>(st, bs[7], bs[8], lane, acc);
+    scatter2d_bin<8>(st, bs[8], bs[9], lane, acc);
+  }
+
+  if (lane < g.L[1]) {
+    const int g1 = wrap_mod(start1 + lane, g.Nt[1]);
+#pragma unroll
+    for (int r = 0; r < k2Lines; ++r) {
+      if (r < g.L[0]) {
+        const int g0 = wrap_mod(start0 + r, g.Nt[0]);
+        atomicAdd(grid + (int64_t)g0 * g.Nt[1] + g1, unpack2(acc[r]));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(k2Threads)
+    scatter2d_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na, const float2* __restrict__ fhat) {
+  __shared__ Stage2d stage[k2Warps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = *na.n_items;
+  const float* frac = reinterpret_cast<const float*>(na.frac);
+  for (int it = blockIdx.x * k2Warps + warp; it < nitems; it += gridDim.x * k2Warps)
+    scatter2d_item(g, grid, na.cell, frac, na.perm, fhat, na.items[it], stage[warp], lane);
+}
+
+__global__ void __launch_bounds__(k2Threads)
+    scatter2d_regacc_batch_kernel(const BatchProblem* __restrict__ probs, float2* __restrict__ grid, BatchNodes nb,
+                                  const float2* __restrict__ fhat) {
+  __shared__ Stage2d stage[k2Warps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = *nb.n_items;
+  const float* frac = reinterpret_cast<const float*>(nb.frac);
+  for (int it = blockIdx.x * k2Warps + warp; it < nitems; it += gridDim.x * k2Warps) {
+    const int4 item = nb.items[it];
+    const BatchProblem& P = probs[item.w];
+    scatter2d_item(P.g, grid + P.grid_off, nb.cell + 2 * P.node_off, frac + 2 * P.node_off,
+                   nb.perm + P.node_off, fhat + P.out_off, item, stage[warp], lane);
+  }
+}
+
+}  // namespace
+
+bool scatter2d_supported(const Geometry& g) {
+  if (g.D != 2 || g.K != k2Taps || g.closed || g.off != -3 || g.m != 4.0) return false;
+  return g.T[0] <= k2Lines + 1 - k2Taps && g.L[1] <= k2Cols && g.T[0] <= g.Nt[0] - k2Taps + 1 &&
+         g.T[1] <= g.Nt[1] - k2Taps + 1;
+}
+
+int scatter2d_ctas_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scatter2d_regacc_kernel, k2Threads, 0) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat, int ctas,
+                                  cudaStream_t s) {
+  scatter2d_regacc_kernel<<<ctas, k2Threads, 0, s>>>(g, (float2*)grid, na, (const float2*)fhat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb, const void* fhat,
+                                        int ctas, cudaStream_t s) {
+  scatter2d_regacc_batch_kernel<<<ctas, k2Threads, 0, s>>>(probs, (float2*)grid, nb, (const float2*)fhat);
+  return cudaGetLastError();
+}
+
+}  // namespace nfftgb

@@ -63,6 +63,32 @@ def test_uneven_problems_against_oracle():
     b.close()
 
 
+def test_uneven_problems_register_scatter_tile():
+    """The 2D register-accumulating scatter (tile 9 x 25, regions of 16 x 32)
+    on the uneven batch: full adjoint on the smallest problems and the
+    largest, the adjoint identity on all."""
+    from paper_2208_00049_gb300.nfft import Batch
+    probs = inputs.batched_problems(n_problems=24, salt=3)
+    Ns = [p["N"] for p in probs]
+    Ms = [p["M"] for p in probs]
+    b = Batch(Ns, list(range(24)), Ms, sigma=2.0, m=4, dtype=torch.complex64)
+    b.set_tile((9, 25))
+    b.set_nodes(torch.from_numpy(np.concatenate([p["k"] for p in probs])).cuda())
+    assert b.info()["tile"] == (9, 25)
+    f_all = _flat([p["f"] for p in probs], torch.complex64)
+    w_all = _flat([p["w"] for p in probs], torch.complex64)
+    fh = _split(b.forward(f_all).cpu().numpy(), Ms)
+    y = _split(b.adjoint(w_all).cpu().numpy(), [int(np.prod(n)) for n in Ns])
+    for i, p in enumerate(probs):
+        lhs = np.vdot(p["w"], fh[i])
+        rhs = np.vdot(y[i], p["f"].ravel())
+        assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(p["w"]) * np.linalg.norm(fh[i])
+    for i in sorted(range(24), key=lambda i: Ms[i])[:3] + [int(np.argmax(Ms))]:
+        p = probs[i]
+        assert_close(y[i].reshape(p["N"]), onfft.adjoint(p["k"], p["w"], p["N"], 2.0, 4), 1e-5, "adjoint %d" % i)
+    b.close()
+
+
 def test_shared_node_set_rhs_graph_and_autotune():
     from paper_2208_00049_gb300.nfft import Batch
     rad = inputs.radial_rhs(n_rhs=32)
