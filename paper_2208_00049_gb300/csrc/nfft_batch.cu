@@ -76,8 +76,8 @@ struct nfft_batch {
   int* item_off = nullptr;
   int64_t items_cap = 0;
   int ctas[2] = {0, 0};
-  bool fast_scatter = false;  // 2D m = 4 complex64 register-accumulating scatter
-  int fast_ctas = 0;
+  bool fast_scatter = false;  // 2D m = 4 complex64 register-accumulating scatter and warp gather
+  int fast_ctas = 0, fast_gather_ctas = 0;
 
   bool has_nodes = false;
   bool graph_mode = false;
@@ -217,9 +217,10 @@ int configure(nfft_batch* b) {
   b->fast_scatter = b->D == 2 && b->dtype == NFFT_C64 && !(b->flags & NFFT_FLAG_COMPENSATED);
   for (int p = 0; p < b->B && b->fast_scatter; ++p) b->fast_scatter = scatter2d_supported(b->probs_host[p].g);
   if (b->fast_scatter) {
-    const int per = scatter2d_ctas_per_sm();
-    b->fast_scatter = per > 0;
+    const int per = scatter2d_ctas_per_sm(), per_g = gather2d_ctas_per_sm();
+    b->fast_scatter = per > 0 && per_g > 0;
     b->fast_ctas = per * b->sms;
+    b->fast_gather_ctas = per_g * b->sms;
   }
   for (int k = 0; k < 2; ++k) {
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
@@ -319,7 +320,9 @@ int enqueue_forward(nfft_batch* b, const void* f, void* fhat, cudaStream_t st) {
   B_CK(b, e);
   int s = run_fft_classes(b, -1, st);
   if (s != NFFT_OK) return s;
-  e = b->dtype == NFFT_C128
+  e = b->fast_scatter
+          ? launch_gather2d_fast_batch(b->probs, b->grid, batch_nodes(b), fhat, b->fast_gather_ctas, st)
+      : b->dtype == NFFT_C128
           ? launch_gather_batch<double>(b->probs, gm, b->grid, batch_nodes(b), fhat, b->ctas[0], st)
           : launch_gather_batch<float>(b->probs, gm, b->grid, batch_nodes(b), fhat, b->ctas[0], st);
   B_CK(b, e);

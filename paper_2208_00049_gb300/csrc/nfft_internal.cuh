@@ -156,10 +156,16 @@ cudaError_t launch_pruned_forward(const void* f, const float* const* beta, const
                                   cudaStream_t s);
 cudaError_t launch_pruned_adjoint(void* grid, const float* const* beta, const float2* tw, void* y, cudaStream_t s);
 
-// 2D, m = 4, complex64 register-accumulating scatter (resample2d.cu): tiles
-// of at most 9 cells in dimension 0 and regions of at most 32 in dimension 1.
+// 2D, m = 4, complex64 register-accumulating scatter and warp-per-item
+// gather (resample2d.cu): tiles of at most 9 cells in dimension 0 and
+// regions of at most 32 in dimension 1.
 bool scatter2d_supported(const Geometry& g);
 int scatter2d_ctas_per_sm();
+int gather2d_ctas_per_sm();
+cudaError_t launch_gather2d_fast(const Geometry& g, const void* grid, const NodeArrays& na, void* fhat, int ctas,
+                                 cudaStream_t s);
+cudaError_t launch_gather2d_fast_batch(const BatchProblem* probs, const void* grid, const BatchNodes& nb, void* fhat,
+                                       int ctas, cudaStream_t s);
 cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat, int ctas,
                                   cudaStream_t s);
 cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb, const void* fhat,

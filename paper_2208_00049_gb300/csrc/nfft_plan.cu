@@ -41,8 +41,8 @@ struct nfft_plan {
   int cmax = 128;
   int64_t max_items = 0;
   int ctas[4] = {0, 0, 0, 0};  // persistent grid per kernel kind
-  bool fast3d = false;         // 3D m = 4 complex64 half-warp-per-node gather
-  bool fast_scatter = false;   // 3D m = 4 / 6 complex64 register-accumulating scatter
+  bool fast_gather = false;    // specialised complex64 gather (3D m = 4 / 6, 2D m = 4)
+  bool fast_scatter = false;   // register-accumulating complex64 scatter (3D m = 4 / 6, 2D m = 4)
   FullMatrix* full = nullptr;  // NFFT_FLAG_FULL_MATRIX: B and B^T as CSR
   int fast_ctas[2] = {0, 0};
   bool pruned = false;         // nfft_step_pad_fft / fft_crop use the pruned 3D FFT
@@ -316,14 +316,14 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
   }
   Geometry g = make_geometry(p);
   const bool plain_c64 = p->dtype == NFFT_C64 && !(p->flags & NFFT_FLAG_COMPENSATED);
-  p->fast3d = plain_c64 && fast3d_supported(g, p->cmax);
-  p->fast_scatter = plain_c64 && (p->fast3d || fast_scatter_supported(g, p->cmax));
-  if (p->fast3d) {
-    const int per_sm = fast3d_ctas_per_sm(g, 0);
-    p->fast3d = per_sm > 0;
+  p->fast_gather = plain_c64 && fast3d_supported(g, p->cmax);
+  p->fast_scatter = plain_c64 && (p->fast_gather || fast_scatter_supported(g, p->cmax));
+  if (p->D == 2) p->fast_gather = p->fast_scatter = plain_c64 && scatter2d_supported(g);
+  if (p->fast_gather) {
+    const int per_sm = p->D == 2 ? gather2d_ctas_per_sm() : fast3d_ctas_per_sm(g, 0);
+    p->fast_gather = per_sm > 0;
     p->fast_ctas[0] = per_sm * p->sms;
   }
-  if (p->D == 2) p->fast_scatter = plain_c64 && scatter2d_supported(g);
   if (p->fast_scatter) {
     const int per_sm = p->D == 2 ? scatter2d_ctas_per_sm() : fast3d_ctas_per_sm(g, 1);
     p->fast_scatter = per_sm > 0;
@@ -383,7 +383,9 @@ int run_gather(nfft_plan* p, void* fhat) {
   Geometry g = make_geometry(p);
   NodeArrays na = node_arrays(p);
   if (p->full) return latch(p, full_forward(p->full, p->grid, fhat, p->stream));
-  cudaError_t e = p->fast3d ? launch_gather3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[0], p->stream)
+  cudaError_t e = p->fast_gather
+                      ? (p->D == 2 ? launch_gather2d_fast(g, p->grid, na, fhat, p->fast_ctas[0], p->stream)
+                                   : launch_gather3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[0], p->stream))
                   : p->dtype == NFFT_C128
                       ? launch_gather<double>(g, p->grid, na, fhat, p->ctas[0], p->stream)
                       : launch_gather<float>(g, p->grid, na, fhat, p->ctas[0], p->stream);
@@ -894,7 +896,7 @@ int nfft_step_fft_crop(nfft_plan* p, void* y) {
 
 int nfft_plan_paths(nfft_plan* p, int* fast_resample, int* pruned_fft) {
   if (!p) return NFFT_ERR_INVALID_ARG;
-  if (fast_resample) *fast_resample = (p->fast3d ? 1 : 0) | (p->fast_scatter ? 2 : 0);
+  if (fast_resample) *fast_resample = (p->fast_gather ? 1 : 0) | (p->fast_scatter ? 2 : 0);
   if (pruned_fft) *pruned_fft = p->pruned ? 1 : 0;
   return NFFT_OK;
 }

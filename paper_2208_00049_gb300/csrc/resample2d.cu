@@ -1,5 +1,6 @@
-// 2D register-accumulating scatter for m = 4 (8 taps per dimension),
-// complex64, for single plans and for batches.
+// 2D kernels for m = 4 (8 taps per dimension), complex64, for single plans
+// and for batches: a register-accumulating scatter and a warp-per-item
+// gather.
 //
 // Same computation as the generic scatter (Eq. SumOverNodeAdjoint, Eq.
 // InnerTensorStructure, Algorithm 4) with the tile + halo region held in
@@ -16,6 +17,12 @@
 // and writes them at its bin slot in the warp's stage; the warp then runs
 // over the bins.  After the item's last chunk the region is added to the grid
 // with vector global reductions (periodic wrap only there).
+//
+// The gather keeps the same one-warp-per-item structure (no block-wide
+// barriers): the warp copies its item's region (<= 16 x 32) into its own
+// shared-memory tile with coalesced row loads, then each lane takes one node
+// (Eq. SumOverNode as the nested sum of Eq. InnerTensorStructure, packed
+// complex FMAs) and writes fhat in the caller's order.
 #include "packed_f32x2.cuh"
 #include "resample.cuh"
 
@@ -149,6 +156,74 @@ __global__ void __launch_bounds__(k2Threads)
   }
 }
 
+struct GTile2d {
+  float2 t[k2Lines][k2Cols];  // the region, row pitch 32 complex
+};
+
+// One work item of one problem (gather), by one warp.
+__device__ __forceinline__ void gather2d_item(const Geometry& g, const float2* __restrict__ grid,
+                                              const int* __restrict__ cell, const float* __restrict__ frac,
+                                              const int* __restrict__ perm, float2* __restrict__ fhat,
+                                              const int4& item, GTile2d& tl, int lane) {
+  const int64_t M = g.M;
+  int tc[2];
+  tile_coords<2>(g, item.x, tc);
+  const int start0 = tc[0] * g.T[0] + g.off, start1 = tc[1] * g.T[1] + g.off;
+  __syncwarp();  // the previous item's tile is no longer read
+  if (lane < g.L[1]) {
+    const int g1 = wrap_mod(start1 + lane, g.Nt[1]);
+#pragma unroll
+    for (int r = 0; r < k2Lines; ++r)  // independent loads in flight together
+      if (r < g.L[0]) tl.t[r][lane] = grid[(int64_t)wrap_mod(start0 + r, g.Nt[0]) * g.Nt[1] + g1];
+  }
+  __syncwarp();
+  for (int i = lane; i < item.z; i += 32) {
+    const int q = item.y + i;
+    const int a0 = cell[q] - tc[0] * g.T[0], a1 = cell[M + q] - tc[1] * g.T[1];
+    float w0[k2Taps], w1[k2Taps];
+    node_weights<k2Taps, float>(g, 0, 4, frac[q], w0);
+    node_weights<k2Taps, float>(g, 1, 4, frac[M + q], w1);
+    f32x2 w1p[k2Taps];
+#pragma unroll
+    for (int i1 = 0; i1 < k2Taps; ++i1) w1p[i1] = pack2(w1[i1], w1[i1]);
+    f32x2 acc = pack2(0.f, 0.f);
+#pragma unroll
+    for (int i0 = 0; i0 < k2Taps; ++i0) {
+      const f32x2* row = reinterpret_cast<const f32x2*>(&tl.t[a0 + i0][a1]);
+      f32x2 sum = mul2(row[0], w1p[0]);
+#pragma unroll
+      for (int i1 = 1; i1 < k2Taps; ++i1) sum = fma2(row[i1], w1p[i1], sum);
+      acc = fma2(sum, pack2(w0[i0], w0[i0]), acc);
+    }
+    fhat[perm[q]] = unpack2(acc);
+  }
+}
+
+__global__ void __launch_bounds__(k2Threads)
+    gather2d_warp_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na, float2* __restrict__ fhat) {
+  __shared__ GTile2d tiles[k2Warps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = *na.n_items;
+  const float* frac = reinterpret_cast<const float*>(na.frac);
+  for (int it = blockIdx.x * k2Warps + warp; it < nitems; it += gridDim.x * k2Warps)
+    gather2d_item(g, grid, na.cell, frac, na.perm, fhat, na.items[it], tiles[warp], lane);
+}
+
+__global__ void __launch_bounds__(k2Threads)
+    gather2d_warp_batch_kernel(const BatchProblem* __restrict__ probs, const float2* __restrict__ grid,
+                               BatchNodes nb, float2* __restrict__ fhat) {
+  __shared__ GTile2d tiles[k2Warps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = *nb.n_items;
+  const float* frac = reinterpret_cast<const float*>(nb.frac);
+  for (int it = blockIdx.x * k2Warps + warp; it < nitems; it += gridDim.x * k2Warps) {
+    const int4 item = nb.items[it];
+    const BatchProblem& P = probs[item.w];
+    gather2d_item(P.g, grid + P.grid_off, nb.cell + 2 * P.node_off, frac + 2 * P.node_off, nb.perm + P.node_off,
+                  fhat + P.out_off, item, tiles[warp], lane);
+  }
+}
+
 }  // namespace
 
 bool scatter2d_supported(const Geometry& g) {
@@ -173,6 +248,24 @@ cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArray
 cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb, const void* fhat,
                                         int ctas, cudaStream_t s) {
   scatter2d_regacc_batch_kernel<<<ctas, k2Threads, 0, s>>>(probs, (float2*)grid, nb, (const float2*)fhat);
+  return cudaGetLastError();
+}
+
+int gather2d_ctas_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather2d_warp_kernel, k2Threads, 0) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_gather2d_fast(const Geometry& g, const void* grid, const NodeArrays& na, void* fhat, int ctas,
+                                 cudaStream_t s) {
+  gather2d_warp_kernel<<<ctas, k2Threads, 0, s>>>(g, (const float2*)grid, na, (float2*)fhat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather2d_fast_batch(const BatchProblem* probs, const void* grid, const BatchNodes& nb, void* fhat,
+                                       int ctas, cudaStream_t s) {
+  gather2d_warp_batch_kernel<<<ctas, k2Threads, 0, s>>>(probs, (const float2*)grid, nb, (float2*)fhat);
   return cudaGetLastError();
 }
 
