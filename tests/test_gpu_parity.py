@@ -188,6 +188,48 @@ def test_edge_cases(dt):
     assert_close(y, onfft.adjoint(case["k"], case["w"], (64, 64), 2.0, 4), TOL[dt], "hot tile adjoint")
 
 
+@pytest.mark.parametrize("m", [4, 6])
+def test_fast3d_edge_cases(m):
+    """The 3D complex64 fast kernels (m = 4 and 6) with no nodes, one node at
+    the corners of the unit cell, and nodes outside [-1/2, 1/2) (wrapped)."""
+    N = (16, 14, 18)
+    plan = _plan(N, 0, 2.0, m, "c64")
+    plan.set_nodes(torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
+    assert plan.paths()["fast_gather"] and plan.paths()["fast_scatter"]
+    assert plan.forward(to_dev(np.ones(N), torch.complex64)).numel() == 0
+    y = plan.adjoint(torch.zeros(0, dtype=torch.complex64, device="cuda"))
+    assert torch.count_nonzero(y).item() == 0
+    plan.close()
+    for kval in ([-0.5, -0.5, -0.5], [0.5 - 1e-12, 0.25, -0.5], [1.3, -0.7, 2.0], [0.0, 0.0, 0.0]):
+        case = inputs.small_case(N, 1, seed=5, m=m)
+        case["k"] = np.array([kval])
+        fh, y = _run(case, "c64")
+        kw = np.mod(case["k"] + 0.5, 1.0) - 0.5
+        assert_close(fh, onfft.forward(kw, case["f"], 2.0, m), 1e-4, "M=1 forward")
+        assert_close(y, onfft.adjoint(kw, case["w"], N, 2.0, m), 1e-4, "M=1 adjoint")
+
+
+@pytest.mark.parametrize("tile", [(9, 25), (8, 25), (3, 7), (9, 1), (1, 25)])
+def test_fast2d_m4_tile_shapes(tile):
+    """2D, m = 4, complex64: the register-accumulating scatter and the
+    warp-per-item gather (regions up to 16 x 32) on tiles dividing N~ or
+    not, with a hot tile (items split) and boundary nodes."""
+    N = (40, 52)
+    case = inputs.small_case(N, 6000, seed=43, m=4)
+    case["k"][:2000] = 0.03 * case["k"][:2000]
+    case["k"][2000:2200, 0] = -0.5
+    from paper_2208_00049_gb300.nfft import Plan
+    plan = Plan(N, case["M"], sigma=2.0, m=4, dtype=torch.complex64)
+    plan.set_tile(tile)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    assert plan.paths()["fast_gather"] and plan.paths()["fast_scatter"]
+    fh = plan.forward(to_dev(case["f"], torch.complex64)).cpu().numpy()
+    y = plan.adjoint(to_dev(case["w"], torch.complex64)).cpu().numpy()
+    plan.close()
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), 1e-5, "forward")
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), 1e-5, "adjoint")
+
+
 @pytest.mark.parametrize("tile", [(4, 4, 4), (7, 5, 3), (8, 8, 16), (12, 32, 8)])
 def test_tile_shapes_agree(tile):
     """Any tile shape (dividing N~ or not) gives the oracle's result."""
