@@ -482,7 +482,7 @@ def run_tiles(args):
         ("3d sigma=1.25 m=6 uniform M=|I_N|", (128,) * 3, 1.25, 6, inputs.uniform_nodes(rng, n3, 3),
          [(4, 4, 4), (5, 5, 5), (5, 5, 4), (4, 5, 5), (8, 8, 8), (8, 8, 4), (16, 8, 8)]),
         ("2d sigma=2 m=4 uniform M=|I_N|", (256, 256), 2.0, 4, inputs.uniform_nodes(rng, 256 * 256, 2),
-         [(8, 8), (16, 16), (32, 32), (64, 64), (16, 32), (32, 16)]),
+         [(8, 8), (16, 16), (32, 32), (64, 64), (16, 32), (32, 16), (9, 25), (8, 25)]),
     ]
     rows = []
     for name, N, sigma, m, k, tiles in cases:
