@@ -693,6 +693,17 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "tile": list(info["tile"]), "work_items": info["n_items"]},
             "nodes_per_s_resampling_only": world * wl["M"] / (resample_ms * 1e-3),
+            # the three ways of the measurement definition: forward (Algorithm 1),
+            # adjoint (Algorithm 2) and both, with and without the FFT steps;
+            # min / median over the timed steps beside the mean of `value`
+            "per_direction": {
+                "forward_nodes_per_s": world * wl["M"] / ((mean["pad_fft"] + mean["gather"]) * 1e-3),
+                "adjoint_nodes_per_s": world * wl["M"] / ((mean["scatter"] + mean["fft_crop"]) * 1e-3),
+                "gather_nodes_per_s": world * wl["M"] / (mean["gather"] * 1e-3),
+                "scatter_nodes_per_s": world * wl["M"] / (mean["scatter"] * 1e-3),
+                "step_ms_min": round(min(steps_ms), 4),
+                "step_ms_median": round(statistics.median(steps_ms), 4),
+            },
             "set_nodes_ms": round(set_nodes_ms, 3),
             "kernels": kernel_table,
             "fft_forms": fft_forms,
