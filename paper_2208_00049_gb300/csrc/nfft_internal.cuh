@@ -137,6 +137,10 @@ int resample_ctas_per_sm(const Geometry& g, int kind);
 // 3D, m = 4, complex64 warp-per-node kernels (resample3d.cu); `poly` holds
 // the FP32 polynomial window coefficients [3][8][9] (launch_build_poly).
 bool fast3d_supported(const Geometry& g, int cmax);
+// 3D m = 4 complex64 node gradient with the gather's layout (resample3d.cu)
+int grad3d_ctas_per_sm(const Geometry& g);
+cudaError_t launch_grad3d_fast(const Geometry& g, const void* grid, const NodeArrays& na, const float* poly,
+                               const void* cot, void* gk, int ctas, cudaStream_t s);
 // 3D complex64 register-accumulating scatter, m = 4 or 6 (any tile of at
 // most 17 - 2m cells per dimension); kind 1 of the two functions below.
 bool fast_scatter_supported(const Geometry& g, int cmax);

@@ -45,6 +45,7 @@ struct nfft_plan {
   bool fast_scatter = false;   // register-accumulating complex64 scatter (3D m = 4 / 6, 2D m = 4)
   FullMatrix* full = nullptr;  // NFFT_FLAG_FULL_MATRIX: B and B^T as CSR
   int fast_ctas[2] = {0, 0};
+  int grad_ctas = 0;           // 3D m = 4 complex64 node-gradient kernel (0: generic)
   bool pruned = false;         // nfft_step_pad_fft / fft_crop use the pruned 3D FFT
   float2* fft_tw = nullptr;    // its 256 twiddles
 
@@ -327,6 +328,8 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
     p->fast_gather = per_sm > 0;
     p->fast_ctas[0] = per_sm * p->sms;
   }
+  p->grad_ctas = 0;
+  if (p->fast_gather && p->D == 3 && p->K == 8) p->grad_ctas = grad3d_ctas_per_sm(g) * p->sms;
   if (p->fast_scatter) {
     const int per_sm = p->D == 2 ? scatter2d_ctas_per_sm() : fast3d_ctas_per_sm(g, 1);
     p->fast_scatter = per_sm > 0;
@@ -456,7 +459,8 @@ int run_grad_gather(nfft_plan* p, const void* cot, void* gk) {
   Geometry g = make_geometry(p);
   NodeArrays na = node_arrays(p);
   cudaError_t e =
-      p->dtype == NFFT_C128
+      p->grad_ctas > 0 ? launch_grad3d_fast(g, p->grid, na, p->poly, cot, gk, p->grad_ctas, p->stream)
+      : p->dtype == NFFT_C128
           ? launch_grad_gather<double>(g, p->grid, na, cot, gk, p->ctas[3], p->stream)
           : launch_grad_gather<float>(g, p->grid, na, cot, gk, p->ctas[3], p->stream);
   return cuda_status(p, e);

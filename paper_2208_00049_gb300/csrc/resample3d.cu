@@ -218,6 +218,119 @@ __global__ void __launch_bounds__(32 * GW)
 }
 
 // ---------------------------------------------------------------------------
+// Node gradient for m = 4, complex64 (the derivative of Eq. SumOverNode with
+// respect to the node): the gather's tile, half-warp and lane layout, with
+// each tap weighted three ways.  For dimension d the window of that
+// dimension is replaced by its derivative:
+//   D_d = sum_l ghat_l psi'(u_d) prod_{e != d} psi(u_e),
+//   gk[j][d] = N~_d Re(conj(cot_j) D_d).
+// The POLYNOMIAL window gives value and derivative in one Horner pass
+// (d/dk = N~ d/dt, t the fraction of N~ k).
+__device__ __forceinline__ float2 horner_d(const float* c, float zeta) {
+  float p = c[kDeg], dp = 0.f;
+#pragma unroll
+  for (int z = kDeg - 1; z >= 0; --z) {
+    dp = fmaf(dp, zeta, p);
+    p = fmaf(p, zeta, c[z]);
+  }
+  return make_float2(p, dp);
+}
+
+template <int GW>
+__global__ void __launch_bounds__(32 * GW)
+    grad3d_m4_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na, const float* __restrict__ poly,
+                     const float2* __restrict__ cot, float* __restrict__ gk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  NodeStage& ns = *reinterpret_cast<NodeStage*>(smem_raw);
+  float2* tile = reinterpret_cast<float2*>(smem_raw + sizeof(NodeStage));
+  const int L1 = g.L[1];
+  const int plane = L1 * kPitch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = lane >> 4, lane16 = lane & 15;
+  const int grp = lane16 >> 3, i2 = lane & 7;
+  const int hbase = 16 * half;
+  float cA[kCoef], cB[kCoef];
+  load_coef(poly, grp, i2, cA);
+  load_coef(poly, 2, i2, cB);
+  const int nitems = *na.n_items;
+  const int shift = (g.T[2] & 1) ? 0 : 1;
+
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 item = na.items[it];
+    int tc[3], start[3];
+    tile_origin(g, item.x, tc);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
+
+    __syncthreads();
+    load_tile(g, start, grid, tile, warp, lane, GW, shift);
+    stage_nodes(g, na, item, tc, ns, nullptr, threadIdx.x, blockDim.x);
+    cp_async_wait_all();
+    __syncthreads();
+
+    for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * GW) {
+      const int s = min(s0 + half, item.z - 1);  // a half without a node repeats the last one
+      const float word = ns.w[s][lane & 7];
+      const float tA = __shfl_sync(0xffffffffu, word, hbase + grp);
+      const float tB = __shfl_sync(0xffffffffu, word, hbase + 2);
+      const int pk = __float_as_int(__shfl_sync(0xffffffffu, word, hbase + 3));
+      const int jout = __float_as_int(__shfl_sync(0xffffffffu, word, hbase + 4));
+      const float2 A = horner_d(cA, tA - 0.5f);  // tap i2 of dimension grp: value, derivative
+      const float2 Bw = horner_d(cB, tB - 0.5f);  // tap i2 of dimension 2
+      const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
+      // rows j + 4 grp: w1 w2, w1' w2, w1 w2'
+      f32x2 w12[4], d1[4], d2[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float w1 = __shfl_sync(0xffffffffu, A.x, hbase + 8 + j + 4 * grp);
+        const float dw1 = __shfl_sync(0xffffffffu, A.y, hbase + 8 + j + 4 * grp);
+        const float a = w1 * Bw.x, b = dw1 * Bw.x, c = w1 * Bw.y;
+        w12[j] = pack2(a, a);
+        d1[j] = pack2(b, b);
+        d2[j] = pack2(c, c);
+      }
+      const f32x2* p =
+          reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1 + 4 * grp) * kPitch + a2 + i2 + shift);
+      f32x2 D0 = pack2(0.f, 0.f), D1 = D0, D2 = D0;
+#pragma unroll
+      for (int i0 = 0; i0 < kTaps; ++i0) {
+        const float w0 = __shfl_sync(0xffffffffu, A.x, hbase + i0);
+        const float dw0 = __shfl_sync(0xffffffffu, A.y, hbase + i0);
+        const f32x2* q = p + i0 * plane;
+        f32x2 s12 = mul2(q[0], w12[0]), s1 = mul2(q[0], d1[0]), s2 = mul2(q[0], d2[0]);
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+          const f32x2 v = q[j * kPitch];
+          s12 = fma2(v, w12[j], s12);
+          s1 = fma2(v, d1[j], s1);
+          s2 = fma2(v, d2[j], s2);
+        }
+        D0 = fma2(s12, pack2(dw0, dw0), D0);
+        D1 = fma2(s1, pack2(w0, w0), D1);
+        D2 = fma2(s2, pack2(w0, w0), D2);
+      }
+      float2 r0 = unpack2(D0), r1 = unpack2(D1), r2 = unpack2(D2);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        r0.x += __shfl_xor_sync(0xffffffffu, r0.x, o);
+        r0.y += __shfl_xor_sync(0xffffffffu, r0.y, o);
+        r1.x += __shfl_xor_sync(0xffffffffu, r1.x, o);
+        r1.y += __shfl_xor_sync(0xffffffffu, r1.y, o);
+        r2.x += __shfl_xor_sync(0xffffffffu, r2.x, o);
+        r2.y += __shfl_xor_sync(0xffffffffu, r2.y, o);
+      }
+      if (lane16 == 0 && s0 + half < item.z) {
+        const float2 c = cot[jout];
+        float* o = gk + (int64_t)jout * 3;
+        o[0] = (float)g.Nt[0] * (c.x * r0.x + c.y * r0.y);
+        o[1] = (float)g.Nt[1] * (c.x * r1.x + c.y * r1.y);
+        o[2] = (float)g.Nt[2] * (c.x * r2.x + c.y * r2.y);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // W warps share one accumulator tile; warp w updates only the planes
 // i0 = i0a + j W (j = 0 .. 8/W - 1) with (a0 + i0a) = w (mod W).
 template <int W>
@@ -807,6 +920,23 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
   auto kern = reinterpret_cast<void (*)(Geometry, const float2*, NodeArrays, const float*, float2*)>(k);
   kern<<<ctas, 32 * w, smem, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat);
   return cudaGetLastError();
+}
+
+cudaError_t launch_grad3d_fast(const Geometry& g, const void* grid, const NodeArrays& na, const float* poly,
+                               const void* cot, void* gk, int ctas, cudaStream_t s) {
+  const size_t smem = smem_bytes(g);
+  cudaError_t e = set_smem(grad3d_m4_kernel<4>, smem);
+  if (e != cudaSuccess) return e;
+  grad3d_m4_kernel<4><<<ctas, 128, smem, s>>>(g, (const float2*)grid, na, poly, (const float2*)cot, (float*)gk);
+  return cudaGetLastError();
+}
+
+int grad3d_ctas_per_sm(const Geometry& g) {
+  const size_t smem = smem_bytes(g);
+  if (set_smem(grad3d_m4_kernel<4>, smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grad3d_m4_kernel<4>, 128, smem) != cudaSuccess) return 0;
+  return n;
 }
 
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,

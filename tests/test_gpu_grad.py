@@ -45,6 +45,22 @@ def test_grad_matches_oracle(N, M, m, dt):
     assert_close(gk, want, GRAD_TOL[dt], "node gradient")
 
 
+@pytest.mark.parametrize("tile", [(9, 9, 8), (5, 7, 9), (8, 8, 1), (16, 4, 3)])
+def test_grad_3d_m4_tiles(tile):
+    """3D m = 4 complex64: the gather-layout gradient kernel (value and
+    derivative from the POLYNOMIAL window) on several tiles, and the generic
+    kernel where the tile does not fit it (16 x 4 x 3), against the oracle."""
+    N, M = (24, 20, 28), 5000
+    case = inputs.small_case(N, M, seed=47, m=4)
+    cot = inputs.complex_normal(np.random.default_rng(5), (M,))
+    plan = _plan(N, M, 4, "c64")
+    plan.set_tile(tile)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    gk = plan.grad(to_dev(case["f"], torch.complex64), to_dev(cot, torch.complex64)).cpu().numpy()
+    plan.close()
+    assert_close(gk, onfft.node_grad(case["k"], case["f"], cot, 2.0, 4), GRAD_TOL["c64"], "node gradient")
+
+
 def test_grad_against_exact_ndft_derivative():
     N, M = (24, 20), 600
     case = inputs.small_case(N, M, seed=43, m=8)
