@@ -628,6 +628,14 @@ def run_gpu(args):
                  "library_pad_fft_ms": round(time_steps(lib_fwd, nlib, 2, stream, flush), 4),
                  "library_fft_crop_ms": round(time_steps(lib_adj, nlib, 2, stream, flush), 4)}
 
+    # node gradient (row a8) through nfft_grad on the same workload: the
+    # forward's pad_fft plus the derivative gather
+    gk_d = torch.empty((wl["M"], len(wl["N"])), dtype=torch.float32 if dt == torch.complex64 else torch.float64,
+                       device="cuda")
+    grad_ms = time_steps(lambda: B.check(B.nfft_grad(h, f_d.data_ptr(), w_d.data_ptr(), gk_d.data_ptr())),
+                         min(20, max(3, args.steps // 4)), 2, stream, flush)
+    grad_form = {"nodes_per_s": world * wl["M"] / (grad_ms * 1e-3), "ms": round(grad_ms, 4)}
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -707,6 +715,7 @@ def run_gpu(args):
             "set_nodes_ms": round(set_nodes_ms, 3),
             "kernels": kernel_table,
             "fft_forms": fft_forms,
+            "grad_form": grad_form,
             "roofline": roofline,
             "fp64_form": fp64,
             "full_matrix_form": full,
