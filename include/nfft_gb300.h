@@ -157,7 +157,13 @@ void *nfft_plan_grid(nfft_plan *p);
 /* Choose the tile shape (grid cells per tile per dimension) used by the
  * resampling kernels; takes effect at the next nfft_set_nodes.  Used by the
  * autotuner.  Tiles must satisfy 1 <= tile_d <= N~_d and fit the shared
- * memory limit with their halo. */
+ * memory limit with their halo.  The tile also selects the kernels (see
+ * nfft_plan_paths): the specialised complex64 ones need tiles of at most
+ * 9 cells per dimension (3D m = 4; the gather also accepts larger tiles in
+ * dimensions 0 and 1), 5 (3D m = 6) or 9 x 25 (2D m = 4); other tiles run the
+ * generic kernels.  Defaults: 9 x 9 x 8 (3D m = 4), 5 x 5 x 5 (3D m = 6),
+ * 9 x 25 or 8 x 8 (2D m = 4, by grid size), else a power-of-two cube sized
+ * for the node density. */
 int nfft_plan_set_tile(nfft_plan *p, const int64_t *tile3);
 
 /* Algorithm 1 lines 1-3: resampling correction and zero pad of f into the
