@@ -63,6 +63,22 @@ def ndft_adjoint(k, fhat, N):
     return out.reshape(N)
 
 
+def ndft_adjoint_at(k, fhat, N, idx):
+    """Eq. NDFTH at selected outputs only: y at the array indices idx (a tuple
+    of D integer arrays, as from np.unravel_index), for checks at sizes where
+    the full adjoint is out of reach.  Nodes are summed in chunks."""
+    k = np.asarray(k, dtype=np.float64)
+    fhat = np.asarray(fhat, dtype=np.complex128).ravel()
+    n = np.stack([np.asarray(idx[d], dtype=np.float64) - (int(N[d]) // 2) for d in range(len(N))], axis=1)
+    out = np.zeros(n.shape[0], dtype=np.complex128)
+    step = _chunk(k.shape[0], n.shape[0])
+    for s in range(0, k.shape[0], step):
+        ph = n @ k[s:s + step].T
+        ph -= np.floor(ph)
+        out += np.exp(2j * np.pi * ph) @ fhat[s:s + step]
+    return out
+
+
 def ndft_node_derivative(k, f):
     """d fhat_j / d k_{j,d} of the exact NDFT: sum_n f_n (-2 pi i n_d) exp(-2 pi i n.k_j).
 

@@ -233,6 +233,28 @@ def test_fast2d_m4_tile_shapes(tile, sigma):
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, sigma, 4), tol, "adjoint", tmax)
 
 
+def test_large_3d_against_ndft_samples():
+    """A larger 3D plan (N = 256 x 256 x 128, N~ = 512 x 512 x 256, M = 4 194 304
+    nodes, the default specialised kernels) against the exact NDFT on
+    sampled outputs: 32 forward values and 32 adjoint values."""
+    N = (256, 256, 128)
+    rng = np.random.default_rng(2208 + 9)
+    M = int(np.prod(N)) // 2
+    k = inputs.uniform_nodes(rng, M, 3)
+    f = inputs.complex_normal(rng, N, dtype=np.complex64)
+    w = inputs.complex_normal(rng, (M,), dtype=np.complex64)
+    plan = _plan(N, M, 2.0, 4, "c64")
+    plan.set_nodes(to_dev(k, torch.float64))
+    assert plan.paths()["fast_gather"] and plan.paths()["fast_scatter"]
+    fh = plan.forward(to_dev(f, torch.complex64)).cpu().numpy()
+    y = plan.adjoint(to_dev(w, torch.complex64)).cpu().numpy()
+    plan.close()
+    sel = rng.choice(M, 32, replace=False)
+    assert_close(fh[sel], ondft.ndft(k[sel], f), 1e-5, "forward vs NDFT")
+    idx = np.unravel_index(rng.choice(int(np.prod(N)), 32, replace=False), N)
+    assert_close(y[idx], ondft.ndft_adjoint_at(k, w, N, idx), 1e-5, "adjoint vs NDFT")
+
+
 @pytest.mark.parametrize("tile", [(4, 4, 4), (7, 5, 3), (8, 8, 16), (12, 32, 8)])
 def test_tile_shapes_agree(tile):
     """Any tile shape (dividing N~ or not) gives the oracle's result."""

@@ -112,3 +112,23 @@ def test_node_grad_convention():
         lp = np.real(np.vdot(cot, ndft.ndft(kp, f)))
         lm = np.real(np.vdot(cot, ndft.ndft(km, f)))
         assert g[j, 0] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-8)
+
+
+def test_adjoint_at_selected_outputs():
+    """ndft_adjoint_at equals the full adjoint at the selected outputs (odd and
+    even N), and reduces to the single-node closed form y_n = fhat e^{2 pi i n.k}."""
+    rng = np.random.default_rng(17)
+    for N in [(7, 6), (5, 4, 3)]:
+        M = 40
+        k = rng.random((M, len(N))) - 0.5
+        w = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+        full = ndft.ndft_adjoint(k, w, N)
+        flat = rng.choice(int(np.prod(N)), 9, replace=False)
+        idx = np.unravel_index(flat, N)
+        assert np.allclose(ndft.ndft_adjoint_at(k, w, N, idx), full[idx], rtol=0, atol=1e-12)
+    k1 = np.array([[0.3, -0.15]])
+    idx = (np.array([0, 3]), np.array([5, 1]))
+    n = np.stack([idx[0] - 4, idx[1] - 3], axis=1)
+    want = 2.0 * np.exp(2j * np.pi * (n @ k1[0]))
+    assert np.allclose(ndft.ndft_adjoint_at(k1, np.array([2.0]), (8, 7), idx), want, rtol=0, atol=1e-13)
+
