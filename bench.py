@@ -87,13 +87,40 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def _strip_comments(src):
+    """C/C++ source without comments and with whitespace runs collapsed:
+    what the compiler sees, so that editing a comment keeps the hash."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":  # string or character literal, copied whole
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash():
+    """Hash of the kernel sources (comments and layout excluded), recorded in
+    the committed ncu summaries beside the counters taken from that code."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2208_00049_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+            with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+                h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -552,7 +579,8 @@ def run_gpu(args):
 
     h = plan.handle
     paths = plan.paths()
-    # Algorithm 1 lines 1-6 | 7-9, Algorithm 2 lines 1-3 | 4-10
+    # Algorithm 1: correction + zero pad + FFT | resampling; Algorithm 2:
+    # adjoint resampling | inverse FFT + crop + correction
     names = ["pad_fft", "gather", "scatter", "fft_crop"]
     nev = len(names) + 1
 
@@ -612,8 +640,8 @@ def run_gpu(args):
         kernel_table[n] = {"ms": round(mean[n], 4), "GBps": round(ab / (mean[n] * 1e-3) / 1e9, 1),
                            "hbm_frac": round(ab / (mean[n] * 1e-3) / 1e9 / peak, 4)}
 
-    # the same Algorithm 1 lines 1-6 / Algorithm 2 lines 4-10 as separate
-    # correction kernels around cuFFT (the form the pruned FFT replaces)
+    # the same FFT steps of Algorithms 1 and 2 as separate correction kernels
+    # around cuFFT (the form the pruned FFT replaces)
     def lib_fwd():
         B.check(B.nfft_step_deconv_pad(h, f_d.data_ptr()))
         B.check(B.nfft_step_fft(h, -1))

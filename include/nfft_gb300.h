@@ -74,8 +74,9 @@ extern "C" {
    accurate than 2m points at the same m (Sec. 5.1).  Exclusive with
    NFFT_FLAG_CLOSED_SUPPORT. */
 #define NFFT_FLAG_WIDE_WINDOW     0x8u
-/* Run Algorithm 1 lines 1-6 and Algorithm 2 lines 4-10 as the separate
-   correction kernels around a full cuFFT transform even where the plan
+/* Run the correction + zero-pad + FFT steps of Algorithm 1 and the inverse
+   FFT + crop + correction steps of Algorithm 2 as the separate correction
+   kernels around a full cuFFT transform even where the plan
    qualifies for the pruned FFT (see nfft_step_pad_fft). */
 #define NFFT_FLAG_LIBRARY_FFT     0x10u
 
@@ -166,28 +167,32 @@ void *nfft_plan_grid(nfft_plan *p);
  * for the node density. */
 int nfft_plan_set_tile(nfft_plan *p, const int64_t *tile3);
 
-/* Algorithm 1 lines 1-3: resampling correction and zero pad of f into the
- * plan grid (fftshift folded into the index map, Sec. 3.5). */
+/* Algorithm 1, correction and zero-pad step: resampling correction and zero
+ * pad of f into the plan grid (fftshift folded into the index map,
+ * Sec. 3.5). */
 int nfft_step_deconv_pad(nfft_plan *p, const void *f);
 
-/* Algorithm 1 lines 4-6 (sign = -1, cuFFT FORWARD) or Algorithm 2 lines 4-6
- * (sign = +1, cuFFT INVERSE, unnormalised), in place on the plan grid. */
+/* The FFT step of Algorithm 1 (sign = -1, cuFFT FORWARD) or the inverse FFT
+ * step of Algorithm 2 (sign = +1, cuFFT INVERSE, unnormalised), in place on
+ * the plan grid. */
 int nfft_step_fft(nfft_plan *p, int sign);
 
-/* Algorithm 1 lines 7-9 / Algorithm 3: block-partitioned resampling
+/* Algorithm 1, resampling step (Algorithm 3): block-partitioned resampling
  * (gather) from the plan grid to fhat (M complex, caller order). */
 int nfft_step_gather(nfft_plan *p, void *fhat);
 
-/* Algorithm 2 lines 1-3 / Algorithm 4: block-partitioned adjoint resampling
- * (scatter) of fhat onto the plan grid; the grid is cleared first. */
+/* Algorithm 2, adjoint resampling step (Algorithm 4): block-partitioned
+ * adjoint resampling (scatter) of fhat onto the plan grid; the grid is
+ * cleared first. */
 int nfft_step_scatter(nfft_plan *p, const void *fhat);
 
-/* Algorithm 2 lines 8-10: crop of the plan grid to I_N and resampling
- * correction into y. */
+/* Algorithm 2, crop and correction step: crop of the plan grid to I_N and
+ * resampling correction into y. */
 int nfft_step_crop_deconv(nfft_plan *p, void *y);
 
-/* Algorithm 1 lines 1-6 in one call: correction, zero pad and forward FFT
- * of f into the plan grid (the grid then holds ghat as after
+/* Algorithm 1, correction + zero-pad + FFT steps in one call: correction,
+ * zero pad and forward FFT of f into the plan grid (the grid then holds
+ * ghat as after
  * nfft_step_deconv_pad + nfft_step_fft(-1)).  For D = 3, complex64 and
  * N~_d = 2 N_d = 256 (and without NFFT_FLAG_LIBRARY_FFT) this is the pruned
  * FFT: three passes of 256-point line DFTs that read only the non-zero part
@@ -196,8 +201,9 @@ int nfft_step_crop_deconv(nfft_plan *p, void *y);
  * it runs the two separate steps. */
 int nfft_step_pad_fft(nfft_plan *p, const void *f);
 
-/* Algorithm 2 lines 4-10 in one call: unnormalised inverse FFT of the plan
- * grid, crop to I_N and correction into y.  Pruned as for nfft_step_pad_fft
+/* Algorithm 2, inverse FFT + crop + correction steps in one call:
+ * unnormalised inverse FFT of the plan grid, crop to I_N and correction into
+ * y.  Pruned as for nfft_step_pad_fft
  * (each inverse pass computes only the N outputs that are kept; the plan
  * grid is used as scratch and does not hold the full inverse FFT
  * afterwards); otherwise nfft_step_fft(+1) + nfft_step_crop_deconv. */
@@ -268,7 +274,7 @@ int nfft_batch_autotune(nfft_batch *b, const void *k, int k_is_fp64, int64_t *ch
  * fragments memory and may synchronise the device), and services whose
  * device memory must be reserved when the library loads.
  *
- * It performs the adjoint resampling of Algorithm 2 lines 1-3 (complex64,
+ * It performs the adjoint resampling step of Algorithm 2 (complex64,
  * half-open support, 2m taps per dimension) without a plan:
  *   grid[l] = sum_j fhat_j prod_d w_d(N~_d k_{j,d} - l_d),
  * with the Kaiser-Bessel window scaled to 1 at u = 0 (the same quantity

@@ -14,8 +14,9 @@ arXiv 2208.00049, Sec. 2.2:
 Storage: a grid index l in I_N~ lives at position (l mod N~) of an
 (N~_1, ..., N~_D) array, which is the natural order of numpy.fft (the
 fftshift of Sec. 3.5 folded into the index map).  numpy.fft.fftn is the
-unnormalised exp(-2 pi i) transform of step 2; numpy.fft.ifftn with
-norm="forward" is the unnormalised exp(+2 pi i) transform of Alg. 2 step 2.
+unnormalised exp(-2 pi i) transform of the FFT step of Algorithm 1;
+numpy.fft.ifftn with norm="forward" is the unnormalised exp(+2 pi i)
+transform of the adjoint FFT step of Algorithm 2.
 
 Footprint I_{N~,m}(k) (Sec. 2.2, definition after Eq. approxNFFT2): the grid
 indices l with -m <= N~ k - l + p N~ < m for some integer p.  For the
@@ -88,7 +89,8 @@ def _positions(p):
 
 
 def correction_pad(p, f):
-    """Alg. 1 lines 1-3: g on I_N~ with g_n = f_n/(|I_N~| phi(n)) on I_N, else 0."""
+    """Algorithm 1, correction and zero-pad step: g on I_N~ with
+    g_n = f_n/(|I_N~| phi(n)) on I_N, else 0."""
     f = np.asarray(f, dtype=np.complex128)
     if f.shape != p.N:
         raise ValueError("f has the wrong shape")
@@ -98,7 +100,7 @@ def correction_pad(p, f):
 
 
 def crop_correction(p, g):
-    """Alg. 2 lines 8-10: y_n = g_n/(|I_N~| phi(n)) for n in I_N."""
+    """Algorithm 2, crop and correction step: y_n = g_n/(|I_N~| phi(n)) for n in I_N."""
     return g[np.ix_(*_positions(p))] * _outer(_correction(p))
 
 
@@ -119,7 +121,8 @@ def footprint(p, k):
 
 
 def resample(p, k, ghat):
-    """Alg. 1 lines 7-9 (Eq. SumOverNode): fhat_j = sum_l ghat_l psi~(k_j - l/N~)."""
+    """Algorithm 1, resampling step (Eq. SumOverNode):
+    fhat_j = sum_l ghat_l psi~(k_j - l/N~)."""
     ls, us = footprint(p, k)
     w = [p.window(u, b) for u, b in zip(us, p.b)]
     M = ls[0].shape[0]
@@ -134,7 +137,7 @@ def resample(p, k, ghat):
 
 
 def resample_adjoint(p, k, fhat):
-    """Alg. 2 lines 1-3 (Eq. SumOverNodeAdjoint), evaluated node by node as
+    """Algorithm 2, adjoint resampling step (Eq. SumOverNodeAdjoint), evaluated node by node as
     Sec. 2.2.2 describes: every node adds fhat_j psi~ into its footprint."""
     fhat = np.asarray(fhat, dtype=np.complex128).ravel()
     ls, us = footprint(p, k)
@@ -152,12 +155,12 @@ def resample_adjoint(p, k, fhat):
 
 
 def fft_forward(g):
-    """Alg. 1 lines 4-6: unnormalised exp(-2 pi i) DFT on the oversampled grid."""
+    """Algorithm 1, FFT step: unnormalised exp(-2 pi i) DFT on the oversampled grid."""
     return np.fft.fftn(g)
 
 
 def fft_adjoint(ghat):
-    """Alg. 2 lines 4-6: unnormalised exp(+2 pi i) DFT on the oversampled grid."""
+    """Algorithm 2, inverse FFT step: unnormalised exp(+2 pi i) DFT on the oversampled grid."""
     return np.fft.ifftn(ghat, norm="forward")
 
 
@@ -179,7 +182,7 @@ def adjoint(k, fhat, N, sigma=2.0, m=4, closed=False, wide=False):
 
 
 def resample_node_derivative(p, k, ghat):
-    """d/dk_{j,d} of Alg. 1 step 3: sum_l ghat_l N~_d psi'(u_d) prod_{e != d} psi(u_e).
+    """d/dk_{j,d} of the resampling step of Algorithm 1: sum_l ghat_l N~_d psi'(u_d) prod_{e != d} psi(u_e).
 
     Differentiates Eq. SumOverNode through u_d = N~_d k_{j,d} - l_d with the
     footprint held fixed (the window vanishes at the footprint's open end).

@@ -1,17 +1,18 @@
 // Pruned 3D FFT with the resampling correction fused in, for N~ = 2N = 256 per
-// dimension (complex64): Algorithm 1 lines 1-6 and Algorithm 2 lines 4-10 in
-// three one-dimensional passes each.
+// dimension (complex64): the correction + zero-pad + FFT steps of Algorithm 1
+// and the inverse FFT + crop + correction steps of Algorithm 2 in three
+// one-dimensional passes each.
 //
-// Forward.  g is non-zero only on I_N (Algorithm 1 lines 1-3), so the 3D DFT
-// (lines 4-6) factorises into passes that each touch only non-zero data:
+// Forward.  g is non-zero only on I_N (after the zero pad), so the 3D DFT of
+// the FFT step factorises into passes that each touch only non-zero data:
 //   A: rows (i0, i1) in [0,N)^2:   read f * beta, DFT along dim 2   -> N x N x N~
 //   B: lines (i0, l2), i0 < N:     DFT along dim 1                  -> N x N~ x N~
 //   C: lines (l1, l2):             DFT along dim 0                  -> N~ x N~ x N~
 // Each line holds its N inputs at array index i = n + N/2; the fftshift of
 // Sec. 3.5 becomes the exact post-phase exp(i pi N l / N~) = i^l (N~ = 2N).
-// Adjoint (lines 4-10): the same passes in reverse keep only the N outputs of
-// each inverse DFT, with the pre-phase (-i)^l, and the last pass multiplies by
-// the correction and writes y.  HBM traffic: 352 MB per direction at N = 128
+// Adjoint (inverse FFT, crop, correction): the same passes in reverse keep
+// only the N outputs of each inverse DFT, with the pre-phase (-i)^l, and the
+// last pass multiplies by the correction and writes y.  HBM traffic: 352 MB per direction at N = 128
 // against about 950 MB for a separate correction pass plus a full 3D FFT.
 //
 // A 256-point line DFT is 16 x 16: thread r of the line's 16 takes the

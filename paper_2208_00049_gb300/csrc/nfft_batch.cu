@@ -43,6 +43,7 @@ struct nfft_batch {
   std::vector<int64_t> M_set, node_off; // [S]
   std::vector<int64_t> grid_off, in_off, out_off, beta_off;  // [B]
   int64_t grid_total = 0, in_total = 0, out_total = 0, node_total = 0, beta_total = 0;
+  int64_t poly_per = 0;                 // POLYNOMIAL coefficients per problem (0: not built)
   int64_t max_grid = 0, max_n = 0, max_set_nodes = 0, max_tiles = 0;
   std::vector<int> set_tiles;           // tiles of each node set
   std::vector<int64_t> set_item_base;   // offsets into set_items
@@ -60,6 +61,7 @@ struct nfft_batch {
   void* grid = nullptr;
   double* beta64 = nullptr;
   float* beta32 = nullptr;
+  float* poly = nullptr;  // [B][D][K][2m + 1], built for the standard (2m-tap) window only
   BatchProblem* probs = nullptr;
   std::vector<BatchProblem> probs_host;
   int* cell = nullptr;
@@ -174,6 +176,7 @@ int configure(nfft_batch* b) {
     P.out_off = b->out_off[p];
     P.in_off = b->in_off[p];
     P.beta_off = b->beta_off[p];
+    P.poly_off = p * b->poly_per;
     b->probs_host[p] = P;
     int64_t nt = 1;
     for (int d = 0; d < b->D; ++d) nt *= P.g.ntile[d];
@@ -214,7 +217,7 @@ int configure(nfft_batch* b) {
     if (per <= 0) return NFFT_ERR_UNSUPPORTED;
     b->ctas[kind] = per * b->sms;
   }
-  b->fast_scatter = b->D == 2 && b->dtype == NFFT_C64 && !(b->flags & NFFT_FLAG_COMPENSATED);
+  b->fast_scatter = b->D == 2 && b->dtype == NFFT_C64 && !(b->flags & NFFT_FLAG_COMPENSATED) && b->poly_per > 0;
   for (int p = 0; p < b->B && b->fast_scatter; ++p) b->fast_scatter = scatter2d_supported(b->probs_host[p].g);
   if (b->fast_scatter) {
     const int per = scatter2d_ctas_per_sm(), per_g = gather2d_ctas_per_sm();
@@ -321,7 +324,7 @@ int enqueue_forward(nfft_batch* b, const void* f, void* fhat, cudaStream_t st) {
   int s = run_fft_classes(b, -1, st);
   if (s != NFFT_OK) return s;
   e = b->fast_scatter
-          ? launch_gather2d_fast_batch(b->probs, b->grid, batch_nodes(b), fhat, b->fast_gather_ctas, st)
+          ? launch_gather2d_fast_batch(b->probs, b->grid, batch_nodes(b), b->poly, fhat, b->fast_gather_ctas, st)
       : b->dtype == NFFT_C128
           ? launch_gather_batch<double>(b->probs, gm, b->grid, batch_nodes(b), fhat, b->ctas[0], st)
           : launch_gather_batch<float>(b->probs, gm, b->grid, batch_nodes(b), fhat, b->ctas[0], st);
@@ -333,7 +336,7 @@ int enqueue_adjoint(nfft_batch* b, const void* fhat, void* y, cudaStream_t st) {
   const Geometry gm = max_geometry(b);
   B_CK(b, cudaMemsetAsync(b->grid, 0, (size_t)b->grid_total * csize(b->dtype), st));
   cudaError_t e = b->fast_scatter
-                      ? launch_scatter2d_fast_batch(b->probs, b->grid, batch_nodes(b), fhat, b->fast_ctas, st)
+                      ? launch_scatter2d_fast_batch(b->probs, b->grid, batch_nodes(b), b->poly, fhat, b->fast_ctas, st)
                   : b->dtype == NFFT_C128
                       ? launch_scatter_batch<double>(b->probs, gm, b->grid, batch_nodes(b), fhat, b->ctas[1], st)
                       : launch_scatter_batch<float>(b->probs, gm, b->grid, batch_nodes(b), fhat, b->ctas[1], st);
@@ -439,7 +442,7 @@ int nfft_batch_destroy(nfft_batch* b) {
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   for (auto& c : b->classes)
     if (c.ok) cufftDestroy(c.plan);
-  void* bufs[] = {b->grid, b->beta64, b->beta32, b->probs, b->cell, b->frac, b->perm, b->key, b->rank,
+  void* bufs[] = {b->grid, b->beta64, b->beta32, b->poly, b->probs, b->cell, b->frac, b->perm, b->key, b->rank,
                   b->tile_count, b->tile_offset, b->set_items, b->set_nitems, b->items, b->n_items,
                   b->item_off};
   for (void* p : bufs)
@@ -570,6 +573,9 @@ int nfft_batch_create(nfft_batch** out, int D, int B, const int64_t* N, const in
   if (st == NFFT_OK) st = balloc(b, &b->grid, (size_t)b->grid_total * csize(dtype));
   if (st == NFFT_OK) st = balloc(b, &b->beta64, sizeof(double) * b->beta_total);
   if (st == NFFT_OK) st = balloc(b, &b->beta32, sizeof(float) * b->beta_total);
+  const bool std_window = !(flags & (NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
+  if (std_window) b->poly_per = (int64_t)D * b->K * (2 * m + 1);
+  if (st == NFFT_OK && std_window) st = balloc(b, &b->poly, sizeof(float) * B * b->poly_per);
   if (st == NFFT_OK) st = balloc(b, &b->probs, sizeof(BatchProblem) * B);
   if (st == NFFT_OK) st = balloc(b, &b->cell, sizeof(int) * (size_t)(b->node_total * D));
   if (st == NFFT_OK) st = balloc(b, &b->frac, rsize(dtype) * (size_t)(b->node_total * D));
@@ -605,6 +611,16 @@ int nfft_batch_create(nfft_batch** out, int D, int B, const int64_t* N, const in
     }
     st = bst(b, launch_build_beta(D, Ni, Nti, m, bb, b->beta64 + b->beta_off[p], b->beta32 + b->beta_off[p],
                                   b->stream));
+    if (st == NFFT_OK && b->poly) {
+      PolyArgs pa{};
+      pa.D = D;
+      pa.K = b->K;
+      pa.off = b->off;
+      pa.deg = 2 * m;
+      pa.m = m;
+      for (int d = 0; d < D; ++d) pa.b[d] = bb[d];
+      st = bst(b, launch_build_poly(pa, b->poly + p * b->poly_per, b->stream));
+    }
   }
   if (st == NFFT_OK) {
     default_batch_tile(b, b->T);

@@ -103,6 +103,7 @@ struct BatchProblem {
   int64_t out_off;   // offset of this problem's fhat in the concatenated fhat buffer
   int64_t in_off;    // offset of this problem's f / y in the concatenated coefficient buffer
   int64_t beta_off;  // offset of this problem's deconvolution vectors
+  int64_t poly_off;  // offset of this problem's POLYNOMIAL coefficients
 };
 struct BatchNodes {
   const int* cell;
@@ -166,14 +167,16 @@ cudaError_t launch_pruned_adjoint(void* grid, const float* const* beta, const fl
 bool scatter2d_supported(const Geometry& g);
 int scatter2d_ctas_per_sm();
 int gather2d_ctas_per_sm();
-cudaError_t launch_gather2d_fast(const Geometry& g, const void* grid, const NodeArrays& na, void* fhat, int ctas,
-                                 cudaStream_t s);
-cudaError_t launch_gather2d_fast_batch(const BatchProblem* probs, const void* grid, const BatchNodes& nb, void* fhat,
-                                       int ctas, cudaStream_t s);
-cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat, int ctas,
-                                  cudaStream_t s);
-cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb, const void* fhat,
-                                        int ctas, cudaStream_t s);
+// poly: POLYNOMIAL coefficients [D][K][2m + 1] of the plan, or of all
+// problems of a batch (problem p's table at poly + probs[p].poly_off).
+cudaError_t launch_gather2d_fast(const Geometry& g, const void* grid, const NodeArrays& na, const float* poly,
+                                 void* fhat, int ctas, cudaStream_t s);
+cudaError_t launch_gather2d_fast_batch(const BatchProblem* probs, const void* grid, const BatchNodes& nb,
+                                       const float* poly, void* fhat, int ctas, cudaStream_t s);
+cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArrays& na, const float* poly,
+                                  const void* fhat, int ctas, cudaStream_t s);
+cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb,
+                                        const float* poly, const void* fhat, int ctas, cudaStream_t s);
 
 // FULL precomputation: B as a CSR matrix, applied with cuSPARSE (nfft_full.cu)
 struct FullMatrix;

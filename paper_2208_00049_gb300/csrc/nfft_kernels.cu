@@ -1,8 +1,9 @@
 // Deconvolution (resampling correction), plan-time tables and node bin-sort.
 //
 // arXiv 2208.00049:
-//  * Algorithm 1 lines 1-3 and Algorithm 2 lines 8-10: the resampling
-//    correction 1/(|I_N~| phi(n)) with zero pad (direct) or crop (adjoint);
+//  * Algorithm 1 (correction and zero-pad step) and Algorithm 2 (crop and
+//    correction step): the resampling correction 1/(|I_N~| phi(n)) with zero
+//    pad (direct) or crop (adjoint);
 //    Sec. 3.5 folds the fftshift into the index map and factorises the
 //    correction into per-dimension vectors beta_d (O(sum N_d) memory).
 //  * Sec. 3.7.3: nodes are grouped by the grid block they fall in (the sets
@@ -148,8 +149,8 @@ cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1 lines 1-3: g[p] = f_n * prod_d beta_d(n_d) where the grid
-// position p_d = n_d mod N~_d, zero at every other position.  One thread
+// Algorithm 1, correction and zero-pad step: g[p] = f_n * prod_d beta_d(n_d)
+// where the grid position p_d = n_d mod N~_d, zero at every other position.  One thread
 // writes two adjacent grid points (16 B for complex64) of the last dimension.
 // ---------------------------------------------------------------------------
 template <int D, typename R>
@@ -248,7 +249,8 @@ __global__ void deconv_pad_batch_kernel(const BatchProblem* __restrict__ probs, 
   deconv_pad_body<D, R>(a, f + P.in_off, grid + P.grid_off);
 }
 
-// Algorithm 2 lines 8-10: y_n = g[n mod N~] * prod_d beta_d(n_d), n in I_N.
+// Algorithm 2, crop and correction step: y_n = g[n mod N~] * prod_d beta_d(n_d),
+// n in I_N.
 template <int D, typename R>
 __device__ __forceinline__ void crop_deconv_body(const DeconvArgs& a, const typename Cplx<R>::type* __restrict__ grid,
                                                  typename Cplx<R>::type* __restrict__ y) {

@@ -390,7 +390,7 @@ int run_gather(nfft_plan* p, void* fhat) {
   NodeArrays na = node_arrays(p);
   if (p->full) return latch(p, full_forward(p->full, p->grid, fhat, p->stream));
   cudaError_t e = p->fast_gather
-                      ? (p->D == 2 ? launch_gather2d_fast(g, p->grid, na, fhat, p->fast_ctas[0], p->stream)
+                      ? (p->D == 2 ? launch_gather2d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[0], p->stream)
                                    : launch_gather3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[0], p->stream))
                   : p->dtype == NFFT_C128
                       ? launch_gather<double>(g, p->grid, na, fhat, p->ctas[0], p->stream)
@@ -406,7 +406,7 @@ int run_scatter(nfft_plan* p, const void* fhat) {
   const int comp = (p->flags & NFFT_FLAG_COMPENSATED) && p->dtype == NFFT_C64 ? 1 : 0;
   cudaError_t e =
       p->fast_scatter
-          ? (p->D == 2 ? launch_scatter2d_fast(g, p->grid, na, fhat, p->fast_ctas[1], p->stream)
+          ? (p->D == 2 ? launch_scatter2d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[1], p->stream)
                        : launch_scatter3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[1], p->stream))
       : p->dtype == NFFT_C128
           ? launch_scatter<double>(g, p->grid, na, fhat, 0, p->ctas[1], p->stream)
@@ -423,8 +423,8 @@ const float* const* beta32_dims(const nfft_plan* p, const float** out) {
   return out;
 }
 
-// Algorithm 1 lines 1-6: pruned FFT where the plan qualifies, else the
-// correction kernel and cuFFT.
+// Algorithm 1, correction + zero-pad + FFT steps: pruned FFT where the plan
+// qualifies, else the correction kernel and cuFFT.
 int run_pad_fft(nfft_plan* p, const void* f) {
   if (p->pruned) {
     const float* beta[kMaxD];
@@ -437,7 +437,7 @@ int run_pad_fft(nfft_plan* p, const void* f) {
 
 int run_crop_deconv(nfft_plan* p, void* y);
 
-// Algorithm 2 lines 4-10.
+// Algorithm 2, inverse FFT + crop + correction steps.
 int run_fft_crop(nfft_plan* p, void* y) {
   if (p->pruned) {
     const float* beta[kMaxD];

@@ -28,4 +28,14 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
   return d;
 }
 
+// A shared-memory load of a pair that the compiler keeps where it is written:
+// it is neither hoisted out of a loop nor merged, for tables whose values
+// would otherwise be held in registers for the whole loop at the cost of
+// occupancy.
+__device__ __forceinline__ f32x2 lds_f32x2(const f32x2* p) {
+  f32x2 r;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(r) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+  return r;
+}
+
 }  // namespace nfftgb

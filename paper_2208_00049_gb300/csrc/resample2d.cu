@@ -13,10 +13,15 @@
 //
 // Each warp works on its own work items (no block-wide barriers): per chunk
 // of 32 nodes, lane i loads node i (cells, fractions, value), evaluates its
-// 16 window values (the direct Kaiser-Bessel form of the generic kernels),
-// and writes them at its bin slot in the warp's stage; the warp then runs
-// over the bins.  After the item's last chunk the region is added to the grid
-// with vector global reductions (periodic wrap only there).
+// 16 window values and writes them at its bin slot in the warp's stage; the
+// warp then runs over the bins.  After the item's last chunk the region is
+// added to the grid with vector global reductions (periodic wrap only there).
+//
+// Window values come from the POLYNOMIAL representation (Sec. 3.7.4): the
+// problem's coefficient table is copied into the warp's shared memory as
+// (tap 2p, tap 2p + 1) pairs per item, and a lane evaluates the 16 values of
+// its own node as 8 packed Horner chains of degree 2m whose coefficient loads
+// are warp-wide broadcasts.
 //
 // The gather keeps the same one-warp-per-item structure (no block-wide
 // barriers): the warp copies its item's region (<= 16 x 32) into its own
@@ -35,12 +40,40 @@ constexpr int k2Cols = 32;                  // one region column per lane, L1 <=
 constexpr int k2Warps = 4;                  // independent warps per CTA
 constexpr int k2Threads = 32 * k2Warps;
 constexpr int k2Bins = 9;                   // a0 < T0 <= 9
+constexpr int k2Deg = 2 * 4;                // POLYNOMIAL degree 2m
+constexpr int k2Pairs = k2Taps / 2;
+
+// POLYNOMIAL coefficients of one problem, (tap 2p, tap 2p + 1) pairs.
+struct Poly2d {
+  f32x2 c[2][k2Pairs][k2Deg + 1];
+};
+
+// Copies the coefficient table coef[(d * K + i) * (deg + 1) + z] (built by
+// the plan or batch at creation) into the warp's pairs.
+__device__ __forceinline__ void load_poly2d(const float* __restrict__ poly, Poly2d& pc, int lane) {
+  constexpr int Z = k2Deg + 1;
+  for (int e = lane; e < 2 * k2Pairs * Z; e += 32) {
+    const int d = e / (k2Pairs * Z), p = (e / Z) % k2Pairs, z = e % Z;
+    pc.c[d][p][z] = pack2(poly[(d * k2Taps + 2 * p) * Z + z], poly[(d * k2Taps + 2 * p + 1) * Z + z]);
+  }
+}
+
+// Window values of taps 2p, 2p + 1 of dimension d at zeta = t - 1/2.
+// The coefficients are read from shared memory at every use (lds_f32x2):
+// held in registers across the node loop they would cost 144 registers.
+__device__ __forceinline__ f32x2 poly2d_pair(const Poly2d& pc, int d, int p, f32x2 zz) {
+  f32x2 w = lds_f32x2(&pc.c[d][p][k2Deg]);
+#pragma unroll
+  for (int z = k2Deg - 1; z >= 0; --z) w = fma2(w, zz, lds_f32x2(&pc.c[d][p][z]));
+  return w;
+}
 
 struct Stage2d {
-  f32x2 w0p[32][k2Taps];  // (w0, w0) pairs, by slot
+  float w0[32][k2Taps];   // by slot (paired in registers: half the shared wavefronts of stored pairs)
   float w1[32][k2Taps];
   f32x2 v[32];
   int a1[32];
+  Poly2d pc;
 };
 
 template <int A0>
@@ -52,12 +85,14 @@ __device__ __forceinline__ void scatter2d_bin(const Stage2d& st, int s0, int s1,
       const float wv = st.w1[s][i1 & (k2Taps - 1)];
       const float p = (unsigned)i1 < (unsigned)k2Taps ? wv : 0.f;
       const f32x2 vp = mul2(st.v[s], pack2(p, p));
-      const float4* wq = reinterpret_cast<const float4*>(&st.w0p[s][0]);
+      const float4* wq = reinterpret_cast<const float4*>(&st.w0[s][0]);
 #pragma unroll
-      for (int q = 0; q < k2Taps / 2; ++q) {
+      for (int q = 0; q < k2Taps / 4; ++q) {
         const float4 x = wq[q];
-        acc[A0 + 2 * q] = fma2(vp, pack2(x.x, x.y), acc[A0 + 2 * q]);
-        acc[A0 + 2 * q + 1] = fma2(vp, pack2(x.z, x.w), acc[A0 + 2 * q + 1]);
+        acc[A0 + 4 * q] = fma2(vp, pack2(x.x, x.x), acc[A0 + 4 * q]);
+        acc[A0 + 4 * q + 1] = fma2(vp, pack2(x.y, x.y), acc[A0 + 4 * q + 1]);
+        acc[A0 + 4 * q + 2] = fma2(vp, pack2(x.z, x.z), acc[A0 + 4 * q + 2]);
+        acc[A0 + 4 * q + 3] = fma2(vp, pack2(x.w, x.w), acc[A0 + 4 * q + 3]);
       }
     }
   }
@@ -67,7 +102,8 @@ __device__ __forceinline__ void scatter2d_bin(const Stage2d& st, int s0, int s1,
 __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __restrict__ grid,
                                                const int* __restrict__ cell, const float* __restrict__ frac,
                                                const int* __restrict__ perm, const float2* __restrict__ fhat,
-                                               const int4& item, Stage2d& st, int lane) {
+                                               const float* __restrict__ poly, const int4& item, Stage2d& st,
+                                               int lane) {
   const int64_t M = g.M;
   int tc[2];
   tile_coords<2>(g, item.x, tc);
@@ -76,6 +112,8 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
   f32x2 acc[k2Lines];
 #pragma unroll
   for (int r = 0; r < k2Lines; ++r) acc[r] = pack2(0.f, 0.f);
+  __syncwarp();  // the previous item's coefficients are no longer read
+  load_poly2d(poly, st.pc, lane);
 
   for (int base = 0; base < item.z; base += 32) {
     const bool valid = base + lane < item.z;
@@ -94,14 +132,13 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
     bs[k2Bins] = run;
     __syncwarp();  // the previous chunk's stage is no longer read
     if (valid) {
-      // window values straight into the node's slot (one tap at a time)
-      const float t0 = frac[q], t1 = frac[M + q];
-      const float b0 = (float)g.b[0], n0 = (float)g.norm[0], b1 = (float)g.b[1], n1 = (float)g.norm[1];
-#pragma unroll 2
-      for (int i = 0; i < k2Taps; ++i) {
-        const float w = kb_window<float>((float)(4 + g.off + i) - t0, (float)(4 - g.off - i) + t0, b0, n0);
-        st.w0p[slot][i] = pack2(w, w);
-        st.w1[slot][i] = kb_window<float>((float)(4 + g.off + i) - t1, (float)(4 - g.off - i) + t1, b1, n1);
+      // window values straight into the node's slot (one tap pair at a time)
+      const float z0 = frac[q] - 0.5f, z1 = frac[M + q] - 0.5f;
+      const f32x2 zz0 = pack2(z0, z0), zz1 = pack2(z1, z1);
+#pragma unroll
+      for (int p = 0; p < k2Pairs; ++p) {
+        *reinterpret_cast<float2*>(&st.w0[slot][2 * p]) = unpack2(poly2d_pair(st.pc, 0, p, zz0));
+        *reinterpret_cast<float2*>(&st.w1[slot][2 * p]) = unpack2(poly2d_pair(st.pc, 1, p, zz1));
       }
       const float2 v = fhat[perm[q]];
       st.v[slot] = pack2(v.x, v.y);
@@ -132,18 +169,19 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
 }
 
 __global__ void __launch_bounds__(k2Threads)
-    scatter2d_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na, const float2* __restrict__ fhat) {
+    scatter2d_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na, const float* __restrict__ poly,
+                            const float2* __restrict__ fhat) {
   __shared__ Stage2d stage[k2Warps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nitems = *na.n_items;
   const float* frac = reinterpret_cast<const float*>(na.frac);
   for (int it = blockIdx.x * k2Warps + warp; it < nitems; it += gridDim.x * k2Warps)
-    scatter2d_item(g, grid, na.cell, frac, na.perm, fhat, na.items[it], stage[warp], lane);
+    scatter2d_item(g, grid, na.cell, frac, na.perm, fhat, poly, na.items[it], stage[warp], lane);
 }
 
 __global__ void __launch_bounds__(k2Threads)
     scatter2d_regacc_batch_kernel(const BatchProblem* __restrict__ probs, float2* __restrict__ grid, BatchNodes nb,
-                                  const float2* __restrict__ fhat) {
+                                  const float* __restrict__ poly, const float2* __restrict__ fhat) {
   __shared__ Stage2d stage[k2Warps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nitems = *nb.n_items;
@@ -152,19 +190,21 @@ __global__ void __launch_bounds__(k2Threads)
     const int4 item = nb.items[it];
     const BatchProblem& P = probs[item.w];
     scatter2d_item(P.g, grid + P.grid_off, nb.cell + 2 * P.node_off, frac + 2 * P.node_off,
-                   nb.perm + P.node_off, fhat + P.out_off, item, stage[warp], lane);
+                   nb.perm + P.node_off, fhat + P.out_off, poly + P.poly_off, item, stage[warp], lane);
   }
 }
 
 struct GTile2d {
   float2 t[k2Lines][k2Cols];  // the region, row pitch 32 complex
+  Poly2d pc;
 };
 
 // One work item of one problem (gather), by one warp.
 __device__ __forceinline__ void gather2d_item(const Geometry& g, const float2* __restrict__ grid,
                                               const int* __restrict__ cell, const float* __restrict__ frac,
                                               const int* __restrict__ perm, float2* __restrict__ fhat,
-                                              const int4& item, GTile2d& tl, int lane) {
+                                              const float* __restrict__ poly, const int4& item, GTile2d& tl,
+                                              int lane) {
   const int64_t M = g.M;
   int tc[2];
   tile_coords<2>(g, item.x, tc);
@@ -176,16 +216,23 @@ __device__ __forceinline__ void gather2d_item(const Geometry& g, const float2* _
     for (int r = 0; r < k2Lines; ++r)  // independent loads in flight together
       if (r < g.L[0]) tl.t[r][lane] = grid[(int64_t)wrap_mod(start0 + r, g.Nt[0]) * g.Nt[1] + g1];
   }
+  load_poly2d(poly, tl.pc, lane);
   __syncwarp();
   for (int i = lane; i < item.z; i += 32) {
     const int q = item.y + i;
     const int a0 = cell[q] - tc[0] * g.T[0], a1 = cell[M + q] - tc[1] * g.T[1];
-    float w0[k2Taps], w1[k2Taps];
-    node_weights<k2Taps, float>(g, 0, 4, frac[q], w0);
-    node_weights<k2Taps, float>(g, 1, 4, frac[M + q], w1);
+    const float z0 = frac[q] - 0.5f, z1 = frac[M + q] - 0.5f;
+    const f32x2 zz0 = pack2(z0, z0), zz1 = pack2(z1, z1);
+    float w0[k2Taps];
     f32x2 w1p[k2Taps];
 #pragma unroll
-    for (int i1 = 0; i1 < k2Taps; ++i1) w1p[i1] = pack2(w1[i1], w1[i1]);
+    for (int p = 0; p < k2Pairs; ++p) {
+      const float2 a = unpack2(poly2d_pair(tl.pc, 0, p, zz0)), b = unpack2(poly2d_pair(tl.pc, 1, p, zz1));
+      w0[2 * p] = a.x;
+      w0[2 * p + 1] = a.y;
+      w1p[2 * p] = pack2(b.x, b.x);
+      w1p[2 * p + 1] = pack2(b.y, b.y);
+    }
     f32x2 acc = pack2(0.f, 0.f);
 #pragma unroll
     for (int i0 = 0; i0 < k2Taps; ++i0) {
@@ -200,18 +247,19 @@ __device__ __forceinline__ void gather2d_item(const Geometry& g, const float2* _
 }
 
 __global__ void __launch_bounds__(k2Threads)
-    gather2d_warp_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na, float2* __restrict__ fhat) {
+    gather2d_warp_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na, const float* __restrict__ poly,
+                         float2* __restrict__ fhat) {
   __shared__ GTile2d tiles[k2Warps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nitems = *na.n_items;
   const float* frac = reinterpret_cast<const float*>(na.frac);
   for (int it = blockIdx.x * k2Warps + warp; it < nitems; it += gridDim.x * k2Warps)
-    gather2d_item(g, grid, na.cell, frac, na.perm, fhat, na.items[it], tiles[warp], lane);
+    gather2d_item(g, grid, na.cell, frac, na.perm, fhat, poly, na.items[it], tiles[warp], lane);
 }
 
 __global__ void __launch_bounds__(k2Threads)
     gather2d_warp_batch_kernel(const BatchProblem* __restrict__ probs, const float2* __restrict__ grid,
-                               BatchNodes nb, float2* __restrict__ fhat) {
+                               BatchNodes nb, const float* __restrict__ poly, float2* __restrict__ fhat) {
   __shared__ GTile2d tiles[k2Warps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nitems = *nb.n_items;
@@ -220,7 +268,7 @@ __global__ void __launch_bounds__(k2Threads)
     const int4 item = nb.items[it];
     const BatchProblem& P = probs[item.w];
     gather2d_item(P.g, grid + P.grid_off, nb.cell + 2 * P.node_off, frac + 2 * P.node_off, nb.perm + P.node_off,
-                  fhat + P.out_off, item, tiles[warp], lane);
+                  fhat + P.out_off, poly + P.poly_off, item, tiles[warp], lane);
   }
 }
 
@@ -239,15 +287,15 @@ int scatter2d_ctas_per_sm() {
   return n;
 }
 
-cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat, int ctas,
-                                  cudaStream_t s) {
-  scatter2d_regacc_kernel<<<ctas, k2Threads, 0, s>>>(g, (float2*)grid, na, (const float2*)fhat);
+cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArrays& na, const float* poly,
+                                  const void* fhat, int ctas, cudaStream_t s) {
+  scatter2d_regacc_kernel<<<ctas, k2Threads, 0, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb, const void* fhat,
-                                        int ctas, cudaStream_t s) {
-  scatter2d_regacc_batch_kernel<<<ctas, k2Threads, 0, s>>>(probs, (float2*)grid, nb, (const float2*)fhat);
+cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb,
+                                        const float* poly, const void* fhat, int ctas, cudaStream_t s) {
+  scatter2d_regacc_batch_kernel<<<ctas, k2Threads, 0, s>>>(probs, (float2*)grid, nb, poly, (const float2*)fhat);
   return cudaGetLastError();
 }
 
@@ -257,15 +305,15 @@ int gather2d_ctas_per_sm() {
   return n;
 }
 
-cudaError_t launch_gather2d_fast(const Geometry& g, const void* grid, const NodeArrays& na, void* fhat, int ctas,
-                                 cudaStream_t s) {
-  gather2d_warp_kernel<<<ctas, k2Threads, 0, s>>>(g, (const float2*)grid, na, (float2*)fhat);
+cudaError_t launch_gather2d_fast(const Geometry& g, const void* grid, const NodeArrays& na, const float* poly,
+                                 void* fhat, int ctas, cudaStream_t s) {
+  gather2d_warp_kernel<<<ctas, k2Threads, 0, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather2d_fast_batch(const BatchProblem* probs, const void* grid, const BatchNodes& nb, void* fhat,
-                                       int ctas, cudaStream_t s) {
-  gather2d_warp_batch_kernel<<<ctas, k2Threads, 0, s>>>(probs, (const float2*)grid, nb, (float2*)fhat);
+cudaError_t launch_gather2d_fast_batch(const BatchProblem* probs, const void* grid, const BatchNodes& nb,
+                                       const float* poly, void* fhat, int ctas, cudaStream_t s) {
+  gather2d_warp_batch_kernel<<<ctas, k2Threads, 0, s>>>(probs, (const float2*)grid, nb, poly, (float2*)fhat);
   return cudaGetLastError();
 }
 

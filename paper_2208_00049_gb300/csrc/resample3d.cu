@@ -16,11 +16,13 @@
 //  * gather: a half-warp per node (a warp instruction serves two nodes);
 //    lane (g, i2) of a half owns taps (i1 = j + 4g, i2), j = 0..3, and loops
 //    over i0, then the half reduces its 16 partial sums;
-//  * scatter: W warps (default 2, measured best of 1/2/4/8) share one
-//    accumulator tile, warp w updating only the planes i0 with
-//    (a0 + i0) = w (mod W), so no two warps touch the same element and the
-//    read-modify-writes need no atomics; the tile (block plus halo) is then
-//    added to the grid with vector global reductions;
+//  * scatter (default): the region is accumulated in registers, see the
+//    register-accumulating scatter below;
+//  * scatter (shared-memory form): W warps (default 2, measured best of
+//    1/2/4/8) share one accumulator tile, warp w updating only the planes i0
+//    with (a0 + i0) = w (mod W), so no two warps touch the same element and
+//    the read-modify-writes need no atomics; the tile (block plus halo) is
+//    then added to the grid with vector global reductions;
 //  * the node records of a work item are staged in shared memory with the tile.
 #include <stdlib.h>
 #include <string.h>
@@ -580,8 +582,11 @@ bool g12_supported(const Geometry& g, int cmax) {
 //  3. evaluate the 3K window values of every node once (POLYNOMIAL form; a
 //     lane takes two taps of all three dimensions with packed Horner steps)
 //     and store, at the node's sorted slot and shifted to region
-//     coordinates: w0 as packed pairs, v w1 per row, w2 as packed pairs per
-//     thread column pair (zero outside the footprint);
+//     coordinates: w0, v w1 per row, and w2 per thread column pair (zero
+//     outside the footprint).  Stored once and paired in registers (a move
+//     per value), w0 and w2 cost half the shared wavefronts of stored
+//     (w, w) pairs: the main loop issues 2 + K/4 shared loads per thread
+//     and node;
 //  4. every warp runs over its node runs;
 //  5. the region is added to the grid with vector global reductions.
 constexpr int kRegAccLines = 16;                   // acc[h][r0], L0 <= 16
@@ -594,9 +599,9 @@ template <int K>
 struct RegAccStage {
   static constexpr int kPairs = K / 2;   // tap pairs per dimension
   float4 rec[kItemCap][2];               // {t0, t1, t2, pk}, {re v, im v, key, rank}
-  f32x2 w0p[kItemCap][K];                // (w0, w0), by slot
+  float w0s[kItemCap][K];                // w0, by slot
   f32x2 vw1[kItemCap][kRegAccLines];     // v w1[r - a1], by slot
-  float4 w2p[kItemCap][8];               // cc -> (w2[cc - a2] x2, w2[cc + 8 - a2] x2), by slot
+  float2 w2s[kItemCap][8];               // cc -> (w2[cc - a2], w2[cc + 8 - a2]), by slot
   int count[kRegAccKeys];
   int start[kRegAccKeys + 1];
   f32x2 coef[3][kPairs][K + 1];          // (tap 2 tp, tap 2 tp + 1) coefficient pairs, degree K
@@ -606,18 +611,20 @@ template <int A0, int K>
 __device__ __forceinline__ void regacc_node(const RegAccStage<K>& st, int s, int r1, int cc,
                                             f32x2 (&acc)[2][kRegAccLines]) {
   const f32x2 vw = st.vw1[s][r1];
-  const float4 w2 = st.w2p[s][cc];
-  const f32x2 vp0 = mul2(vw, pack2(w2.x, w2.y));
-  const f32x2 vp1 = mul2(vw, pack2(w2.z, w2.w));
-  const float4* wq = reinterpret_cast<const float4*>(&st.w0p[s][0]);
+  const float2 w2 = st.w2s[s][cc];
+  const f32x2 vp0 = mul2(vw, pack2(w2.x, w2.x));
+  const f32x2 vp1 = mul2(vw, pack2(w2.y, w2.y));
+  const float4* wq = reinterpret_cast<const float4*>(&st.w0s[s][0]);
 #pragma unroll
-  for (int q = 0; q < K / 2; ++q) {
+  for (int q = 0; q < K / 4; ++q) {
     const float4 x = wq[q];
-    const f32x2 wa = pack2(x.x, x.y), wb = pack2(x.z, x.w);
-    acc[0][A0 + 2 * q] = fma2(vp0, wa, acc[0][A0 + 2 * q]);
-    acc[0][A0 + 2 * q + 1] = fma2(vp0, wb, acc[0][A0 + 2 * q + 1]);
-    acc[1][A0 + 2 * q] = fma2(vp1, wa, acc[1][A0 + 2 * q]);
-    acc[1][A0 + 2 * q + 1] = fma2(vp1, wb, acc[1][A0 + 2 * q + 1]);
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const f32x2 wa = pack2(xs[j], xs[j]);
+      acc[0][A0 + 4 * q + j] = fma2(vp0, wa, acc[0][A0 + 4 * q + j]);
+      acc[1][A0 + 4 * q + j] = fma2(vp1, wa, acc[1][A0 + 4 * q + j]);
+    }
   }
 }
 
@@ -687,12 +694,12 @@ __global__ void __launch_bounds__(kRegAccThreads, 4)
       st.rec[i][1] = make_float4(v.x, v.y, __int_as_float(key), __int_as_float(rank));
     }
     {
-      // clear the shifted rows of the slots in use (vw1 and w2p: 8 float4 each per slot)
+      // clear the shifted rows of the slots in use (vw1: 8 float4, w2s: 4 float4 per slot)
       float4* z1 = reinterpret_cast<float4*>(&st.vw1[0][0]);
-      float4* z2 = &st.w2p[0][0];
+      float4* z2 = reinterpret_cast<float4*>(&st.w2s[0][0]);
       for (int e = tid; e < count * 8; e += kRegAccThreads) {
         z1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-        z2[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < count * 4) z2[e] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     __syncthreads();
@@ -741,15 +748,15 @@ __global__ void __launch_bounds__(kRegAccThreads, 4)
           for (int e = K - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[d][e]);
           w[d] = unpack2(pw);  // taps 2 tp, 2 tp + 1
         }
-        *reinterpret_cast<float4*>(&st.w0p[q][2 * tp]) = make_float4(w[0].x, w[0].x, w[0].y, w[0].y);
+        *reinterpret_cast<float2*>(&st.w0s[q][2 * tp]) = w[0];
         const int r = ((pk >> 8) & 0xff) + 2 * tp;
         st.vw1[q][r] = pack2(rv.x * w[1].x, rv.y * w[1].x);
         st.vw1[q][r + 1] = pack2(rv.x * w[1].y, rv.y * w[1].y);
         // column c sits in pair cc = c & 7, half c >> 3 (two copies)
         const int c0 = (pk >> 16) + 2 * tp, c1 = c0 + 1;
-        float* w2f = reinterpret_cast<float*>(&st.w2p[q][0]);
-        *reinterpret_cast<float2*>(&w2f[4 * (c0 & 7) + 2 * (c0 >> 3)]) = make_float2(w[2].x, w[2].x);
-        *reinterpret_cast<float2*>(&w2f[4 * (c1 & 7) + 2 * (c1 >> 3)]) = make_float2(w[2].y, w[2].y);
+        float* w2f = reinterpret_cast<float*>(&st.w2s[q][0]);
+        w2f[2 * (c0 & 7) + (c0 >> 3)] = w[2].x;
+        w2f[2 * (c1 & 7) + (c1 >> 3)] = w[2].y;
       }
     }
     __syncthreads();

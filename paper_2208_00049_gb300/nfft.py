@@ -174,12 +174,12 @@ class Plan:
         return out
 
     def step_pad_fft(self, f):
-        """Algorithm 1 lines 1-6 (the pruned FFT where the plan qualifies)."""
+        """Algorithm 1's correction, zero-pad and FFT steps (the pruned FFT where the plan qualifies)."""
         self._check_tensor(f, self.N, self.dtype, "f")
         B.check(B.nfft_step_pad_fft(self.handle, _ptr(f)), "nfft_step_pad_fft")
 
     def step_fft_crop(self, out):
-        """Algorithm 2 lines 4-10 (the pruned FFT where the plan qualifies)."""
+        """Algorithm 2's inverse FFT, crop and correction steps (the pruned FFT where the plan qualifies)."""
         self._check_tensor(out, self.N, self.dtype, "out")
         B.check(B.nfft_step_fft_crop(self.handle, _ptr(out)), "nfft_step_fft_crop")
         return out

@@ -266,14 +266,20 @@ def test_tile_shapes_agree(tile):
 
 
 def test_compensated_scatter():
+    """The compensated shared-memory scatter against the plain one of the same
+    kernel family (a 16 x 16 tile is outside the register-accumulating 2D
+    kernels, which evaluate the window in POLYNOMIAL form; the shared-memory
+    kernels evaluate it directly), and the default plan beside them."""
     from paper_2208_00049_gb300 import binding as B
     N = (48, 40)
     case = inputs.small_case(N, 20000, seed=11, m=4)
     want = onfft.adjoint(case["k"], case["w"], N, 2.0, 4)
-    _, y0 = _run(case, "c64")
-    _, y1 = _run(case, "c64", flags=B.NFFT_FLAG_COMPENSATED)
+    _, y0 = _run(case, "c64", tile=(16, 16))
+    _, y1 = _run(case, "c64", flags=B.NFFT_FLAG_COMPENSATED, tile=(16, 16))
+    _, y2 = _run(case, "c64")
     e0 = assert_close(y0, want, 1e-5, "plain")
     e1 = assert_close(y1, want, 1e-5, "compensated")
+    assert_close(y2, want, 1e-5, "default plan")
     assert e1 <= 1.5 * e0 + 1e-7
 
 

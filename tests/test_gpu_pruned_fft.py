@@ -1,6 +1,7 @@
 """GPU parity of the pruned 3D FFT (N~_d = 2 N_d = 256, complex64) against the
-FP64 oracle: the fused steps Algorithm 1 lines 1-6 and Algorithm 2 lines
-4-10 element by element on the full 256^3 grid / 128^3 output, the whole
+FP64 oracle: the fused steps (Algorithm 1: correction + zero pad + FFT;
+Algorithm 2: inverse FFT + crop + correction) element by element on the full
+256^3 grid / 128^3 output, the whole
 transforms and the node gradient through them, and the selection rule."""
 import numpy as np
 import pytest
@@ -49,7 +50,7 @@ def test_pruned_path_selection():
 
 
 def test_pad_fft_matches_oracle():
-    """Algorithm 1 lines 1-6 on the full grid: correction, zero pad, FFT."""
+    """Algorithm 1's correction, zero-pad and FFT steps on the full grid."""
     rng = np.random.default_rng(2208)
     f = inputs.complex_normal(rng, N3)
     p = onfft.Params(N3, 2.0, 4)
@@ -63,7 +64,7 @@ def test_pad_fft_matches_oracle():
 
 
 def test_fft_crop_matches_oracle():
-    """Algorithm 2 lines 4-10: inverse FFT of an arbitrary grid, crop, correction."""
+    """Algorithm 2's inverse FFT, crop and correction steps on an arbitrary grid."""
     rng = np.random.default_rng(49)
     p = onfft.Params(N3, 2.0, 4)
     G = inputs.complex_normal(rng, p.Nt)
