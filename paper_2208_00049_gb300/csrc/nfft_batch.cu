@@ -7,9 +7,14 @@
 // list ({tile, first node, count, problem}) walked by one persistent gather /
 // scatter launch.  Forward = deconv_pad (one launch, blockIdx.y = problem) ->
 // one cuFFT per size class -> gather (one launch); adjoint = memset ->
-// scatter (one launch) -> cuFFT per class -> crop_deconv (one launch).  With
-// graph mode on, each sequence is captured once into a CUDA graph and
-// replayed while the caller's buffers stay the same.
+// scatter (one launch) -> cuFFT per class -> crop_deconv (one launch).  The
+// size classes' FFTs are independent and most are small (a 128 x 128 class
+// cannot fill the GPU), so they run concurrently: forked from the batch's
+// stream onto a few side streams (classes assigned largest first to the
+// least loaded stream) and joined back with events.  With graph mode on,
+// each sequence is captured once into a CUDA graph (the fork and join become
+// parallel branches of the graph) and replayed while the caller's buffers
+// stay the same.
 //
 // Tile shapes (the block size of Sec. 3.7.3, whose best value the paper finds
 // by a sweep, Sec. 5.2, and proposes to choose automatically like
@@ -18,6 +23,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -55,8 +61,12 @@ struct nfft_batch {
     int count = 0;
     cufftHandle plan = 0;
     bool ok = false;
+    int side = 0;  // side stream of this class's FFT
   };
   std::vector<SizeClass> classes;
+  std::vector<cudaStream_t> fft_streams;  // empty: the FFTs run on the calling stream
+  std::vector<cudaEvent_t> join_ev;       // one per side stream
+  cudaEvent_t fork_ev = nullptr;
 
   void* grid = nullptr;
   double* beta64 = nullptr;
@@ -90,6 +100,8 @@ struct nfft_batch {
 };
 
 namespace {
+
+constexpr int kFftSideStreams = 4;  // concurrent size-class FFTs
 
 size_t rsize(int dtype) { return dtype == NFFT_C128 ? 8 : 4; }
 size_t csize(int dtype) { return 2 * rsize(dtype); }
@@ -295,8 +307,13 @@ BatchNodes batch_nodes(const nfft_batch* b) {
 }
 
 int run_fft_classes(nfft_batch* b, int sign, cudaStream_t st) {
+  const int ns = (int)b->fft_streams.size();
+  if (ns > 0) {  // fork
+    B_CK(b, cudaEventRecord(b->fork_ev, st));
+    for (cudaStream_t side : b->fft_streams) B_CK(b, cudaStreamWaitEvent(side, b->fork_ev, 0));
+  }
   for (auto& c : b->classes) {
-    if (cufftSetStream(c.plan, st) != CUFFT_SUCCESS) return NFFT_ERR_CUFFT;
+    if (cufftSetStream(c.plan, ns > 0 ? b->fft_streams[c.side] : st) != CUFFT_SUCCESS) return NFFT_ERR_CUFFT;
     const int dir = sign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
     cufftResult r;
     if (b->dtype == NFFT_C128) {
@@ -307,6 +324,10 @@ int run_fft_classes(nfft_batch* b, int sign, cudaStream_t st) {
       r = cufftExecC2C(c.plan, g, g, dir);
     }
     if (r != CUFFT_SUCCESS) return NFFT_ERR_CUFFT;
+  }
+  for (int k = 0; k < ns; ++k) {  // join
+    B_CK(b, cudaEventRecord(b->join_ev[k], b->fft_streams[k]));
+    B_CK(b, cudaStreamWaitEvent(st, b->join_ev[k], 0));
   }
   return NFFT_OK;
 }
@@ -440,6 +461,9 @@ int nfft_batch_destroy(nfft_batch* b) {
   for (int k = 0; k < 2; ++k)
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  for (cudaStream_t side : b->fft_streams) cudaStreamDestroy(side);
+  for (cudaEvent_t ev : b->join_ev) cudaEventDestroy(ev);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   for (auto& c : b->classes)
     if (c.ok) cufftDestroy(c.plan);
   void* bufs[] = {b->grid, b->beta64, b->beta32, b->poly, b->probs, b->cell, b->frac, b->perm, b->key, b->rank,
@@ -599,6 +623,37 @@ int nfft_batch_create(nfft_batch** out, int D, int B, const int64_t* N, const in
                                   dtype == NFFT_C128 ? CUFFT_Z2Z : CUFFT_C2C, c.count);
     if (r != CUFFT_SUCCESS) st = r == CUFFT_ALLOC_FAILED ? NFFT_ERR_OOM : NFFT_ERR_CUFFT;
     else c.ok = true;
+  }
+  // side streams for the class FFTs: each class, largest first, goes to the
+  // stream with the fewest grid points so far
+  const int n_side = std::min<int>(kFftSideStreams, (int)b->classes.size());
+  if (st == NFFT_OK && n_side > 1) {
+    std::vector<int> order(b->classes.size());
+    std::vector<int64_t> load(n_side, 0);
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    auto points = [&](int i) {
+      int64_t sz = b->classes[i].count;
+      for (int64_t v : b->classes[i].nt) sz *= v;
+      return sz;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return points(x) > points(y); });
+    for (int i : order) {
+      int k = 0;
+      for (int j = 1; j < n_side; ++j)
+        if (load[j] < load[k]) k = j;
+      b->classes[i].side = k;
+      load[k] += points(i);
+    }
+    for (int k = 0; k < n_side && st == NFFT_OK; ++k) {
+      cudaStream_t side = nullptr;
+      cudaEvent_t ev = nullptr;
+      if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess) st = NFFT_ERR_CUDA;
+      else b->fft_streams.push_back(side);
+      if (st == NFFT_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) st = NFFT_ERR_CUDA;
+      else if (st == NFFT_OK) b->join_ev.push_back(ev);
+    }
+    if (st == NFFT_OK && cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+      st = NFFT_ERR_CUDA;
   }
   // deconvolution vectors, one set per problem
   for (int p = 0; p < B && st == NFFT_OK; ++p) {
