@@ -112,15 +112,17 @@ def _strip_comments(src):
     return " ".join("".join(out).split())
 
 
-def kernel_source_hash():
-    """Hash of the kernel sources (comments and layout excluded), recorded in
-    the committed ncu summaries beside the counters taken from that code."""
+def kernel_source_hash(files=None):
+    """Hash of kernel sources (comments and layout excluded), recorded in the
+    committed ncu summaries beside the counters taken from that code: the
+    named files of the source directory (those that define the profiled
+    kernels and their launch configuration), or all of them."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2208_00049_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), encoding="utf-8") as fh:
-                h.update(_strip_comments(fh.read()).encode())
+    names = sorted(files) if files else sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    for f in names:
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -133,7 +135,14 @@ def profiled_traffic(kernel, workload):
     text = open(path).read()
     mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
     mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not mh or not mt or mh.group(1) != kernel_source_hash():
+    mf = re.search(r"source_files:\s*([^\n]+)", text)
+    files = mf.group(1).split() if mf else None
+    if not mh or not mt:
+        return None
+    try:
+        if mh.group(1) != kernel_source_hash(files):
+            return None
+    except OSError:
         return None
     return float(mt.group(1))
 

@@ -20,3 +20,11 @@ def test_source_hash_is_stable():
     import bench
     h = bench.kernel_source_hash()
     assert len(h) == 16 and h == bench.kernel_source_hash()
+
+
+def test_source_hash_over_named_files():
+    import bench
+    one = bench.kernel_source_hash(["resample3d.cu"])
+    assert one == bench.kernel_source_hash(["resample3d.cu"])
+    assert one != bench.kernel_source_hash(["resample3d.cu", "nfft_plan.cu"])
+    assert one != bench.kernel_source_hash()
