@@ -68,6 +68,26 @@ __device__ __forceinline__ f32x2 poly2d_pair(const Poly2d& pc, int d, int p, f32
   return w;
 }
 
+// Node data of one chunk of 32 nodes of a work item (lane i: node base + i),
+// loaded one chunk ahead of its use so that the load latency overlaps the
+// current chunk's work (the kernels are latency-bound: one warp per item).
+struct Chunk2d {
+  int c0 = 0, c1 = 0, j = 0;  // cells, caller index
+  float t0 = 0.f, t1 = 0.f;   // fractions
+  __device__ __forceinline__ void load(const int* __restrict__ cell, const float* __restrict__ frac,
+                                       const int* __restrict__ perm, int64_t M, const int4& item, int base,
+                                       int lane) {
+    if (base + lane < item.z) {
+      const int q = item.y + base + lane;
+      c0 = cell[q];
+      c1 = cell[M + q];
+      t0 = frac[q];
+      t1 = frac[M + q];
+      j = perm[q];
+    }
+  }
+};
+
 struct Stage2d {
   float w0[32][k2Taps];   // by slot (paired in registers: half the shared wavefronts of stored pairs)
   float w1[32][k2Taps];
@@ -112,13 +132,17 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
   f32x2 acc[k2Lines];
 #pragma unroll
   for (int r = 0; r < k2Lines; ++r) acc[r] = pack2(0.f, 0.f);
+  Chunk2d next;
+  next.load(cell, frac, perm, M, item, 0, lane);
   __syncwarp();  // the previous item's coefficients are no longer read
   load_poly2d(poly, st.pc, lane);
 
   for (int base = 0; base < item.z; base += 32) {
     const bool valid = base + lane < item.z;
-    const int q = item.y + base + lane;
-    const int a0 = valid ? cell[q] - tc[0] * g.T[0] : -1;
+    const Chunk2d cur = next;
+    const float2 v = valid ? fhat[cur.j] : make_float2(0.f, 0.f);
+    const int a0 = valid ? cur.c0 - tc[0] * g.T[0] : -1;
+    if (base + 32 < item.z) next.load(cell, frac, perm, M, item, base + 32, lane);
     // counting sort of the chunk by a0 (ballots): bin starts bs[], own slot
     int bs[k2Bins + 1];
     int slot = 0, run = 0;
@@ -133,16 +157,15 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
     __syncwarp();  // the previous chunk's stage is no longer read
     if (valid) {
       // window values straight into the node's slot (one tap pair at a time)
-      const float z0 = frac[q] - 0.5f, z1 = frac[M + q] - 0.5f;
+      const float z0 = cur.t0 - 0.5f, z1 = cur.t1 - 0.5f;
       const f32x2 zz0 = pack2(z0, z0), zz1 = pack2(z1, z1);
 #pragma unroll
       for (int p = 0; p < k2Pairs; ++p) {
         *reinterpret_cast<float2*>(&st.w0[slot][2 * p]) = unpack2(poly2d_pair(st.pc, 0, p, zz0));
         *reinterpret_cast<float2*>(&st.w1[slot][2 * p]) = unpack2(poly2d_pair(st.pc, 1, p, zz1));
       }
-      const float2 v = fhat[perm[q]];
       st.v[slot] = pack2(v.x, v.y);
-      st.a1[slot] = cell[M + q] - tc[1] * g.T[1];
+      st.a1[slot] = cur.c1 - tc[1] * g.T[1];
     }
     __syncwarp();
     scatter2d_bin<0>(st, bs[0], bs[1], lane, acc);
@@ -168,7 +191,9 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
   }
 }
 
-__global__ void __launch_bounds__(k2Threads)
+// 5 CTAs per SM (96 registers): measured faster than the 4 the compiler
+// would otherwise allow with the chunk prefetch's registers.
+__global__ void __launch_bounds__(k2Threads, 5)
     scatter2d_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na, const float* __restrict__ poly,
                             const float2* __restrict__ fhat) {
   __shared__ Stage2d stage[k2Warps];
@@ -179,7 +204,7 @@ __global__ void __launch_bounds__(k2Threads)
     scatter2d_item(g, grid, na.cell, frac, na.perm, fhat, poly, na.items[it], stage[warp], lane);
 }
 
-__global__ void __launch_bounds__(k2Threads)
+__global__ void __launch_bounds__(k2Threads, 5)
     scatter2d_regacc_batch_kernel(const BatchProblem* __restrict__ probs, float2* __restrict__ grid, BatchNodes nb,
                                   const float* __restrict__ poly, const float2* __restrict__ fhat) {
   __shared__ Stage2d stage[k2Warps];
@@ -209,6 +234,8 @@ __device__ __forceinline__ void gather2d_item(const Geometry& g, const float2* _
   int tc[2];
   tile_coords<2>(g, item.x, tc);
   const int start0 = tc[0] * g.T[0] + g.off, start1 = tc[1] * g.T[1] + g.off;
+  Chunk2d next;  // the first chunk's node data in flight with the region loads
+  next.load(cell, frac, perm, M, item, 0, lane);
   __syncwarp();  // the previous item's tile is no longer read
   if (lane < g.L[1]) {
     const int g1 = wrap_mod(start1 + lane, g.Nt[1]);
@@ -218,10 +245,12 @@ __device__ __forceinline__ void gather2d_item(const Geometry& g, const float2* _
   }
   load_poly2d(poly, tl.pc, lane);
   __syncwarp();
-  for (int i = lane; i < item.z; i += 32) {
-    const int q = item.y + i;
-    const int a0 = cell[q] - tc[0] * g.T[0], a1 = cell[M + q] - tc[1] * g.T[1];
-    const float z0 = frac[q] - 0.5f, z1 = frac[M + q] - 0.5f;
+  for (int base = 0; base < item.z; base += 32) {
+    const bool valid = base + lane < item.z;
+    const int a0 = valid ? next.c0 - tc[0] * g.T[0] : 0, a1 = valid ? next.c1 - tc[1] * g.T[1] : 0;
+    const float z0 = next.t0 - 0.5f, z1 = next.t1 - 0.5f;
+    const int jout = next.j;
+    if (base + 32 < item.z) next.load(cell, frac, perm, M, item, base + 32, lane);
     const f32x2 zz0 = pack2(z0, z0), zz1 = pack2(z1, z1);
     float w0[k2Taps];
     f32x2 w1p[k2Taps];
@@ -242,11 +271,13 @@ __device__ __forceinline__ void gather2d_item(const Geometry& g, const float2* _
       for (int i1 = 1; i1 < k2Taps; ++i1) sum = fma2(row[i1], w1p[i1], sum);
       acc = fma2(sum, pack2(w0[i0], w0[i0]), acc);
     }
-    fhat[perm[q]] = unpack2(acc);
+    if (valid) fhat[jout] = unpack2(acc);
   }
 }
 
-__global__ void __launch_bounds__(k2Threads)
+// 9 CTAs per SM (at most 56 registers): the occupancy the gather was
+// measured at; the kernel is latency-bound.
+__global__ void __launch_bounds__(k2Threads, 9)
     gather2d_warp_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na, const float* __restrict__ poly,
                          float2* __restrict__ fhat) {
   __shared__ GTile2d tiles[k2Warps];
@@ -257,7 +288,7 @@ __global__ void __launch_bounds__(k2Threads)
     gather2d_item(g, grid, na.cell, frac, na.perm, fhat, poly, na.items[it], tiles[warp], lane);
 }
 
-__global__ void __launch_bounds__(k2Threads)
+__global__ void __launch_bounds__(k2Threads, 9)
     gather2d_warp_batch_kernel(const BatchProblem* __restrict__ probs, const float2* __restrict__ grid,
                                BatchNodes nb, const float* __restrict__ poly, float2* __restrict__ fhat) {
   __shared__ GTile2d tiles[k2Warps];
