@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", default=None,
+                    help="batched workload: fixed tile shape (e.g. 9,25) instead of the autotuner's choice; "
+                         "for profiling, where timings taken under the profiler would steer the autotuner")
     ap.add_argument("--cpu-sample", type=int, default=131072,
                     help="nodes in the oracle's bounded sample")
     ap.add_argument("--no-fp64-form", action="store_true",
@@ -423,7 +426,12 @@ def run_batched(args):
     Ms = [p["M"] for p in probs]
     b = Batch(Ns, list(range(64)), Ms, sigma=2.0, m=4, dtype=torch.complex64)
     k_all = torch.from_numpy(np.concatenate([p["k"] for p in probs])).cuda()
-    tile = b.autotune(k_all)
+    if args.tile:
+        tile = tuple(int(x) for x in args.tile.split(","))
+        b.set_tile(tile)
+        b.set_nodes(k_all)
+    else:
+        tile = b.autotune(k_all)
     b.set_graph(True)
     f_all = torch.cat([torch.from_numpy(p["f"].ravel()) for p in probs]).to(torch.complex64).cuda()
     w_all = torch.cat([torch.from_numpy(p["w"]) for p in probs]).to(torch.complex64).cuda()
@@ -445,7 +453,8 @@ def run_batched(args):
             "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded PCG64)",
             "config": {"workload": "batched 64 x 2D N in {64..512}^2, M = N1 N2 U(0.5,2), total M = %d" % M,
-                       "tile": list(tile), "work_items": info["n_items"], "fft_classes": info["fft_classes"],
+                       "tile": list(tile), "tile_from": "--tile" if args.tile else "autotuner",
+                       "work_items": info["n_items"], "fft_classes": info["fft_classes"],
                        "graph": True, "l2": "flushed between steps (256 MiB write)"},
             "clocks": clk.summary()}
     print(json.dumps(line))

@@ -72,6 +72,9 @@ struct nfft_batch {
   double* beta64 = nullptr;
   float* beta32 = nullptr;
   float* poly = nullptr;  // [B][D][K][2m + 1], built for the standard (2m-tap) window only
+  int* pad_blocks = nullptr;   // [B + 1] block ranges of the batched deconv_pad launch
+  int* crop_blocks = nullptr;  // [B + 1] block ranges of the batched crop_deconv launch
+  int n_pad_blocks = 0, n_crop_blocks = 0;
   BatchProblem* probs = nullptr;
   std::vector<BatchProblem> probs_host;
   int* cell = nullptr;
@@ -339,8 +342,10 @@ const void* beta_ptr(const nfft_batch* b) {
 int enqueue_forward(nfft_batch* b, const void* f, void* fhat, cudaStream_t st) {
   const Geometry gm = max_geometry(b);
   cudaError_t e = b->dtype == NFFT_C128
-                      ? launch_deconv_pad_batch<double>(b->D, b->B, b->max_grid, b->probs, beta_ptr(b), f, b->grid, st)
-                      : launch_deconv_pad_batch<float>(b->D, b->B, b->max_grid, b->probs, beta_ptr(b), f, b->grid, st);
+                      ? launch_deconv_pad_batch<double>(b->D, b->B, b->pad_blocks, b->n_pad_blocks, b->probs,
+                                                        beta_ptr(b), f, b->grid, st)
+                      : launch_deconv_pad_batch<float>(b->D, b->B, b->pad_blocks, b->n_pad_blocks, b->probs,
+                                                       beta_ptr(b), f, b->grid, st);
   B_CK(b, e);
   int s = run_fft_classes(b, -1, st);
   if (s != NFFT_OK) return s;
@@ -365,8 +370,10 @@ int enqueue_adjoint(nfft_batch* b, const void* fhat, void* y, cudaStream_t st) {
   int s = run_fft_classes(b, +1, st);
   if (s != NFFT_OK) return s;
   e = b->dtype == NFFT_C128
-          ? launch_crop_deconv_batch<double>(b->D, b->B, b->max_n, b->probs, beta_ptr(b), b->grid, y, st)
-          : launch_crop_deconv_batch<float>(b->D, b->B, b->max_n, b->probs, beta_ptr(b), b->grid, y, st);
+          ? launch_crop_deconv_batch<double>(b->D, b->B, b->crop_blocks, b->n_crop_blocks, b->probs, beta_ptr(b),
+                                             b->grid, y, st)
+          : launch_crop_deconv_batch<float>(b->D, b->B, b->crop_blocks, b->n_crop_blocks, b->probs, beta_ptr(b),
+                                            b->grid, y, st);
   B_CK(b, e);
   return NFFT_OK;
 }
@@ -466,7 +473,7 @@ int nfft_batch_destroy(nfft_batch* b) {
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   for (auto& c : b->classes)
     if (c.ok) cufftDestroy(c.plan);
-  void* bufs[] = {b->grid, b->beta64, b->beta32, b->poly, b->probs, b->cell, b->frac, b->perm, b->key, b->rank,
+  void* bufs[] = {b->grid, b->beta64, b->beta32, b->poly, b->pad_blocks, b->crop_blocks, b->probs, b->cell, b->frac, b->perm, b->key, b->rank,
                   b->tile_count, b->tile_offset, b->set_items, b->set_nitems, b->items, b->n_items,
                   b->item_off};
   for (void* p : bufs)
@@ -654,6 +661,36 @@ int nfft_batch_create(nfft_batch** out, int D, int B, const int64_t* N, const in
     }
     if (st == NFFT_OK && cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess)
       st = NFFT_ERR_CUDA;
+  }
+  // block ranges of the batched correction kernels: about four grid-stride
+  // iterations per thread for every problem (complex pairs for deconv_pad)
+  if (st == NFFT_OK) {
+    constexpr int64_t per_block = 4 * kBatchDeconvThreads;
+    std::vector<int> pad(B + 1, 0), crop(B + 1, 0);
+    for (int p = 0; p < B; ++p) {
+      int64_t pairs = 1, n = 1;
+      for (int d = 0; d < D; ++d) {
+        pairs *= b->Nt[(size_t)p * D + d];
+        n *= N[(size_t)p * D + d];
+      }
+      pairs /= 2;
+      const int64_t np = (pairs + per_block - 1) / per_block, nc = (n + per_block - 1) / per_block;
+      if ((int64_t)pad[p] + np > INT32_MAX || (int64_t)crop[p] + nc > INT32_MAX) {
+        st = NFFT_ERR_INVALID_ARG;
+        break;
+      }
+      pad[p + 1] = pad[p] + (int)np;
+      crop[p + 1] = crop[p] + (int)nc;
+    }
+    if (st == NFFT_OK) st = balloc(b, &b->pad_blocks, sizeof(int) * (B + 1));
+    if (st == NFFT_OK) st = balloc(b, &b->crop_blocks, sizeof(int) * (B + 1));
+    if (st == NFFT_OK) {
+      b->n_pad_blocks = pad[B];
+      b->n_crop_blocks = crop[B];
+      st = bst(b, cudaMemcpy(b->pad_blocks, pad.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice));
+      if (st == NFFT_OK)
+        st = bst(b, cudaMemcpy(b->crop_blocks, crop.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice));
+    }
   }
   // deconvolution vectors, one set per problem
   for (int p = 0; p < B && st == NFFT_OK; ++p) {

@@ -207,11 +207,15 @@ struct PolyArgs {
 };
 cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s);
 
+// Batched correction kernels: one 1D grid of `blocks` blocks of
+// kBatchDeconvThreads threads, problem p owning blocks
+// [block_start[p], block_start[p + 1]) (device array of B + 1 entries).
+constexpr int kBatchDeconvThreads = 256;
 template <typename R>
-cudaError_t launch_deconv_pad_batch(int D, int B, int64_t max_grid, const BatchProblem* probs,
+cudaError_t launch_deconv_pad_batch(int D, int B, const int* block_start, int blocks, const BatchProblem* probs,
                                     const void* beta_all, const void* f, void* grid, cudaStream_t s);
 template <typename R>
-cudaError_t launch_crop_deconv_batch(int D, int B, int64_t max_n, const BatchProblem* probs,
+cudaError_t launch_crop_deconv_batch(int D, int B, const int* block_start, int blocks, const BatchProblem* probs,
                                      const void* beta_all, const void* grid, void* y, cudaStream_t s);
 cudaError_t launch_items_expand(const int4* src, const int* n_src, int max_n, int4* dst, const int* dst_off, int p,
                                 cudaStream_t s);

@@ -155,7 +155,8 @@ cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 template <int D, typename R>
 __device__ __forceinline__ void deconv_pad_body(const DeconvArgs& a, const typename Cplx<R>::type* __restrict__ f,
-                                                typename Cplx<R>::type* __restrict__ grid) {
+                                                typename Cplx<R>::type* __restrict__ grid, int64_t first,
+                                                int64_t stride) {
   using C = typename Cplx<R>::type;
   const R* __restrict__ beta0 = (const R*)a.beta[0];
   const R* __restrict__ beta1 = (const R*)a.beta[D > 1 ? 1 : 0];
@@ -165,8 +166,7 @@ __device__ __forceinline__ void deconv_pad_body(const DeconvArgs& a, const typen
   int64_t rows = 1;
   for (int d = 0; d < last; ++d) rows *= a.Nt[d];
   const int64_t total = rows * half_last;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = first; t < total; t += stride) {
     const int pair = (int)(t % half_last);
     int64_t row = t / half_last;
     // index into f of the outer dimensions; -1 if outside I_N
@@ -221,10 +221,23 @@ __device__ __forceinline__ void deconv_pad_body(const DeconvArgs& a, const typen
 template <int D, typename R>
 __global__ void deconv_pad_kernel(DeconvArgs a, const typename Cplx<R>::type* __restrict__ f,
                                   typename Cplx<R>::type* __restrict__ grid) {
-  deconv_pad_body<D, R>(a, f, grid);
+  deconv_pad_body<D, R>(a, f, grid, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
-// Batched: blockIdx.y selects the problem; sizes and offsets from the table.
+// Batched: one 1D grid over all problems, problem p owning the blocks
+// [block_start[p], block_start[p + 1]) (in proportion to its size, set at
+// batch creation), so that small problems do not launch the blocks of the
+// largest; sizes and offsets from the problem table.
+__device__ __forceinline__ int batch_problem_of_block(const int* __restrict__ block_start, int B) {
+  int lo = 0, hi = B;  // block_start[0] = 0 <= blockIdx.x < block_start[B]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (block_start[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 template <int D, typename R>
 __device__ __forceinline__ DeconvArgs batch_deconv_args(const BatchProblem& P, const R* beta_all) {
   DeconvArgs a{};
@@ -241,27 +254,31 @@ __device__ __forceinline__ DeconvArgs batch_deconv_args(const BatchProblem& P, c
 }
 
 template <int D, typename R>
-__global__ void deconv_pad_batch_kernel(const BatchProblem* __restrict__ probs, const R* __restrict__ beta_all,
+__global__ void deconv_pad_batch_kernel(const BatchProblem* __restrict__ probs, const int* __restrict__ block_start,
+                                        int B, const R* __restrict__ beta_all,
                                         const typename Cplx<R>::type* __restrict__ f,
                                         typename Cplx<R>::type* __restrict__ grid) {
-  const BatchProblem& P = probs[blockIdx.y];
+  const int p = batch_problem_of_block(block_start, B);
+  const BatchProblem& P = probs[p];
   const DeconvArgs a = batch_deconv_args<D, R>(P, beta_all);
-  deconv_pad_body<D, R>(a, f + P.in_off, grid + P.grid_off);
+  const int b0 = block_start[p], nb = block_start[p + 1] - b0;
+  deconv_pad_body<D, R>(a, f + P.in_off, grid + P.grid_off, (blockIdx.x - b0) * (int64_t)blockDim.x + threadIdx.x,
+                        (int64_t)nb * blockDim.x);
 }
 
 // Algorithm 2, crop and correction step: y_n = g[n mod N~] * prod_d beta_d(n_d),
 // n in I_N.
 template <int D, typename R>
 __device__ __forceinline__ void crop_deconv_body(const DeconvArgs& a, const typename Cplx<R>::type* __restrict__ grid,
-                                                 typename Cplx<R>::type* __restrict__ y) {
+                                                 typename Cplx<R>::type* __restrict__ y, int64_t first,
+                                                 int64_t stride) {
   using C = typename Cplx<R>::type;
   const R* __restrict__ beta0 = (const R*)a.beta[0];
   const R* __restrict__ beta1 = (const R*)a.beta[D > 1 ? 1 : 0];
   const R* __restrict__ beta2 = (const R*)a.beta[D > 2 ? 2 : 0];
   int64_t total = 1;
   for (int d = 0; d < D; ++d) total *= a.N[d];
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = first; t < total; t += stride) {
     int64_t rem = t;
     int i[kMaxD];
 #pragma unroll
@@ -290,16 +307,20 @@ __device__ __forceinline__ void crop_deconv_body(const DeconvArgs& a, const type
 template <int D, typename R>
 __global__ void crop_deconv_kernel(DeconvArgs a, const typename Cplx<R>::type* __restrict__ grid,
                                    typename Cplx<R>::type* __restrict__ y) {
-  crop_deconv_body<D, R>(a, grid, y);
+  crop_deconv_body<D, R>(a, grid, y, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 template <int D, typename R>
-__global__ void crop_deconv_batch_kernel(const BatchProblem* __restrict__ probs, const R* __restrict__ beta_all,
+__global__ void crop_deconv_batch_kernel(const BatchProblem* __restrict__ probs, const int* __restrict__ block_start,
+                                         int B, const R* __restrict__ beta_all,
                                          const typename Cplx<R>::type* __restrict__ grid,
                                          typename Cplx<R>::type* __restrict__ y) {
-  const BatchProblem& P = probs[blockIdx.y];
+  const int p = batch_problem_of_block(block_start, B);
+  const BatchProblem& P = probs[p];
   const DeconvArgs a = batch_deconv_args<D, R>(P, beta_all);
-  crop_deconv_body<D, R>(a, grid + P.grid_off, y + P.in_off);
+  const int b0 = block_start[p], nb = block_start[p + 1] - b0;
+  crop_deconv_body<D, R>(a, grid + P.grid_off, y + P.in_off, (blockIdx.x - b0) * (int64_t)blockDim.x + threadIdx.x,
+                         (int64_t)nb * blockDim.x);
 }
 
 template <typename R>
@@ -334,42 +355,46 @@ cudaError_t launch_crop_deconv(const DeconvArgs& a, const void* grid, void* y, c
 
 
 template <typename R>
-cudaError_t launch_deconv_pad_batch(int D, int B, int64_t max_grid, const BatchProblem* probs,
+cudaError_t launch_deconv_pad_batch(int D, int B, const int* block_start, int blocks, const BatchProblem* probs,
                                     const void* beta_all, const void* f, void* grid, cudaStream_t s) {
   using C = typename Cplx<R>::type;
-  dim3 blocks(launch_blocks(max_grid / 2, 256), B);
   const R* beta = (const R*)beta_all;
   if (D == 1)
-    deconv_pad_batch_kernel<1, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)f, (C*)grid);
+    deconv_pad_batch_kernel<1, R><<<blocks, kBatchDeconvThreads, 0, s>>>(probs, block_start, B, beta, (const C*)f,
+                                                                         (C*)grid);
   else if (D == 2)
-    deconv_pad_batch_kernel<2, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)f, (C*)grid);
+    deconv_pad_batch_kernel<2, R><<<blocks, kBatchDeconvThreads, 0, s>>>(probs, block_start, B, beta, (const C*)f,
+                                                                         (C*)grid);
   else
-    deconv_pad_batch_kernel<3, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)f, (C*)grid);
+    deconv_pad_batch_kernel<3, R><<<blocks, kBatchDeconvThreads, 0, s>>>(probs, block_start, B, beta, (const C*)f,
+                                                                         (C*)grid);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_crop_deconv_batch(int D, int B, int64_t max_n, const BatchProblem* probs,
+cudaError_t launch_crop_deconv_batch(int D, int B, const int* block_start, int blocks, const BatchProblem* probs,
                                      const void* beta_all, const void* grid, void* y, cudaStream_t s) {
   using C = typename Cplx<R>::type;
-  dim3 blocks(launch_blocks(max_n, 256), B);
   const R* beta = (const R*)beta_all;
   if (D == 1)
-    crop_deconv_batch_kernel<1, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)grid, (C*)y);
+    crop_deconv_batch_kernel<1, R><<<blocks, kBatchDeconvThreads, 0, s>>>(probs, block_start, B, beta,
+                                                                          (const C*)grid, (C*)y);
   else if (D == 2)
-    crop_deconv_batch_kernel<2, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)grid, (C*)y);
+    crop_deconv_batch_kernel<2, R><<<blocks, kBatchDeconvThreads, 0, s>>>(probs, block_start, B, beta,
+                                                                          (const C*)grid, (C*)y);
   else
-    crop_deconv_batch_kernel<3, R><<<blocks, 256, 0, s>>>(probs, beta, (const C*)grid, (C*)y);
+    crop_deconv_batch_kernel<3, R><<<blocks, kBatchDeconvThreads, 0, s>>>(probs, block_start, B, beta,
+                                                                          (const C*)grid, (C*)y);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_deconv_pad_batch<float>(int, int, int64_t, const BatchProblem*, const void*,
+template cudaError_t launch_deconv_pad_batch<float>(int, int, const int*, int, const BatchProblem*, const void*,
                                                     const void*, void*, cudaStream_t);
-template cudaError_t launch_deconv_pad_batch<double>(int, int, int64_t, const BatchProblem*, const void*,
+template cudaError_t launch_deconv_pad_batch<double>(int, int, const int*, int, const BatchProblem*, const void*,
                                                      const void*, void*, cudaStream_t);
-template cudaError_t launch_crop_deconv_batch<float>(int, int, int64_t, const BatchProblem*, const void*,
+template cudaError_t launch_crop_deconv_batch<float>(int, int, const int*, int, const BatchProblem*, const void*,
                                                      const void*, void*, cudaStream_t);
-template cudaError_t launch_crop_deconv_batch<double>(int, int, int64_t, const BatchProblem*, const void*,
+template cudaError_t launch_crop_deconv_batch<double>(int, int, const int*, int, const BatchProblem*, const void*,
                                                       const void*, void*, cudaStream_t);
 
 template cudaError_t launch_deconv_pad<float>(const DeconvArgs&, const void*, void*, cudaStream_t);
