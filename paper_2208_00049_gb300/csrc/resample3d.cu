@@ -428,14 +428,15 @@ __global__ void __launch_bounds__(32 * W)
 // reads 12 consecutive complex of one row, one shared wavefront per half.
 // The 36 window values of every node are evaluated once per work item
 // (POLYNOMIAL form, packed Horner, two taps per lane) into shared memory:
-// w0 and w1 as packed pairs, w2 zero-padded to 16.
+// w0 and w1 once per tap (paired in registers: stored (w, w) pairs doubled
+// the shared wavefronts of their broadcast loads), w2 zero-padded to 16.
 constexpr int kG12Taps = 12;
 constexpr int kG12Warps = 8;
 constexpr int kG12Threads = 32 * kG12Warps;
 
 struct G12Weights {
-  f32x2 w0p[kItemCap][kG12Taps];
-  f32x2 w1p[kItemCap][kG12Taps];
+  float w0s[kItemCap][kG12Taps];
+  float w1s[kItemCap][kG12Taps];
   float w2[kItemCap][16];
   f32x2 coef[3][kG12Taps / 2][kG12Taps + 1];
 };
@@ -498,9 +499,9 @@ __global__ void __launch_bounds__(kG12Threads, 3)
           for (int e = K - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[e]);
           const float2 w = unpack2(pw);  // taps 2 tp, 2 tp + 1
           if (d == 0) {
-            *reinterpret_cast<float4*>(&wt.w0p[s][2 * tp]) = make_float4(w.x, w.x, w.y, w.y);
+            *reinterpret_cast<float2*>(&wt.w0s[s][2 * tp]) = w;
           } else if (d == 1) {
-            *reinterpret_cast<float4*>(&wt.w1p[s][2 * tp]) = make_float4(w.x, w.x, w.y, w.y);
+            *reinterpret_cast<float2*>(&wt.w1s[s][2 * tp]) = w;
           } else {
             *reinterpret_cast<float2*>(&wt.w2[s][2 * tp]) = w;
             if (tp == 0) *reinterpret_cast<float4*>(&wt.w2[s][K]) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -518,26 +519,28 @@ __global__ void __launch_bounds__(kG12Threads, 3)
       const float w2 = wt.w2[s][i2];
       const f32x2* col = reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1) * pitch + a2 + i2c);
       f32x2 w1[K];
-      const float4* w1q = reinterpret_cast<const float4*>(&wt.w1p[s][0]);
+      const float4* w1q = reinterpret_cast<const float4*>(&wt.w1s[s][0]);
 #pragma unroll
-      for (int q = 0; q < K / 2; ++q) {
+      for (int q = 0; q < K / 4; ++q) {
         const float4 x = w1q[q];
-        w1[2 * q] = pack2(x.x, x.y);
-        w1[2 * q + 1] = pack2(x.z, x.w);
+        w1[4 * q] = pack2(x.x, x.x);
+        w1[4 * q + 1] = pack2(x.y, x.y);
+        w1[4 * q + 2] = pack2(x.z, x.z);
+        w1[4 * q + 3] = pack2(x.w, x.w);
       }
-      const float4* w0q = reinterpret_cast<const float4*>(&wt.w0p[s][0]);
+      const float4* w0q = reinterpret_cast<const float4*>(&wt.w0s[s][0]);
       f32x2 acc = pack2(0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < K / 2; ++q) {
+      for (int q = 0; q < K / 4; ++q) {
         const float4 x = w0q[q];
-        const f32x2 w0a = pack2(x.x, x.y), w0b = pack2(x.z, x.w);
+        const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const f32x2* pl = col + (2 * q + h) * plane;
+        for (int h = 0; h < 4; ++h) {
+          const f32x2* pl = col + (4 * q + h) * plane;
           f32x2 sum = mul2(pl[0], w1[0]);
 #pragma unroll
           for (int i1 = 1; i1 < K; ++i1) sum = fma2(pl[i1 * pitch], w1[i1], sum);
-          acc = fma2(sum, h == 0 ? w0a : w0b, acc);
+          acc = fma2(sum, pack2(xs[h], xs[h]), acc);
         }
       }
       float2 r = unpack2(acc);
