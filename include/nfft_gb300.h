@@ -234,7 +234,9 @@ int nfft_plan_autotune(nfft_plan *p, const void *k, int k_is_fp64, int64_t *chos
  * Many independent problems of one dimension D, sigma, m and dtype, with
  * uneven sizes, run as one persistent gather / scatter launch over all their
  * work items, one deconvolution launch, and one batched cuFFT per distinct
- * oversampled size (Algorithms 1 and 2 applied to each problem).
+ * oversampled size (Algorithms 1 and 2 applied to each problem); the size
+ * classes' FFTs run concurrently on internal streams forked from and joined
+ * back to `stream`.
  *   B problems; problem p has coefficient size N[p*D .. p*D+D-1] and uses
  *   node set set_of[p] (0 <= set_of[p] < S).  S node sets, set s has
  *   M_set[s] nodes; problems sharing a node set must have equal N (several
