@@ -1,8 +1,11 @@
 """Benchmark: NFFT forward + adjoint nodes/s on one GB300 (or N replicas).
 
 A step is one pass of the whole path over one batch: Algorithm 1
-(deconv_pad -> cuFFT forward -> gather) and Algorithm 2 (scatter ->
-cuFFT inverse -> crop_deconv), every kernel launched through the C ABI, on
+(correction + zero pad + FFT -> gather) and Algorithm 2 (scatter -> inverse
+FFT + crop + correction), the FFT steps pruned and fused with the correction
+where the plan qualifies (3D, complex64, N~ = 2N = 256; cuFFT between the
+separate correction kernels otherwise), every kernel launched through the C
+ABI, on
 device-resident inputs (nodes set once: the plan's precomputation, timed
 separately as set_nodes).  value = M / (mean step time) nodes/s, summed over
 ranks; each rank runs an independent replica of the same workload (a single

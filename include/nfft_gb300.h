@@ -270,11 +270,11 @@ int nfft_batch_autotune(nfft_batch *b, const void *k, int k_is_fp64, int64_t *ch
 
 /* ---- spreading without device allocation ------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
- * that must not call cudaMalloc: code running while a CUDA graph is being
- * captured (an allocation there breaks the capture), code living under
- * another framework's allocator (a raw cudaMalloc beside a caching allocator
- * fragments memory and may synchronise the device), and services whose
- * device memory must be reserved when the library loads.
+ * that must not call cudaMalloc: code living under another framework's
+ * allocator (a raw cudaMalloc beside a caching allocator fragments memory
+ * and may synchronise the device), latency-critical loops that cannot take
+ * the implicit device synchronisation of cudaMalloc / cudaFree, and services
+ * whose device memory must be reserved when the library loads.
  *
  * It performs the adjoint resampling step of Algorithm 2 (complex64,
  * half-open support, 2m taps per dimension) without a plan:

@@ -2,10 +2,10 @@
 // NFFT_NOALLOC_MAX_NODES nodes onto a caller-provided oversampled grid with
 // no device allocation at all.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (an allocation there breaks the capture), code running under
-// another framework's allocator (a raw cudaMalloc beside a caching allocator
-// fragments memory and can implicitly synchronise the device), and services
+// Some callers cannot call cudaMalloc: code running under another
+// framework's allocator (a raw cudaMalloc beside a caching allocator
+// fragments memory and can implicitly synchronise the device), latency-
+// critical loops that cannot take that implicit synchronisation, and services
 // with a fixed memory budget that must be reserved when the library is
 // loaded.  For them the bin-sort scratch (node keys, ranks, sorted cells and
 // fractions, the permutation, per-tile counts and offsets, work items) lives
