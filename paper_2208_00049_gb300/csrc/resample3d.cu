@@ -15,7 +15,13 @@
 //  * complex x real products on packed FP32 pairs (fma.rn.f32x2);
 //  * gather: a half-warp per node (a warp instruction serves two nodes);
 //    lane (g, i2) of a half owns taps (i1 = j + 4g, i2), j = 0..3, and loops
-//    over i0, then the half reduces its 16 partial sums;
+//    over i0, then the half reduces its 16 partial sums (reduce-scatter:
+//    one exchange splits real and imaginary parts between the two 8-lane
+//    groups, three more sum each part, 4 shuffles instead of 8); the node
+//    record is read with one 16-byte broadcast load and the w0 / w1 values
+//    are handed out through a per-warp shared slot (three 16-byte broadcast
+//    loads instead of twelve shuffles), since the shared-memory pipe, which
+//    also carries the shuffles, is the binding resource;
 //  * scatter (default): the region is accumulated in registers, see the
 //    register-accumulating scatter below;
 //  * scatter (shared-memory form): W warps (default 2, measured best of
@@ -39,6 +45,8 @@ constexpr int kCoef = kDeg + 1;
 constexpr int kPitch = 18;          // shared row pitch (complex) along dim 2
 constexpr int kMaxTile2 = 9;        // L2 = T2 + 7 <= 16: two rows per warp step
 constexpr int kItemCap = 128;       // nodes per work item staged in shared memory
+constexpr int kGatherSlot = 32;     // floats of window slot per gather warp
+constexpr int kGatherMaxWarps = 8;
 
 // One staged node = 8 words {t0, t1, t2, a0 | a1 << 8 | a2 << 16, perm, re v, im v, 0}
 // (fractions, cell offsets in the tile, caller index, scatter input).  A warp
@@ -150,6 +158,7 @@ template <int GW>
 __global__ void __launch_bounds__(32 * GW)
     gather3d_m4_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na,
                        const float* __restrict__ poly, float2* __restrict__ fhat) {
+  static_assert(GW <= kGatherMaxWarps, "one window slot per warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NodeStage& ns = *reinterpret_cast<NodeStage*>(smem_raw);
   float2* tile = reinterpret_cast<float2*>(smem_raw + sizeof(NodeStage));
@@ -159,6 +168,9 @@ __global__ void __launch_bounds__(32 * GW)
   const int half = lane >> 4, lane16 = lane & 15;
   const int grp = lane16 >> 3, i2 = lane & 7;
   const int hbase = 16 * half;
+  // this warp's window slot (after the tile): [16 half + i] = tap i of
+  // dimension 0 (i < 8) or of dimension 1 (tap i - 8) of the half's node
+  float* wslot = reinterpret_cast<float*>(tile + g.L[0] * plane) + kGatherSlot * warp;
   // lane evaluates tap i2 of dimension grp (weights wA) and of dimension 2 (wB)
   float cA[kCoef], cB[kCoef];
   load_coef(poly, grp, i2, cA);
@@ -181,40 +193,46 @@ __global__ void __launch_bounds__(32 * GW)
 
     for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * GW) {
       const int s = min(s0 + half, item.z - 1);  // a half without a node repeats the last one
-      const float word = ns.w[s][lane & 7];
-      const float tA = __shfl_sync(0xffffffffu, word, hbase + grp);
-      const float tB = __shfl_sync(0xffffffffu, word, hbase + 2);
-      const int pk = __float_as_int(__shfl_sync(0xffffffffu, word, hbase + 3));
-      const int jout = __float_as_int(__shfl_sync(0xffffffffu, word, hbase + 4));
-      const float wA = horner(cA, tA - 0.5f);
-      const float wB = horner(cB, tB - 0.5f);
+      const float4 rec = *reinterpret_cast<const float4*>(ns.w[s]);  // t0, t1, t2, packed offsets
+      const float wA = horner(cA, (grp ? rec.y : rec.x) - 0.5f);
+      const float wB = horner(cB, rec.z - 0.5f);
+      const int pk = __float_as_int(rec.w);
       const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
+      __syncwarp();  // the previous node pair's slot reads are done
+      wslot[lane] = wA;
+      __syncwarp();
+      const float4 w0lo = *reinterpret_cast<const float4*>(wslot + hbase);
+      const float4 w0hi = *reinterpret_cast<const float4*>(wslot + hbase + 4);
+      const float4 w1q = *reinterpret_cast<const float4*>(wslot + hbase + 8 + 4 * grp);
+      const float w0v[kTaps] = {w0lo.x, w0lo.y, w0lo.z, w0lo.w, w0hi.x, w0hi.y, w0hi.z, w0hi.w};
+      const float w1v[4] = {w1q.x * wB, w1q.y * wB, w1q.z * wB, w1q.w * wB};
       f32x2 w12[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float w = __shfl_sync(0xffffffffu, wA, hbase + 8 + j + 4 * grp) * wB;
-        w12[j] = pack2(w, w);
-      }
+      for (int j = 0; j < 4; ++j) w12[j] = pack2(w1v[j], w1v[j]);
       const f32x2* p =
           reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1 + 4 * grp) * kPitch + a2 + i2 + shift);
       f32x2 acc = pack2(0.f, 0.f);
 #pragma unroll
       for (int i0 = 0; i0 < kTaps; ++i0) {
-        const float w0 = __shfl_sync(0xffffffffu, wA, hbase + i0);
         const f32x2* q = p + i0 * plane;
         f32x2 sum = mul2(q[0], w12[0]);
         sum = fma2(q[kPitch], w12[1], sum);
         sum = fma2(q[2 * kPitch], w12[2], sum);
         sum = fma2(q[3 * kPitch], w12[3], sum);
-        acc = fma2(sum, pack2(w0, w0), acc);
+        acc = fma2(sum, pack2(w0v[i0], w0v[i0]), acc);
       }
-      float2 r = unpack2(acc);
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) {
-        r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
-        r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+      // reduce-scatter over the half: group 0 sums the real parts, group 1
+      // the imaginary parts; lane16 = 0 ends with the real sum, lane16 = 8
+      // with the imaginary sum
+      const float2 r = unpack2(acc);
+      float v = (grp ? r.y : r.x) + __shfl_xor_sync(0xffffffffu, grp ? r.x : r.y, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      if (i2 == 0 && s0 + half < item.z) {
+        const int jout = __float_as_int(ns.w[s][4]);
+        reinterpret_cast<float*>(fhat + jout)[grp] = v;
       }
-      if (lane16 == 0 && s0 + half < item.z) fhat[jout] = r;
     }
   }
 }
@@ -242,6 +260,7 @@ template <int GW>
 __global__ void __launch_bounds__(32 * GW)
     grad3d_m4_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na, const float* __restrict__ poly,
                      const float2* __restrict__ cot, float* __restrict__ gk) {
+  static_assert(2 * GW <= kGatherMaxWarps, "two window slots per warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NodeStage& ns = *reinterpret_cast<NodeStage*>(smem_raw);
   float2* tile = reinterpret_cast<float2*>(smem_raw + sizeof(NodeStage));
@@ -251,6 +270,10 @@ __global__ void __launch_bounds__(32 * GW)
   const int half = lane >> 4, lane16 = lane & 15;
   const int grp = lane16 >> 3, i2 = lane & 7;
   const int hbase = 16 * half;
+  // this warp's window slots (after the tile): values at [16 half + i],
+  // derivatives at [32 + 16 half + i] (tap i of dimension 0, tap i - 8 of
+  // dimension 1)
+  float* wslot = reinterpret_cast<float*>(tile + g.L[0] * plane) + 2 * kGatherSlot * warp;
   float cA[kCoef], cB[kCoef];
   load_coef(poly, grp, i2, cA);
   load_coef(poly, 2, i2, cB);
@@ -272,32 +295,41 @@ __global__ void __launch_bounds__(32 * GW)
 
     for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * GW) {
       const int s = min(s0 + half, item.z - 1);  // a half without a node repeats the last one
-      const float word = ns.w[s][lane & 7];
-      const float tA = __shfl_sync(0xffffffffu, word, hbase + grp);
-      const float tB = __shfl_sync(0xffffffffu, word, hbase + 2);
-      const int pk = __float_as_int(__shfl_sync(0xffffffffu, word, hbase + 3));
-      const int jout = __float_as_int(__shfl_sync(0xffffffffu, word, hbase + 4));
-      const float2 A = horner_d(cA, tA - 0.5f);  // tap i2 of dimension grp: value, derivative
-      const float2 Bw = horner_d(cB, tB - 0.5f);  // tap i2 of dimension 2
+      const float4 rec = *reinterpret_cast<const float4*>(ns.w[s]);  // t0, t1, t2, packed offsets
+      const int jout = __float_as_int(ns.w[s][4]);
+      const float2 c = cot[jout];
+      const float2 A = horner_d(cA, (grp ? rec.y : rec.x) - 0.5f);  // tap i2 of dimension grp: value, derivative
+      const float2 Bw = horner_d(cB, rec.z - 0.5f);                 // tap i2 of dimension 2
+      const int pk = __float_as_int(rec.w);
       const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
+      __syncwarp();  // the previous node pair's slot reads are done
+      wslot[lane] = A.x;
+      wslot[32 + lane] = A.y;
+      __syncwarp();
+      const float4 w0lo = *reinterpret_cast<const float4*>(wslot + hbase);
+      const float4 w0hi = *reinterpret_cast<const float4*>(wslot + hbase + 4);
+      const float4 d0lo = *reinterpret_cast<const float4*>(wslot + 32 + hbase);
+      const float4 d0hi = *reinterpret_cast<const float4*>(wslot + 32 + hbase + 4);
+      const float4 w1q = *reinterpret_cast<const float4*>(wslot + hbase + 8 + 4 * grp);
+      const float4 d1q = *reinterpret_cast<const float4*>(wslot + 32 + hbase + 8 + 4 * grp);
+      const float w0v[kTaps] = {w0lo.x, w0lo.y, w0lo.z, w0lo.w, w0hi.x, w0hi.y, w0hi.z, w0hi.w};
+      const float dw0v[kTaps] = {d0lo.x, d0lo.y, d0lo.z, d0lo.w, d0hi.x, d0hi.y, d0hi.z, d0hi.w};
+      const float w1v[4] = {w1q.x, w1q.y, w1q.z, w1q.w};
+      const float dw1v[4] = {d1q.x, d1q.y, d1q.z, d1q.w};
       // rows j + 4 grp: w1 w2, w1' w2, w1 w2'
       f32x2 w12[4], d1[4], d2[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float w1 = __shfl_sync(0xffffffffu, A.x, hbase + 8 + j + 4 * grp);
-        const float dw1 = __shfl_sync(0xffffffffu, A.y, hbase + 8 + j + 4 * grp);
-        const float a = w1 * Bw.x, b = dw1 * Bw.x, c = w1 * Bw.y;
+        const float a = w1v[j] * Bw.x, b = dw1v[j] * Bw.x, e = w1v[j] * Bw.y;
         w12[j] = pack2(a, a);
         d1[j] = pack2(b, b);
-        d2[j] = pack2(c, c);
+        d2[j] = pack2(e, e);
       }
       const f32x2* p =
           reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1 + 4 * grp) * kPitch + a2 + i2 + shift);
       f32x2 D0 = pack2(0.f, 0.f), D1 = D0, D2 = D0;
 #pragma unroll
       for (int i0 = 0; i0 < kTaps; ++i0) {
-        const float w0 = __shfl_sync(0xffffffffu, A.x, hbase + i0);
-        const float dw0 = __shfl_sync(0xffffffffu, A.y, hbase + i0);
         const f32x2* q = p + i0 * plane;
         f32x2 s12 = mul2(q[0], w12[0]), s1 = mul2(q[0], d1[0]), s2 = mul2(q[0], d2[0]);
 #pragma unroll
@@ -307,26 +339,27 @@ __global__ void __launch_bounds__(32 * GW)
           s1 = fma2(v, d1[j], s1);
           s2 = fma2(v, d2[j], s2);
         }
-        D0 = fma2(s12, pack2(dw0, dw0), D0);
-        D1 = fma2(s1, pack2(w0, w0), D1);
-        D2 = fma2(s2, pack2(w0, w0), D2);
+        D0 = fma2(s12, pack2(dw0v[i0], dw0v[i0]), D0);
+        D1 = fma2(s1, pack2(w0v[i0], w0v[i0]), D1);
+        D2 = fma2(s2, pack2(w0v[i0], w0v[i0]), D2);
       }
-      float2 r0 = unpack2(D0), r1 = unpack2(D1), r2 = unpack2(D2);
+      // Re(conj(cot) D_d) is linear in D_d: project each lane's partial sums
+      // before reducing, three real sums over the half instead of six
+      const float2 r0 = unpack2(D0), r1 = unpack2(D1), r2 = unpack2(D2);
+      float e0 = c.x * r0.x + c.y * r0.y;
+      float e1 = c.x * r1.x + c.y * r1.y;
+      float e2 = c.x * r2.x + c.y * r2.y;
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
-        r0.x += __shfl_xor_sync(0xffffffffu, r0.x, o);
-        r0.y += __shfl_xor_sync(0xffffffffu, r0.y, o);
-        r1.x += __shfl_xor_sync(0xffffffffu, r1.x, o);
-        r1.y += __shfl_xor_sync(0xffffffffu, r1.y, o);
-        r2.x += __shfl_xor_sync(0xffffffffu, r2.x, o);
-        r2.y += __shfl_xor_sync(0xffffffffu, r2.y, o);
+        e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+        e1 += __shfl_xor_sync(0xffffffffu, e1, o);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
       }
       if (lane16 == 0 && s0 + half < item.z) {
-        const float2 c = cot[jout];
         float* o = gk + (int64_t)jout * 3;
-        o[0] = (float)g.Nt[0] * (c.x * r0.x + c.y * r0.y);
-        o[1] = (float)g.Nt[1] * (c.x * r1.x + c.y * r1.y);
-        o[2] = (float)g.Nt[2] * (c.x * r2.x + c.y * r2.y);
+        o[0] = (float)g.Nt[0] * e0;
+        o[1] = (float)g.Nt[1] * e1;
+        o[2] = (float)g.Nt[2] * e2;
       }
     }
   }
@@ -868,6 +901,11 @@ size_t smem_bytes(const Geometry& g) {
   return sizeof(NodeStage) + (size_t)g.L[0] * g.L[1] * kPitch * sizeof(float2);
 }
 
+// the gather adds one window slot per warp after the tile
+size_t gather_smem_bytes(const Geometry& g) {
+  return smem_bytes(g) + (size_t)kGatherMaxWarps * kGatherSlot * sizeof(float);
+}
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t smem) {
   if (smem > 48 * 1024)
@@ -883,7 +921,7 @@ bool fast3d_supported(const Geometry& g, int cmax) {
   if (g.T[2] > kMaxTile2 || cmax > kItemCap) return false;
   for (int d = 0; d < 3; ++d)
     if (g.T[d] > g.Nt[d] - kTaps + 1 || g.L[d] > 255) return false;
-  return smem_bytes(g) <= 200 * 1024;
+  return gather_smem_bytes(g) <= 200 * 1024;
 }
 
 int fast3d_ctas_per_sm(const Geometry& g, int kind) {
@@ -904,7 +942,7 @@ int fast3d_ctas_per_sm(const Geometry& g, int kind) {
     return n;
   }
   if (g.K != kTaps) return 0;
-  const size_t smem = smem_bytes(g);
+  const size_t smem = kind == 0 ? gather_smem_bytes(g) : smem_bytes(g);
   void* k = kind == 0 ? gather_kernel_for(gather_warps()) : scatter_kernel_for(scatter_warps());
   const int threads = kind == 0 ? 32 * gather_warps() : 32 * scatter_warps();
   if (set_smem(k, smem) != cudaSuccess) return 0;
@@ -922,7 +960,7 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
     gather3d_k12_kernel<<<ctas, kG12Threads, smem, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat);
     return cudaGetLastError();
   }
-  const size_t smem = smem_bytes(g);
+  const size_t smem = gather_smem_bytes(g);
   const int w = gather_warps();
   void* k = gather_kernel_for(w);
   cudaError_t e = set_smem(k, smem);
@@ -934,7 +972,7 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
 
 cudaError_t launch_grad3d_fast(const Geometry& g, const void* grid, const NodeArrays& na, const float* poly,
                                const void* cot, void* gk, int ctas, cudaStream_t s) {
-  const size_t smem = smem_bytes(g);
+  const size_t smem = gather_smem_bytes(g);
   cudaError_t e = set_smem(grad3d_m4_kernel<4>, smem);
   if (e != cudaSuccess) return e;
   grad3d_m4_kernel<4><<<ctas, 128, smem, s>>>(g, (const float2*)grid, na, poly, (const float2*)cot, (float*)gk);
@@ -942,7 +980,7 @@ cudaError_t launch_grad3d_fast(const Geometry& g, const void* grid, const NodeAr
 }
 
 int grad3d_ctas_per_sm(const Geometry& g) {
-  const size_t smem = smem_bytes(g);
+  const size_t smem = gather_smem_bytes(g);
   if (set_smem(grad3d_m4_kernel<4>, smem) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grad3d_m4_kernel<4>, 128, smem) != cudaSuccess) return 0;
