@@ -146,6 +146,10 @@ cudaError_t launch_grad3d_fast(const Geometry& g, const void* grid, const NodeAr
 // most 17 - 2m cells per dimension); kind 1 of the two functions below.
 bool fast_scatter_supported(const Geometry& g, int cmax);
 int fast3d_ctas_per_sm(const Geometry& g, int kind);  // kind 0 gather, 1 scatter
+// 1 if a CTA of the 3D gather / node gradient gave up its bounded wait for a
+// region copy since the last call (the flag is cleared), 0 if not, -1 if the
+// flag could not be read.  Synchronous; call with the plan's device current.
+int fast3d_take_wait_timeout();
 cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na,
                                  const float* poly, void* fhat, int ctas, cudaStream_t s);
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,

@@ -700,6 +700,11 @@ int nfft_plan_sync(nfft_plan* p) {
   DeviceGuard guard(p->device);
   cudaError_t e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_status(p, e);
+  if (p->fast_gather && p->D == 3) {
+    const int t = fast3d_take_wait_timeout();
+    if (t < 0) return latch(p, NFFT_ERR_CUDA);
+    if (t > 0) return latch(p, NFFT_ERR_TIMEOUT);
+  }
   return p->err;
 }
 

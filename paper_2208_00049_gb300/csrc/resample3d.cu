@@ -29,7 +29,18 @@
 //    with (a0 + i0) = w (mod W), so no two warps touch the same element and
 //    the read-modify-writes need no atomics; the tile (block plus halo) is
 //    then added to the grid with vector global reductions;
-//  * the node records of a work item are staged in shared memory with the tile.
+//  * the node records of a work item are staged in shared memory with the tile;
+//  * gather and node gradient: a region that lies inside the grid (no
+//    periodic wrap; about 81 % of the items at 256^3 with 9 x 9 x 8 tiles)
+//    is copied by the tensor memory accelerator, one 3D box of 18 x L1 x L0
+//    points (cp.async.bulk.tensor, completion on a shared mbarrier) that
+//    lands directly in the padded row layout; a region that wraps, or a tile
+//    with odd T2 (whose rows start on odd points, not on the 16-byte
+//    boundary the copy needs), is copied with 16-byte / 8-byte cp.async.
+//    The mbarrier wait is bounded: a CTA whose copy does not arrive sets a
+//    device flag that nfft_plan_sync reports as NFFT_ERR_TIMEOUT, and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -47,6 +58,47 @@ constexpr int kMaxTile2 = 9;        // L2 = T2 + 7 <= 16: two rows per warp step
 constexpr int kItemCap = 128;       // nodes per work item staged in shared memory
 constexpr int kGatherSlot = 32;     // floats of window slot per gather warp
 constexpr int kGatherMaxWarps = 8;
+constexpr int kGatherTail = kGatherMaxWarps * kGatherSlot * 4 + 16;  // window slots + mbarrier (bytes)
+constexpr int kWaitSpins = 1 << 22;  // bound on the polls of one region copy's mbarrier
+
+// Set by a CTA whose bounded wait for a region copy gave up (read and
+// cleared by fast3d_take_wait_timeout).
+__device__ int g_wait_timeout;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// One 3D box of the grid's tensor map into shared memory (x the contiguous
+// coordinate, in points; x * 8 bytes must be a multiple of 16).
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                             uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 
 // One staged node = 8 words {t0, t1, t2, a0 | a1 << 8 | a2 << 16, perm, re v, im v, 0}
 // (fractions, cell offsets in the tile, caller index, scatter input).  A warp
@@ -153,11 +205,50 @@ __device__ __forceinline__ void load_tile(const Geometry& g, const int* start, c
   }
 }
 
+// Region of one work item into shared memory (a TMA box where the CTA may
+// use one and the region lies inside the grid, cp.async otherwise) and its
+// node records staged; ends with a CTA barrier.  Returns false, uniformly
+// over the CTA, when the bounded wait for a TMA copy gave up.
+__device__ __forceinline__ bool load_region(const Geometry& g, const CUtensorMap* tmap, uint64_t* bar,
+                                            unsigned& phase, bool tma_cta, const int* start,
+                                            const float2* grid, float2* tile, int warp, int lane, int nwarps,
+                                            int shift, const NodeArrays& na, const int4& item, const int* tc,
+                                            NodeStage& ns) {
+  const bool by_tma = tma_cta && shift && start[0] >= 0 && start[0] + g.L[0] <= g.Nt[0] && start[1] >= 0 &&
+                      start[1] + g.L[1] <= g.Nt[1] && start[2] >= 1 && start[2] - 1 + kPitch <= g.Nt[2];
+  if (by_tma) {
+    if (threadIdx.x == 0) {
+      // the previous item's reads of the tile (generic proxy) are ordered
+      // before the copy's writes (async proxy) by the caller's barrier
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(bar, (unsigned)(g.L[0] * g.L[1] * kPitch * (int)sizeof(float2)));
+      tma_load_box(tile, tmap, start[2] - 1, start[1], start[0], bar);
+    }
+  } else {
+    load_tile(g, start, grid, tile, warp, lane, nwarps, shift);
+  }
+  stage_nodes(g, na, item, tc, ns, nullptr, threadIdx.x, blockDim.x);
+  if (!by_tma) {
+    cp_async_wait_all();
+    __syncthreads();
+    return true;
+  }
+  bool done = false;
+  for (int i = 0; i < kWaitSpins && !done; ++i) done = mbar_try_wait(bar, phase);
+  phase ^= 1u;
+  if (__syncthreads_or(!done)) {
+    if (threadIdx.x == 0) atomicExch(&g_wait_timeout, 1);
+    return false;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 template <int GW>
 __global__ void __launch_bounds__(32 * GW)
     gather3d_m4_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na,
-                       const float* __restrict__ poly, float2* __restrict__ fhat) {
+                       const float* __restrict__ poly, float2* __restrict__ fhat,
+                       const __grid_constant__ CUtensorMap tmap, int tma_on) {
   static_assert(GW <= kGatherMaxWarps, "one window slot per warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NodeStage& ns = *reinterpret_cast<NodeStage*>(smem_raw);
@@ -171,6 +262,11 @@ __global__ void __launch_bounds__(32 * GW)
   // this warp's window slot (after the tile): [16 half + i] = tap i of
   // dimension 0 (i < 8) or of dimension 1 (tap i - 8) of the half's node
   float* wslot = reinterpret_cast<float*>(tile + g.L[0] * plane) + kGatherSlot * warp;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(tile + g.L[0] * plane) +
+                                              kGatherMaxWarps * kGatherSlot);
+  const bool tma_cta = tma_on && (smem_u32(tile) & 127) == 0;
+  if (tma_cta && threadIdx.x == 0) mbar_init(bar);
+  unsigned phase = 0;
   // lane evaluates tap i2 of dimension grp (weights wA) and of dimension 2 (wB)
   float cA[kCoef], cB[kCoef];
   load_coef(poly, grp, i2, cA);
@@ -186,10 +282,8 @@ __global__ void __launch_bounds__(32 * GW)
     for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
 
     __syncthreads();
-    load_tile(g, start, grid, tile, warp, lane, GW, shift);
-    stage_nodes(g, na, item, tc, ns, nullptr, threadIdx.x, blockDim.x);
-    cp_async_wait_all();
-    __syncthreads();
+    if (!load_region(g, &tmap, bar, phase, tma_cta, start, grid, tile, warp, lane, GW, shift, na, item, tc, ns))
+      return;
 
     for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * GW) {
       const int s = min(s0 + half, item.z - 1);  // a half without a node repeats the last one
@@ -259,7 +353,8 @@ __device__ __forceinline__ float2 horner_d(const float* c, float zeta) {
 template <int GW>
 __global__ void __launch_bounds__(32 * GW)
     grad3d_m4_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na, const float* __restrict__ poly,
-                     const float2* __restrict__ cot, float* __restrict__ gk) {
+                     const float2* __restrict__ cot, float* __restrict__ gk,
+                     const __grid_constant__ CUtensorMap tmap, int tma_on) {
   static_assert(2 * GW <= kGatherMaxWarps, "two window slots per warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NodeStage& ns = *reinterpret_cast<NodeStage*>(smem_raw);
@@ -274,6 +369,11 @@ __global__ void __launch_bounds__(32 * GW)
   // derivatives at [32 + 16 half + i] (tap i of dimension 0, tap i - 8 of
   // dimension 1)
   float* wslot = reinterpret_cast<float*>(tile + g.L[0] * plane) + 2 * kGatherSlot * warp;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(tile + g.L[0] * plane) +
+                                              kGatherMaxWarps * kGatherSlot);
+  const bool tma_cta = tma_on && (smem_u32(tile) & 127) == 0;
+  if (tma_cta && threadIdx.x == 0) mbar_init(bar);
+  unsigned phase = 0;
   float cA[kCoef], cB[kCoef];
   load_coef(poly, grp, i2, cA);
   load_coef(poly, 2, i2, cB);
@@ -288,10 +388,8 @@ __global__ void __launch_bounds__(32 * GW)
     for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
 
     __syncthreads();
-    load_tile(g, start, grid, tile, warp, lane, GW, shift);
-    stage_nodes(g, na, item, tc, ns, nullptr, threadIdx.x, blockDim.x);
-    cp_async_wait_all();
-    __syncthreads();
+    if (!load_region(g, &tmap, bar, phase, tma_cta, start, grid, tile, warp, lane, GW, shift, na, item, tc, ns))
+      return;
 
     for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * GW) {
       const int s = min(s0 + half, item.z - 1);  // a half without a node repeats the last one
@@ -901,9 +999,62 @@ size_t smem_bytes(const Geometry& g) {
   return sizeof(NodeStage) + (size_t)g.L[0] * g.L[1] * kPitch * sizeof(float2);
 }
 
-// the gather adds one window slot per warp after the tile
-size_t gather_smem_bytes(const Geometry& g) {
-  return smem_bytes(g) + (size_t)kGatherMaxWarps * kGatherSlot * sizeof(float);
+// the gather and the node gradient add the window slots and the region
+// copy's mbarrier after the tile
+size_t gather_smem_bytes(const Geometry& g) { return smem_bytes(g) + kGatherTail; }
+
+// Tensor-memory-accelerator map of the grid for the region copies of the
+// gather and the node gradient: 3D, 8-byte points, box {18, L1, L0} (a
+// region with its padded rows).  False where the copy cannot be used (odd
+// T2, a box larger than the grid or than 256 points, the driver entry point
+// or the encoding unavailable); the kernels then use cp.async throughout.
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// NFFT_GB300_GATHER_TMA=0 keeps every region copy on cp.async (read at each
+// launch, so that both copy forms can be compared in one process).
+bool use_region_tma() {
+  const char* e = getenv("NFFT_GB300_GATHER_TMA");
+  return !(e && strcmp(e, "0") == 0);
+}
+
+bool region_map(const Geometry& g, const void* grid, CUtensorMap* map) {
+  memset(map, 0, sizeof(*map));
+  if (!use_region_tma() || (g.T[2] & 1) || ((uintptr_t)grid & 15)) return false;
+  const int box[3] = {kPitch, g.L[1], g.L[0]};
+  const int dim[3] = {g.Nt[2], g.Nt[1], g.Nt[0]};
+  for (int d = 0; d < 3; ++d)
+    if (box[d] > 256 || box[d] > dim[d]) return false;
+  if ((g.Nt[2] * sizeof(float2)) % 16 != 0) return false;
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t gdim[3] = {(cuuint64_t)dim[0], (cuuint64_t)dim[1], (cuuint64_t)dim[2]};
+  const cuuint64_t gstride[2] = {(cuuint64_t)g.Nt[2] * sizeof(float2),
+                                 (cuuint64_t)g.Nt[1] * g.Nt[2] * sizeof(float2)};
+  const cuuint32_t bdim[3] = {(cuuint32_t)box[0], (cuuint32_t)box[1], (cuuint32_t)box[2]};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(grid), gdim, gstride, bdim,
+                        estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    memset(map, 0, sizeof(*map));
+    return false;
+  }
+  return true;
 }
 
 template <typename K>
@@ -965,8 +1116,11 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
   void* k = gather_kernel_for(w);
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
-  auto kern = reinterpret_cast<void (*)(Geometry, const float2*, NodeArrays, const float*, float2*)>(k);
-  kern<<<ctas, 32 * w, smem, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat);
+  CUtensorMap map;
+  const int tma_on = region_map(g, grid, &map) ? 1 : 0;
+  auto kern = reinterpret_cast<void (*)(Geometry, const float2*, NodeArrays, const float*, float2*,
+                                        const CUtensorMap, int)>(k);
+  kern<<<ctas, 32 * w, smem, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat, map, tma_on);
   return cudaGetLastError();
 }
 
@@ -975,7 +1129,10 @@ cudaError_t launch_grad3d_fast(const Geometry& g, const void* grid, const NodeAr
   const size_t smem = gather_smem_bytes(g);
   cudaError_t e = set_smem(grad3d_m4_kernel<4>, smem);
   if (e != cudaSuccess) return e;
-  grad3d_m4_kernel<4><<<ctas, 128, smem, s>>>(g, (const float2*)grid, na, poly, (const float2*)cot, (float*)gk);
+  CUtensorMap map;
+  const int tma_on = region_map(g, grid, &map) ? 1 : 0;
+  grad3d_m4_kernel<4><<<ctas, 128, smem, s>>>(g, (const float2*)grid, na, poly, (const float2*)cot, (float*)gk,
+                                              map, tma_on);
   return cudaGetLastError();
 }
 
@@ -1006,6 +1163,16 @@ cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArray
   auto kern = reinterpret_cast<void (*)(Geometry, float2*, NodeArrays, const float*, const float2*)>(k);
   kern<<<ctas, 32 * w, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
   return cudaGetLastError();
+}
+
+int fast3d_take_wait_timeout() {
+  int h = 0;
+  if (cudaMemcpyFromSymbol(&h, g_wait_timeout, sizeof(int)) != cudaSuccess) return -1;
+  if (h) {
+    const int z = 0;
+    if (cudaMemcpyToSymbol(g_wait_timeout, &z, sizeof(int)) != cudaSuccess) return -1;
+  }
+  return h;
 }
 
 }  // namespace nfftgb

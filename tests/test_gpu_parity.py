@@ -353,6 +353,35 @@ def test_fast3d_m4_tile_shapes(tile):
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), 1e-5, "adjoint")
 
 
+@pytest.mark.parametrize("tile", [(9, 9, 8), (8, 8, 8), (4, 6, 2)])
+def test_region_copy_forms_agree(tile, monkeypatch):
+    """3D, m = 4, complex64: the gather and the node gradient copy a region
+    that lies inside the grid with one tensor-memory-accelerator box and a
+    wrapping region with cp.async.  Both forms move the same bytes into the
+    same layout, so with the TMA switched off (NFFT_GB300_GATHER_TMA=0) the
+    results must be bit-identical; and both match the oracle."""
+    from paper_2208_00049_gb300.nfft import Plan
+    N, M = (40, 36, 44), 20000
+    case = inputs.small_case(N, M, seed=53, m=4)
+    cot = inputs.complex_normal(np.random.default_rng(7), (M,))
+    plan = Plan(N, M, sigma=2.0, m=4, dtype=torch.complex64)
+    plan.set_tile(tile)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    assert plan.paths()["fast_gather"]
+    f, c = to_dev(case["f"], torch.complex64), to_dev(cot, torch.complex64)
+    out = {}
+    for form in ("1", "0"):
+        monkeypatch.setenv("NFFT_GB300_GATHER_TMA", form)
+        fh = plan.forward(f).cpu().numpy()
+        gk = plan.grad(f, c).cpu().numpy()
+        plan.sync()
+        out[form] = (fh, gk)
+    plan.close()
+    assert np.array_equal(out["1"][0], out["0"][0]), "forward differs between the copy forms"
+    assert np.array_equal(out["1"][1], out["0"][1]), "node gradient differs between the copy forms"
+    assert_close(out["1"][0], onfft.forward(case["k"], case["f"], 2.0, 4), 1e-5, "forward")
+
+
 @pytest.mark.parametrize("sigma", [2.0, 1.25])
 @pytest.mark.parametrize("tile", [(5, 5, 5), (3, 4, 5), (5, 5, 1), (2, 5, 3)])
 def test_fast_m6_tile_shapes(sigma, tile):
