@@ -353,13 +353,14 @@ def test_fast3d_m4_tile_shapes(tile):
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, 4), 1e-5, "adjoint")
 
 
-@pytest.mark.parametrize("tile", [(9, 9, 8), (8, 8, 8), (4, 6, 2)])
+@pytest.mark.parametrize("tile", [(9, 9, 8), (8, 8, 8), (4, 6, 2), (5, 7, 9)])
 def test_region_copy_forms_agree(tile, monkeypatch):
     """3D, m = 4, complex64: the gather and the node gradient copy a region
-    that lies inside the grid with one tensor-memory-accelerator box and a
-    wrapping region with cp.async.  Both forms move the same bytes into the
-    same layout, so with the TMA switched off (NFFT_GB300_GATHER_TMA=0) the
-    results must be bit-identical; and both match the oracle."""
+    that lies inside the grid with one tensor-memory-accelerator box (even
+    T2) and a wrapping region, or any region of an odd-T2 tile, with
+    cp.async.  With the TMA switched off (NFFT_GB300_GATHER_TMA=0) every
+    region goes through cp.async; the same bytes land in the same layout, so
+    the results must be bit-identical; and both match the oracle."""
     from paper_2208_00049_gb300.nfft import Plan
     N, M = (40, 36, 44), 20000
     case = inputs.small_case(N, M, seed=53, m=4)
