@@ -42,6 +42,7 @@ PROFILE_DIR = os.path.join(ROOT, "profiles")
 WORKLOADS = {
     "accuracy": "accuracy",
     "batched": "batched",
+    "diff": "diff",
     "tiles": "tiles",
     "3d": "3d",
     "3d_lean": "3d_lean",
@@ -463,6 +464,73 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+def run_diff(args):
+    """Workload 5 (differentiation): one loss-and-gradient step on the 2D
+    256 x 256 problem with the jittered 402 x 512 radial node set:
+    r = A(x) f - y (nfft_forward), then grad_f = A^H (2 r) (nfft_adjoint)
+    and grad_x = Re(conj(2 r) d(A(x) f)/dx) (nfft_grad), all through the C
+    ABI; the residual 2 (fhat - y) is the caller's loss, computed with torch.
+    nodes/s = M / step time, complex64 (the line's value) beside complex128;
+    the complex64 gradients' relative L2 error against the complex128 form."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_00049_gb300 import inputs
+    from paper_2208_00049_gb300.nfft import Plan
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    wl = inputs.differentiation()
+    M, N = wl["M"], wl["N"]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    k = torch.from_numpy(wl["k"]).cuda()
+    ms, grads, clocks = {}, {}, None
+    for name, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
+        plan = Plan(N, M, sigma=wl["sigma"], m=wl["m"], dtype=dt)
+        plan.set_nodes(k)
+        f = torch.from_numpy(wl["f"]).to(dt).cuda()
+        y = torch.from_numpy(wl["y"]).to(dt).cuda()
+        fh = torch.empty(M, dtype=dt, device="cuda")
+        cot = torch.empty(M, dtype=dt, device="cuda")
+        gf = torch.empty(N, dtype=dt, device="cuda")
+        gk = torch.empty((M, 2), dtype=plan.real_dtype, device="cuda")
+
+        def step():
+            plan.forward(f, out=fh)
+            torch.sub(fh, y, out=cot)
+            cot.mul_(2)
+            plan.adjoint(cot, out=gf)
+            plan.grad(f, cot, out=gk)
+        steps = args.steps if name == "c64" else max(10, min(args.steps, 50))
+        if name == "c64":
+            with ClockSampler(local) as clk:
+                ms[name] = time_steps(step, steps, max(3, args.warmup), stream, flush)
+            clocks = clk.summary()
+        else:
+            ms[name] = time_steps(step, steps, max(3, args.warmup), stream, flush)
+        plan.sync()
+        grads[name] = (gf.cpu().numpy().astype(np.complex128), gk.cpu().numpy().astype(np.float64))
+        plan.close()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    line = {"metric": "NFFT loss + gradients (f and nodes) nodes/s, 2D 256^2, jittered radial set",
+            "value": M / (ms["c64"] * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms["c64"], 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded PCG64)",
+            "config": {"workload": "differentiation 2D N=256x256 M=%d (402 spokes x 512, angle jitter 1e-3) "
+                                   "sigma=2 m=4" % M,
+                       "step": "nfft_forward, residual, nfft_adjoint, nfft_grad",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "fp64_form": {"value": M / (ms["c128"] * 1e-3), "unit": UNIT, "ms_per_step": round(ms["c128"], 4),
+                          "dtype": "f64"},
+            "accuracy": {"rel_l2_grad_f_fp32_vs_fp64": rel(grads["c64"][0], grads["c128"][0]),
+                         "rel_l2_grad_x_fp32_vs_fp64": rel(grads["c64"][1], grads["c128"][1])},
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
 def run_accuracy(args):
     """Figs. 1-2 analogue on the GPU: relative errors (L2 and the paper's
     infinity norm) of the direct and adjoint NFFT against the exact NDFT for
@@ -786,6 +854,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "diff":
+        run_diff(args)
     elif args.workload == "accuracy":
         run_accuracy(args)
     elif args.workload == "tiles":
