@@ -140,7 +140,9 @@ int nfft_grad(nfft_plan *p, const void *f, const void *cot, void *gk);
  * tensor memory accelerator and wait for it on a shared-memory barrier
  * with an iteration limit; a copy that never arrives makes the kernel
  * return early and this call return NFFT_ERR_TIMEOUT (the outputs of that
- * transform are then undefined). */
+ * transform are then undefined).  The flag behind it is kept per device,
+ * not per plan: the first nfft_plan_sync after the event, of any plan on
+ * that device that uses these kernels, reports it and clears it. */
 int nfft_plan_sync(nfft_plan *p);
 
 /* Static, human-readable text for a status code. */
