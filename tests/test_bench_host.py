@@ -62,3 +62,31 @@ def test_reference_arm_other_ranks_exit_quietly():
                          env=dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == ""
+
+
+def test_reference_plan_fits_the_budget():
+    """The reference arm sizes each step so that --steps K ends within the
+    budget: many steps reuse one full-size grid timing and take small node
+    samples; few steps re-time the grid and take large samples (up to the cap)."""
+    import bench
+    grid_each, n = bench.reference_plan(t_grid=0.7, t_fixed=0.03, s_per_node=4e-5, steps=300, M=2097152,
+                                        cap=131072, budget=90.0)
+    assert not grid_each
+    assert n == int((90.0 / 300 - 0.03) / 4e-5)
+    assert 300 * (0.03 + n * 4e-5) <= 90.0 + 1e-6
+    grid_each, n = bench.reference_plan(t_grid=0.7, t_fixed=0.03, s_per_node=4e-5, steps=20, M=2097152,
+                                        cap=131072, budget=90.0)
+    assert grid_each and n == int((90.0 / 20 - 0.7 - 0.03) / 4e-5)
+    assert 20 * (0.7 + 0.03 + n * 4e-5) <= 90.0 + 1e-6
+    assert bench.reference_plan(0.7, 0.03, 4e-5, 5, 2097152, 131072, 90.0) == (True, 131072)
+    # never below 1024 nodes, never above M
+    assert bench.reference_plan(5.0, 1.0, 1e-3, 10000, 2097152, 131072, 90.0)[1] == 1024
+    assert bench.reference_plan(0.001, 0.0, 1e-7, 1, 1024, 131072, 90.0)[1] == 1024
+
+
+def test_reference_estimate_counts_the_fixed_part_once():
+    import bench
+    est = bench.reference_estimate(t_grid=1.0, t_fixed=0.1, t_nodes=0.1 + 1000 * 1e-4, n=1000, M=2000000)
+    assert abs(est - (1.0 + 0.1 + 1e-4 * 2000000)) < 1e-6
+    # a step faster than the calibrated fixed part contributes no negative time
+    assert bench.reference_estimate(1.0, 0.1, 0.05, 1000, 2000000) == 1.1
