@@ -277,3 +277,36 @@ def test_wide_footprint_invariants():
         ee[d] = h
         fd = (nfft.resample(p, k + ee, ghat) - nfft.resample(p, k - ee, ghat)) / (2 * h)
         assert np.allclose(dk[:, d], fd, rtol=0, atol=2e-6 * np.abs(fd).max())
+
+
+@pytest.mark.parametrize("N", [(8,), (6, 10), (4, 6, 8)])
+def test_fftshift_as_phase_when_oversampling_by_two(N):
+    """The pruned FFT's reading of the index map (Sec. 3.5) for N~ = 2N: the
+    oracle's correction + zero pad (f_n stored at n mod N~) followed by the
+    forward FFT equals storing the corrected f at array index n + N/2 (a plain
+    zero pad) and multiplying the DFT output at l by i^l per dimension; the
+    adjoint FFT followed by crop + correction equals multiplying the grid by
+    (-i)^l, the inverse DFT, and reading index n + N/2."""
+    rng = np.random.default_rng(31)
+    p = nfft.Params(N, 2.0, 2)
+    assert p.Nt == tuple(2 * n for n in N)
+    f = _cn(rng, N)
+    g = nfft.correction_pad(p, f)
+    want = nfft.fft_forward(g)
+    # the same corrected values, stored at index n + N/2 (no wrap)
+    corrected = g[np.ix_(*[np.mod(window.index_set(n), nt) for n, nt in zip(N, p.Nt)])]
+    shifted = np.zeros(p.Nt, complex)
+    shifted[tuple(slice(0, n) for n in N)] = corrected
+    phase = np.ones(p.Nt, complex)
+    for d, nt in enumerate(p.Nt):
+        shape = [1] * len(N)
+        shape[d] = nt
+        phase = phase * (1j ** np.arange(nt)).reshape(shape)
+    got = np.fft.fftn(shifted) * phase
+    assert np.allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+    # adjoint: (-i)^l on the grid, unnormalised inverse DFT, read index n + N/2
+    gh = _cn(rng, p.Nt)
+    want_y = nfft.crop_correction(p, nfft.fft_adjoint(gh))
+    y = np.fft.ifftn(gh * np.conj(phase), norm="forward")[tuple(slice(0, n) for n in N)]
+    corr = nfft.crop_correction(p, np.ones(p.Nt, complex))  # the correction factors alone
+    assert np.allclose(y * corr, want_y, rtol=0, atol=1e-12 * np.abs(want_y).max())
