@@ -71,3 +71,24 @@ def test_status_strings_and_argument_validation(built_lib):
     assert B.nfft_set_nodes(None, None, 1) == B.NFFT_ERR_INVALID_ARG
     assert B.nfft_plan_destroy(None) == B.NFFT_OK
     assert B.nfft_plan_grid(None) is None
+
+
+def test_spread_noalloc_rejects_before_touching_a_device(built_lib):
+    """The allocation-free spreading call checks its arguments on the host:
+    invalid sizes, sizes beyond its static scratch, and buffers that are not
+    device memory are rejected with a status code (no kernel is launched)."""
+    import numpy as np
+    from paper_2208_00049_gb300 import binding as B
+    dummy = 256  # never dereferenced: the size checks come first
+    assert B.nfft_spread_noalloc(0, (32,), 2.0, 4, 8, dummy, dummy, dummy, None) == B.NFFT_ERR_INVALID_ARG
+    assert B.nfft_spread_noalloc(1, (32,), 1.0, 4, 8, dummy, dummy, dummy, None) == B.NFFT_ERR_INVALID_ARG
+    assert B.nfft_spread_noalloc(1, (32,), 2.0, 0, 8, dummy, dummy, dummy, None) == B.NFFT_ERR_INVALID_ARG
+    assert B.nfft_spread_noalloc(1, (32,), 2.0, 4, 8, 0, dummy, dummy, None) == B.NFFT_ERR_INVALID_ARG
+    assert B.nfft_spread_noalloc(1, (32,), 2.0, 4, B.NFFT_NOALLOC_MAX_NODES + 1, dummy, dummy, dummy,
+                                 None) == B.NFFT_ERR_UNSUPPORTED
+    # host buffers of valid sizes: not device memory
+    k = np.zeros((8, 1))
+    w = np.zeros(8, np.complex64)
+    g = np.zeros(64, np.complex64)
+    assert B.nfft_spread_noalloc(1, (32,), 2.0, 4, 8, k.ctypes.data, w.ctypes.data, g.ctypes.data,
+                                 None) == B.NFFT_ERR_INVALID_ARG
