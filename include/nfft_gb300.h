@@ -49,7 +49,8 @@ extern "C" {
 #define NFFT_ERR_CUFFT         -4   /* cuFFT returned an error */
 #define NFFT_ERR_CUDA          -5   /* CUDA runtime returned an error */
 #define NFFT_ERR_TIMEOUT       -6   /* a bounded device wait gave up */
-#define NFFT_ERR_DEVICE_CHECK  -7   /* a device-side range check failed */
+#define NFFT_ERR_DEVICE_CHECK  -7   /* a device-side range check failed (reserved: no
+                                        kernel of this build makes such checks) */
 #define NFFT_ERR_UNSUPPORTED   -8   /* valid but not supported by this build */
 
 /* ---- dtypes and flags ------------------------------------------------ */
