@@ -70,6 +70,10 @@ def parse():
                     help="skip the complex128 (FP64) comparison run")
     ap.add_argument("--no-full-form", action="store_true",
                     help="skip the FULL sparse-matrix (cuSPARSE) comparison run")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="default line only: skip the other workloads measured in the same run")
+    ap.add_argument("--other-steps", type=int, default=20,
+                    help="timed steps of each other workload in the default line")
     return ap.parse_args()
 
 
@@ -260,6 +264,118 @@ def cpu_cores_used():
     return 1
 
 
+def host_cpu():
+    """CPU model name and the cores this process may use."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return {"model": model or "unknown", "nproc": cores}
+
+
+def _oracle_node_worker(task):
+    """One process of the all-core oracle: the oracle's gather and scatter
+    steps on a chunk of nodes; the gather reads the shared grid, the scatter
+    writes this worker's partial grid into its own shared block."""
+    import numpy as np
+    from multiprocessing import shared_memory
+    from oracle import nfft as onfft
+    grid_name, part_name, shape, N, sigma, m, k, w = task
+    gsh = shared_memory.SharedMemory(name=grid_name)
+    psh = shared_memory.SharedMemory(name=part_name)
+    try:
+        gh = np.ndarray(shape, dtype=np.complex128, buffer=gsh.buf)
+        part = np.ndarray(shape, dtype=np.complex128, buffer=psh.buf)
+        p = onfft.Params(N, sigma, m)
+        fh = onfft.resample(p, k, gh)
+        part[...] = onfft.resample_adjoint(p, k, w)
+        return int(fh.shape[0])
+    finally:
+        del gh, part
+        gsh.close()
+        psh.close()
+
+
+def _oracle_warm(_):
+    from oracle import nfft  # noqa: F401  (import once per worker before timing)
+    return 0
+
+
+def oracle_all_cores(wl, procs=None, max_nodes=None):
+    """The unchanged FP64 oracle on every host core: the grid steps
+    (correction + pad, FFT, inverse FFT, crop + correction; numpy, one core)
+    at full size, and the node steps (gather and scatter) on the node set split
+    into one chunk per process (spawned processes, the grid in shared memory),
+    the partial grids of the scatter summed at the end.  Times the full node
+    set unless max_nodes caps it (then scaled by M / nodes).  Returns
+    (nodes/s for the full workload, details)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import numpy as np
+    from oracle import nfft as onfft
+    info = host_cpu()
+    P = max(1, min(int(procs or info["nproc"]), 64))
+    M = wl["M"]
+    n = M if not max_nodes else min(M, int(max_nodes))
+    p = onfft.Params(wl["N"], wl["sigma"], wl["m"])
+    t0 = time.perf_counter()
+    g = onfft.correction_pad(p, wl["f"])
+    gh = onfft.fft_forward(g)
+    t_grid_fwd = time.perf_counter() - t0
+    shape = gh.shape
+    nbytes = gh.nbytes
+    gsh = shared_memory.SharedMemory(create=True, size=nbytes)
+    parts = [shared_memory.SharedMemory(create=True, size=nbytes) for _ in range(P)]
+    try:
+        np.ndarray(shape, dtype=np.complex128, buffer=gsh.buf)[...] = gh
+        bounds = np.linspace(0, n, P + 1).astype(int)
+        tasks = [(gsh.name, parts[i].name, shape, wl["N"], wl["sigma"], wl["m"],
+                  wl["k"][bounds[i]:bounds[i + 1]], wl["w"][bounds[i]:bounds[i + 1]]) for i in range(P)]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(P) as pool:
+            pool.map(_oracle_warm, range(P))
+            t1 = time.perf_counter()
+            pool.map(_oracle_node_worker, tasks)
+            acc = np.zeros(shape, dtype=np.complex128)
+            for ps in parts:
+                acc += np.ndarray(shape, dtype=np.complex128, buffer=ps.buf)
+            t_nodes = time.perf_counter() - t1
+        t2 = time.perf_counter()
+        onfft.crop_correction(p, onfft.fft_adjoint(acc))
+        t_grid_adj = time.perf_counter() - t2
+    finally:
+        for sh in [gsh] + parts:
+            sh.close()
+            sh.unlink()
+    t_full = t_grid_fwd + t_grid_adj + t_nodes * M / n
+    return M / t_full, {
+        "cores": P, "cpu_model": info["model"], "nproc": info["nproc"],
+        "sample": ("full %s grid, %s; node steps in %d spawned processes (grid in shared memory, partial "
+                   "scatter grids summed), grid steps on one core" % (
+                       "x".join(str(v) for v in wl["N"]),
+                       "all %d nodes" % M if n == M else "%d of %d nodes scaled by M/sample" % (n, M), P)),
+        "t_grid_s": round(t_grid_fwd + t_grid_adj, 3), "t_nodes_s": round(t_nodes, 3),
+        "t_full_s": round(t_full, 3)}
+
+
 REF_BUDGET_S = 90.0  # timed part of a --impl reference run, whatever --steps asks for
 
 
@@ -337,27 +453,34 @@ def run_reference(args):
     for i in range(max(1, args.warmup)):
         _oracle_nodes_s(wl, p, gh, 0, min(Ms, 4096))
     vals = []
+    t_loop = time.perf_counter()
     for i in range(max(1, args.steps)):
         tg = _oracle_grid_s(wl, p)[0] if grid_each else t_grid
         lo = (i * Ms) % max(1, M - Ms + 1)
         tn = _oracle_nodes_s(wl, p, gh, lo, Ms)
         vals.append(M / reference_estimate(tg, t_fixed, tn, Ms, M))
+    t_loop = time.perf_counter() - t_loop
     value = statistics.median(vals)
+    # a step is the bounded sample actually run (its wall time), not the
+    # full-workload time that value extrapolates to
+    ms_step = 1e3 * t_loop / max(1, args.steps)
     sample = ("full %s grid (grid steps %s), %d of %d nodes per step; the node steps' per-node part "
               "scaled by M/sample, their fixed part (%.3f s) counted once" % (
                   "x".join(str(n) for n in wl["N"]),
                   "timed each step" if grid_each else "timed once at full size", Ms, M, t_fixed))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * M / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded PCG64, uniform nodes)",
         "config": {"workload": workload_desc(wl), "parallelism": "none (host cores)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": host_cpu()["model"], "nproc": host_cpu()["nproc"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "oracle_detail": {"t_grid_s": round(t_grid, 3), "t_node_fixed_s": round(t_fixed, 4),
-                          "s_per_node": s_per_node, "nodes_per_step": Ms, "grid_timed_each_step": grid_each},
+                          "s_per_node": s_per_node, "nodes_per_step": Ms, "grid_timed_each_step": grid_each,
+                          "full_workload_s_per_step_estimate": round(M / value, 3),
+                          "timed_loop_s": round(t_loop, 3)},
     }
     print(json.dumps(line))
 
@@ -399,6 +522,41 @@ def aggregate_replicas(local_ms_total, units_per_rank, steps):
     ms_per_step = total / steps
     return {"world": world, "ms_total_max": total, "ms_per_step": ms_per_step,
             "value": world * units_per_rank / (ms_per_step * 1e-3)}
+
+
+def split_problems(weights, world, rank):
+    """Indices of the independent problems rank `rank` of `world` runs: each
+    problem goes to exactly one rank, largest first to the least-loaded rank
+    (ties to the lower rank), so every rank's share of the total weight is
+    within one problem of the mean.  Host logic only."""
+    order = sorted(range(len(weights)), key=lambda i: (-float(weights[i]), i))
+    load = [0.0] * world
+    owner = [0] * len(weights)
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += float(weights[i])
+    return [i for i in range(len(weights)) if owner[i] == rank]
+
+
+def aggregate_split(local_ms_total, local_units, steps):
+    """Whole-job numbers when ranks share one workload (strong scaling): the
+    slowest rank's total time and the units of all ranks over it.  Works with
+    any initialised process group; world size 1 needs none."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    total, units = float(local_ms_total), float(local_units)
+    if world > 1:
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total, units = float(t.item()), float(u.item())
+    ms_per_step = total / steps
+    return {"world": world, "ms_total_max": total, "ms_per_step": ms_per_step, "units": units,
+            "value": units / (ms_per_step * 1e-3)}
 
 
 def time_steps(step_fn, steps, warmup, stream, flush):
@@ -488,24 +646,27 @@ def ndft_sample_error(wl, fhat, n=48, seed=11):
     return float(np.linalg.norm(fhat[sel] - ex) / np.linalg.norm(ex))
 
 
-def run_batched(args):
-    """Workload 4: 64 uneven 2D problems in one persistent launch per step,
-    graph-captured, autotuned tile (nodes/s summed over the problems)."""
+def batch_weights(probs):
+    """Work of each batched problem: its nodes plus its oversampled grid points."""
+    return [p["M"] + 4 * p["N"][0] * p["N"][1] for p in probs]
+
+
+def measure_batched(steps, warmup, flush, tile=None, which=None, clock_gpu=None):
+    """Workload 4: the given problems (default: all 64) of the uneven 2D batch
+    in one persistent launch per step, graph-captured, tile from the
+    autotuner unless given.  Returns a dict (ms per step, nodes, ...)."""
     import numpy as np
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2208_00049_gb300 import inputs
     from paper_2208_00049_gb300.nfft import Batch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     probs = inputs.batched_problems(n_problems=64)
+    which = list(range(len(probs))) if which is None else list(which)
+    probs = [probs[i] for i in which]
     Ns = [p["N"] for p in probs]
     Ms = [p["M"] for p in probs]
-    b = Batch(Ns, list(range(64)), Ms, sigma=2.0, m=4, dtype=torch.complex64)
+    b = Batch(Ns, list(range(len(probs))), Ms, sigma=2.0, m=4, dtype=torch.complex64)
     k_all = torch.from_numpy(np.concatenate([p["k"] for p in probs])).cuda()
-    if args.tile:
-        tile = tuple(int(x) for x in args.tile.split(","))
+    if tile:
         b.set_tile(tile)
         b.set_nodes(k_all)
     else:
@@ -515,49 +676,80 @@ def run_batched(args):
     w_all = torch.cat([torch.from_numpy(p["w"]) for p in probs]).to(torch.complex64).cuda()
     fh = torch.empty(sum(Ms), dtype=torch.complex64, device="cuda")
     y = torch.empty(f_all.numel(), dtype=torch.complex64, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
         b.forward(f_all, fh)
         b.adjoint(w_all, y)
-    with ClockSampler(local) as clk:
-        ms = time_steps(step, args.steps, max(3, args.warmup), stream, flush)
+    clocks = None
+    if clock_gpu is not None:
+        with ClockSampler(clock_gpu) as clk:
+            ms = time_steps(step, steps, max(3, warmup), stream, flush)
+        clocks = clk.summary()
+    else:
+        ms = time_steps(step, steps, max(3, warmup), stream, flush)
     info = b.info()
     b.close()
-    M = sum(Ms)
-    line = {"metric": "batched NFFT fwd+adj nodes/s (64 uneven 2D problems, one launch per step)",
-            "value": M / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic (seeded PCG64)",
-            "config": {"workload": "batched 64 x 2D N in {64..512}^2, M = N1 N2 U(0.5,2), total M = %d" % M,
-                       "tile": list(tile), "tile_from": "--tile" if args.tile else "autotuner",
-                       "work_items": info["n_items"], "fft_classes": info["fft_classes"],
-                       "graph": True, "l2": "flushed between steps (256 MiB write)"},
-            "clocks": clk.summary()}
-    print(json.dumps(line))
+    return {"ms": ms, "M": sum(Ms), "problems": which, "tile": list(tile), "info": info, "clocks": clocks}
 
 
-def run_diff(args):
+def run_batched(args):
+    """Workload 4: 64 uneven 2D problems in one persistent launch per step,
+    graph-captured, autotuned tile (nodes/s summed over the problems).  With
+    N ranks the problems are split over the ranks (no collective on the data
+    path): each rank runs its share as one batch, the job time is the max
+    over ranks and the value sums all ranks' nodes (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_00049_gb300 import inputs
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    which = split_problems(batch_weights(inputs.batched_problems(n_problems=64)), world, rank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    tile = tuple(int(x) for x in args.tile.split(",")) if args.tile else None
+    if world > 1:
+        dist.barrier()
+    r = measure_batched(args.steps, args.warmup, flush, tile=tile, which=which, clock_gpu=local)
+    agg = aggregate_split(r["ms"] * args.steps, r["M"], args.steps)
+    if rank == 0:
+        line = {"metric": "batched NFFT fwd+adj nodes/s (64 uneven 2D problems, one launch per step)",
+                "value": agg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(agg["ms_per_step"], 4), "higher_is_better": True,
+                "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded PCG64)",
+                "config": {"workload": "batched 64 x 2D N in {64..512}^2, M = N1 N2 U(0.5,2), total M = %d"
+                           % int(agg["units"]),
+                           "split": "problems split over ranks (largest first to the least-loaded rank)"
+                                    if world > 1 else "one batch",
+                           "rank0_problems": len(r["problems"]), "tile": r["tile"],
+                           "tile_from": "--tile" if args.tile else "autotuner",
+                           "work_items": r["info"]["n_items"], "fft_classes": r["info"]["fft_classes"],
+                           "graph": True, "l2": "flushed between steps (256 MiB write)"},
+                "clocks": r["clocks"]}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_diff(steps, warmup, flush, clock_gpu=None):
     """Workload 5 (differentiation): one loss-and-gradient step on the 2D
     256 x 256 problem with the jittered 402 x 512 radial node set:
     r = A(x) f - y (nfft_forward), then grad_f = A^H (2 r) (nfft_adjoint)
     and grad_x = Re(conj(2 r) d(A(x) f)/dx) (nfft_grad), all through the C
     ABI; the residual 2 (fhat - y) is the caller's loss, computed with torch.
-    nodes/s = M / step time, complex64 (the line's value) beside complex128;
-    the complex64 gradients' relative L2 error against the complex128 form."""
+    complex64 beside complex128, and the complex64 gradients' relative L2
+    error against the complex128 ones."""
     import numpy as np
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2208_00049_gb300 import inputs
     from paper_2208_00049_gb300.nfft import Plan
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     wl = inputs.differentiation()
     M, N = wl["M"], wl["N"]
     stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     k = torch.from_numpy(wl["k"]).cuda()
     ms, grads, clocks = {}, {}, None
     for name, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
@@ -576,19 +768,34 @@ def run_diff(args):
             cot.mul_(2)
             plan.adjoint(cot, out=gf)
             plan.grad(f, cot, out=gk)
-        steps = args.steps if name == "c64" else max(10, min(args.steps, 50))
-        if name == "c64":
-            with ClockSampler(local) as clk:
-                ms[name] = time_steps(step, steps, max(3, args.warmup), stream, flush)
+        n = steps if name == "c64" else max(10, min(steps, 50))
+        if name == "c64" and clock_gpu is not None:
+            with ClockSampler(clock_gpu) as clk:
+                ms[name] = time_steps(step, n, max(3, warmup), stream, flush)
             clocks = clk.summary()
         else:
-            ms[name] = time_steps(step, steps, max(3, args.warmup), stream, flush)
+            ms[name] = time_steps(step, n, max(3, warmup), stream, flush)
         plan.sync()
         grads[name] = (gf.cpu().numpy().astype(np.complex128), gk.cpu().numpy().astype(np.float64))
         plan.close()
 
     def rel(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"M": M, "ms": ms, "clocks": clocks,
+            "accuracy": {"rel_l2_grad_f_fp32_vs_fp64": rel(grads["c64"][0], grads["c128"][0]),
+                         "rel_l2_grad_x_fp32_vs_fp64": rel(grads["c64"][1], grads["c128"][1])}}
+
+
+def run_diff(args):
+    """Workload 5 as its own line (see measure_diff)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    r = measure_diff(args.steps, args.warmup, flush, clock_gpu=local)
+    M, ms = r["M"], r["ms"]
     line = {"metric": "NFFT loss + gradients (f and nodes) nodes/s, 2D 256^2, jittered radial set",
             "value": M / (ms["c64"] * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms["c64"], 4), "higher_is_better": True,
@@ -599,10 +806,137 @@ def run_diff(args):
                        "l2": "flushed between steps (256 MiB write)"},
             "fp64_form": {"value": M / (ms["c128"] * 1e-3), "unit": UNIT, "ms_per_step": round(ms["c128"], 4),
                           "dtype": "f64"},
-            "accuracy": {"rel_l2_grad_f_fp32_vs_fp64": rel(grads["c64"][0], grads["c128"][0]),
-                         "rel_l2_grad_x_fp32_vs_fp64": rel(grads["c64"][1], grads["c128"][1])},
-            "clocks": clocks}
+            "accuracy": r["accuracy"], "clocks": r["clocks"]}
     print(json.dumps(line))
+
+
+def measure_single(name, steps, warmup, flush, clock_gpu=None, cpu_oracle=False):
+    """One single-problem workload through the step ABI (correction + pad +
+    FFT, gather, scatter, inverse FFT + crop + correction), like the default
+    line: ms per step and per kernel, nodes/s, accuracy against the exact
+    NDFT on sampled nodes / outputs, the complex64 result against the
+    complex128 form of the same workload, and (cpu_oracle) the FP64 oracle
+    timed on the full workload on one core."""
+    import numpy as np
+    import torch
+    from oracle import ndft as ondft
+    from oracle import nfft as onfft
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300 import inputs
+    from paper_2208_00049_gb300.nfft import Plan
+    wl = inputs.workload(name)
+    dt = torch.complex64 if wl["dtype"] == "c64" else torch.complex128
+    stream = torch.cuda.current_stream()
+    N, M = wl["N"], wl["M"]
+
+    def build(dtype):
+        plan = Plan(N, M, sigma=wl["sigma"], m=wl["m"], dtype=dtype)
+        plan.set_nodes(torch.from_numpy(wl["k"]).cuda())
+        return plan
+    plan = build(dt)
+    h = plan.handle
+    f_d = torch.from_numpy(wl["f"]).to(dt).cuda()
+    w_d = torch.from_numpy(wl["w"]).to(dt).cuda()
+    fh = torch.empty(M, dtype=dt, device="cuda")
+    y = torch.empty(N, dtype=dt, device="cuda")
+    names = ["pad_fft", "gather", "scatter", "fft_crop"]
+
+    def step(evs):
+        evs[0].record(stream)
+        B.check(B.nfft_step_pad_fft(h, f_d.data_ptr()))
+        evs[1].record(stream)
+        B.check(B.nfft_step_gather(h, fh.data_ptr()))
+        evs[2].record(stream)
+        B.check(B.nfft_step_scatter(h, w_d.data_ptr()))
+        evs[3].record(stream)
+        B.check(B.nfft_step_fft_crop(h, y.data_ptr()))
+        evs[4].record(stream)
+    for _ in range(max(3, warmup)):
+        flush.zero_()
+        step([torch.cuda.Event(enable_timing=True) for _ in range(5)])
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+
+    def timed():
+        for e in evs:
+            flush.zero_()
+            step(e)
+        torch.cuda.synchronize()
+    clocks = None
+    if clock_gpu is not None:
+        with ClockSampler(clock_gpu) as clk:
+            timed()
+        clocks = clk.summary()
+    else:
+        timed()
+    B.check(B.nfft_plan_sync(h))
+    step_ms = statistics.mean(e[0].elapsed_time(e[-1]) for e in evs)
+    kern = {n: round(statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs), 4) for j, n in enumerate(names)}
+    fh_np, y_np = fh.cpu().numpy().astype(np.complex128), y.cpu().numpy().astype(np.complex128)
+    plan.close()
+    # accuracy: exact NDFT on sampled nodes and outputs
+    rng = np.random.default_rng(11)
+    ns = min(M, 16 if len(N) == 3 else 64)
+    sel = rng.choice(M, ns, replace=False)
+    ex = ondft.ndft(wl["k"][sel], wl["f"])
+    flat = rng.choice(int(np.prod(N)), ns, replace=False)
+    idx = np.unravel_index(flat, N)
+    nn = np.stack([idx[d] - N[d] // 2 for d in range(len(N))], axis=1).astype(float)
+    exa = np.empty(ns, complex)
+    for a in range(0, ns, 8):
+        ph = nn[a:a + 8] @ wl["k"].T
+        ph -= np.floor(ph)
+        exa[a:a + 8] = np.exp(2j * np.pi * ph) @ wl["w"]
+    acc = {"rel_l2_fwd_vs_ndft_sampled": float(np.linalg.norm(fh_np[sel] - ex) / np.linalg.norm(ex)),
+           "rel_l2_adj_vs_ndft_sampled": float(np.linalg.norm(y_np[idx] - exa) / np.linalg.norm(exa)),
+           "ndft_samples": ns}
+    fp64 = None
+    if dt == torch.complex64:
+        p64 = build(torch.complex128)
+        ref = p64.forward(torch.from_numpy(wl["f"]).cuda()).cpu().numpy()
+        p64.close()
+        acc["rel_l2_fwd_fp32_vs_fp64_form"] = float(np.linalg.norm(fh_np - ref) / np.linalg.norm(ref))
+    out = {"workload": workload_desc(wl), "steps": steps, "ms_per_step": round(step_ms, 4),
+           "nodes_per_s": M / (step_ms * 1e-3), "kernels_ms": kern, "accuracy": acc, "clocks": clocks,
+           "dtype": "f32" if dt == torch.complex64 else "f64"}
+    if cpu_oracle:
+        t0 = time.perf_counter()
+        onfft.forward(wl["k"], wl["f"], wl["sigma"], wl["m"])
+        onfft.adjoint(wl["k"], wl["w"], N, wl["sigma"], wl["m"])
+        t = time.perf_counter() - t0
+        out["cpu_oracle"] = {"value": M / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "full workload (all %d nodes), forward + adjoint" % M}
+    del fp64
+    return out
+
+
+def other_configs(steps, warmup, flush, gpu):
+    """The other workloads, measured in the same run as the headline line."""
+    import torch
+    out = {}
+    for name in ("3d_lean", "2d_c64", "2d_c128", "1d"):
+        try:
+            out[name] = measure_single(name, steps, warmup, flush, clock_gpu=gpu,
+                                       cpu_oracle=name in ("2d_c64", "2d_c128", "1d"))
+        except Exception as exc:
+            out[name] = {"unavailable": str(exc)}
+        torch.cuda.synchronize()
+    try:
+        r = measure_batched(steps, warmup, flush, clock_gpu=gpu)
+        out["batched"] = {"workload": "64 uneven 2D problems, graph replay, autotuned tile %s" % (r["tile"],),
+                          "ms_per_step": round(r["ms"], 4), "nodes_per_s": r["M"] / (r["ms"] * 1e-3),
+                          "M": r["M"], "work_items": r["info"]["n_items"], "clocks": r["clocks"]}
+    except Exception as exc:
+        out["batched"] = {"unavailable": str(exc)}
+    try:
+        r = measure_diff(steps, warmup, flush, clock_gpu=gpu)
+        out["diff"] = {"workload": "differentiation 2D 256^2, %d jittered radial nodes" % r["M"],
+                       "ms_per_step": round(r["ms"]["c64"], 4), "nodes_per_s": r["M"] / (r["ms"]["c64"] * 1e-3),
+                       "fp64_form_nodes_per_s": r["M"] / (r["ms"]["c128"] * 1e-3), "accuracy": r["accuracy"],
+                       "clocks": r["clocks"]}
+    except Exception as exc:
+        out["diff"] = {"unavailable": str(exc)}
+    return out
 
 
 def run_accuracy(args):
@@ -797,6 +1131,25 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "algorithmic_bytes": abytes}
+    # on-chip bounds of the resampling kernels (they are not HBM-bound at 3D):
+    # useful FP32 FMAs ((2m)^D complex x real products = 2 (2m)^D FMAs per node)
+    # against the FP32 peak (SMs x 128 FMA/clk), and the shared-memory floor of
+    # reading each of the (2m)^D complex64 taps once (8 B; 128 B per wavefront)
+    # against one wavefront per clock per SM; clock = the SM maximum
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    taps = (2 * wl["m"]) ** len(wl["N"])
+    fmas = 2 * taps * wl["M"]
+    wavefronts = wl["M"] * taps * (8 if dt == torch.complex64 else 16) / 128.0
+    clk_hz = 2070e6
+    onchip = {"clock_mhz": clk_hz / 1e6, "sms": sms,
+              "fp32_peak_tflops": round(2 * sms * 128 * clk_hz / 1e12, 1),
+              "shared_peak_wavefronts_per_s": sms * clk_hz}
+    for n in ("gather", "scatter"):
+        t = mean[n] * 1e-3
+        onchip[n] = {"useful_fma_tflops": round(2 * fmas / t / 1e12, 2),
+                     "fma_frac": round(fmas / t / (sms * 128 * clk_hz), 4),
+                     "shared_floor_frac": round(wavefronts / t / (sms * clk_hz), 4)}
+    roofline["onchip"] = onchip
     kernel_table = {}
     for n in names:
         ab = algorithmic_bytes(wl, n)
@@ -871,11 +1224,23 @@ def run_gpu(args):
         except Exception as exc:  # e.g. too many nonzeros for 32-bit CSR indices
             full = {"unavailable": str(exc)}
 
+    other = None
+    if rank == 0 and world == 1 and not args.no_other_configs and args.workload == "3d":
+        other = other_configs(max(3, args.other_steps), 3, flush, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, det = oracle_throughput(wl, args.cpu_sample)
-        cpu = {"value": v, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": det["sample"], "detail": det}
+        v1, det1 = oracle_throughput(wl, args.cpu_sample)
+        hc = host_cpu()
+        one = {"value": v1, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": det1["sample"], "detail": det1}
+        try:
+            va, deta = oracle_all_cores(wl)
+            cpu = {"value": va, "unit": UNIT, "cores": deta["cores"], "kind": "oracle",
+                   "sample": deta["sample"], "cpu_model": hc["model"], "nproc": hc["nproc"],
+                   "detail": deta, "one_core": one}
+        except Exception as exc:  # e.g. no shared memory for the process pool
+            cpu = dict(one, cpu_model=hc["model"], nproc=hc["nproc"], all_cores_unavailable=str(exc))
         accuracy["rel_l2_vs_ndft_48_sampled_nodes"] = ndft_sample_error(wl, fhat32)
 
     # pruned FFT: 3 + 3 line-DFT kernels; else deconv_pad and crop_deconv
@@ -915,6 +1280,7 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
+            "other_configs": other,
         }
         print(json.dumps(line))
     if world > 1:

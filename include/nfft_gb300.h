@@ -284,14 +284,15 @@ int nfft_batch_autotune(nfft_batch *b, const void *k, int k_is_fp64, int64_t *ch
  * the implicit device synchronisation of cudaMalloc / cudaFree, and services
  * whose device memory must be reserved when the library loads.
  *
- * It performs the adjoint resampling step of Algorithm 2 (complex64,
- * half-open support, 2m taps per dimension) without a plan:
+ * It spreads nodes onto the oversampled grid without a plan (complex64,
+ * half-open support, 2m taps per dimension):
  *   grid[l] = sum_j fhat_j prod_d w_d(N~_d k_{j,d} - l_d),
  * with the Kaiser-Bessel window scaled to 1 at u = 0 (the same quantity
  * nfft_step_scatter leaves in a plan's grid).  grid is N~_1 x ... x N~_D
  * complex64 in natural FFT order, N~_d = sigma N_d rounded up to even; it is
  * overwritten.  k: (M, D) FP64, fhat: M complex64; all three are device
- * pointers owned by the caller; the call is asynchronous on `stream`.
+ * pointers owned by the caller, on the current device (memory of another
+ * device is rejected); the call is asynchronous on `stream`.
  *
  * Scratch: the bin-sort buffers live in one static device array sized for
  * M <= NFFT_NOALLOC_MAX_NODES nodes and at most NFFT_NOALLOC_MAX_TILES
@@ -303,7 +304,9 @@ int nfft_batch_autotune(nfft_batch *b, const void *k, int k_is_fp64, int64_t *ch
  * contents (each call clears what must start at zero); calls that overlap on
  * the GPU race on it and must be serialised by the caller.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it, so make that first call before any stream capture. */
+ * and caches it, so make that first call before any stream capture, and do
+ * not use this call across a device reset (cudaDeviceReset), after which the
+ * cached address is stale. */
 #define NFFT_NOALLOC_MAX_NODES  262144
 #define NFFT_NOALLOC_MAX_TILES  65536
 int nfft_spread_noalloc(int D, const int64_t *N, double sigma, int m, int64_t M,

@@ -21,7 +21,10 @@
 // Host code cannot use the array's name as a device address: the first call
 // on a device looks the address up with cudaGetSymbolAddress (with that
 // device current) and caches it, so that first call should be made before
-// any stream capture begins.
+// any stream capture begins.  The cached address belongs to the device's
+// current context: after cudaDeviceReset (or anything else that destroys and
+// recreates the primary context) the array may live elsewhere, so this entry
+// point must not be used across a device reset.
 #include <math.h>
 
 #include <mutex>
@@ -73,12 +76,15 @@ int scratch_address(int device, unsigned char** out) {
   return NFFT_OK;
 }
 
-bool on_device(const void* ptr) {
+// Device memory (*dev = its device) or managed memory (*dev = -1); false for
+// host memory and for pointers CUDA does not know.
+bool on_device(const void* ptr, int* dev) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
+  *dev = attr.type == cudaMemoryTypeDevice ? attr.device : -1;
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
@@ -117,14 +123,18 @@ extern "C" int nfft_spread_noalloc(int D, const int64_t* N, double sigma, int m,
     n_tiles *= g.ntile[d];
     if (n_tiles > kMaxTiles) return NFFT_ERR_UNSUPPORTED;  // beyond the static scratch
   }
-  if (M > 0 && (!on_device(k) || !on_device(fhat))) return NFFT_ERR_INVALID_ARG;
-  if (!on_device(grid)) return NFFT_ERR_INVALID_ARG;
+  int dev_k = -1, dev_f = -1, dev_g = -1;
+  if (M > 0 && (!on_device(k, &dev_k) || !on_device(fhat, &dev_f))) return NFFT_ERR_INVALID_ARG;
+  if (!on_device(grid, &dev_g)) return NFFT_ERR_INVALID_ARG;
 
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) {
     cudaGetLastError();
     return NFFT_ERR_CUDA;
   }
+  // the kernels run on the current device: memory of another GPU is rejected
+  for (int dv : {dev_k, dev_f, dev_g})
+    if (dv >= 0 && dv != device) return NFFT_ERR_INVALID_ARG;
   unsigned char* base = nullptr;
   int st = scratch_address(device, &base);
   if (st != NFFT_OK) return st;

@@ -73,3 +73,67 @@ def tol_for(N, sigma, m, dt):
 def tol_max_for(N, sigma, m, dt):
     """Element-wise counterpart of tol_for: max(10 target, u * kappa_max)."""
     return max(10 * TOL[dt], UNIT_ROUNDOFF[dt] * kappa(N, sigma, m, norm="max"))
+
+
+def fp32_floor(N, sigma, m, k, f, w):
+    """Single-precision floor of the method: the oracle's steps (Algorithms 1
+    and 2) run with complex64 arrays, FP32 window weights (scaled to 1 at
+    u = 0, as the library stores them) and single-precision sums and FFTs,
+    compared with the FP64 oracle.  Returns the relative L2 errors (forward
+    on the nodes k, adjoint from the nodes k with inputs w).  The kernels
+    use another summation order, so their error is a small multiple of this,
+    not equal to it."""
+    import itertools
+    from oracle import nfft as onfft
+    p = onfft.Params(N, sigma, m)
+    c64, f32 = np.complex64, np.float32
+    peaks = [float(onfft.psi(0.0, m, b)) for b in p.b]
+    peak = float(np.prod(peaks))
+    ls, us = onfft.footprint(p, k)
+    wts = [(p.window(u, b) / pk).astype(f32) for u, b, pk in zip(us, p.b, peaks)]
+    taps = list(itertools.product(range(p.taps()), repeat=p.D))
+
+    def tap_index(tap):
+        return tuple(np.mod(ls[d][:, tap[d]], p.Nt[d]) for d in range(p.D))
+
+    def tap_weight(tap):
+        wt = np.ones(k.shape[0], f32)
+        for d in range(p.D):
+            wt = wt * wts[d][:, tap[d]]
+        return wt
+
+    # forward
+    exact = onfft.resample(p, k, onfft.fft_forward(onfft.correction_pad(p, f)))
+    gh = np.fft.fftn((onfft.correction_pad(p, f) * peak).astype(c64))
+    assert gh.dtype == c64, "numpy FFT must run in single precision for this model"
+    out = np.zeros(k.shape[0], c64)
+    for tap in taps:
+        out += gh[tap_index(tap)] * tap_weight(tap)
+    e_f = rel_l2(out.astype(np.complex128), exact)
+    # adjoint
+    exact_a = onfft.crop_correction(p, onfft.fft_adjoint(onfft.resample_adjoint(p, k, w)))
+    acc = np.zeros(int(np.prod(p.Nt)), c64)
+    w32 = np.asarray(w).astype(c64)
+    for tap in taps:
+        np.add.at(acc, np.ravel_multi_index(tap_index(tap), p.Nt), w32 * tap_weight(tap))
+    g = np.fft.ifftn(acc.reshape(p.Nt), norm="forward")
+    y = onfft.crop_correction(p, g.astype(np.complex128)).astype(c64) * f32(peak)
+    return e_f, rel_l2(y.astype(np.complex128), exact_a)
+
+
+def oracle_spread_box(N, sigma, m, k, w, lo, size):
+    """The oracle's adjoint resampling step (Algorithm 2, Eq. SumOverNodeAdjoint)
+    on the grid box [lo_d, lo_d + size) (periodic): only the nodes whose
+    footprint meets the box contribute there, so the oracle runs on those
+    alone.  Returns the box (size^D complex) and its index arrays."""
+    from oracle import nfft as onfft
+    p = onfft.Params(N, sigma, m)
+    sel = np.ones(k.shape[0], bool)
+    for d in range(p.D):
+        c = np.mod(np.floor(p.Nt[d] * k[:, d]).astype(np.int64), p.Nt[d])
+        d0 = np.mod(c - m + 1 - lo[d], p.Nt[d])    # footprint = d0 .. d0 + 2m - 1 (mod N~) from lo
+        sel &= (d0 < size) | (d0 + 2 * m - 1 >= p.Nt[d])
+    g = onfft.resample_adjoint(p, k[sel], w[sel])
+    idx = np.ix_(*[np.mod(np.arange(lo[d], lo[d] + size), p.Nt[d]) for d in range(p.D)])
+    return g[idx], idx, int(sel.sum())
+

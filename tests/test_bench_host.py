@@ -90,3 +90,22 @@ def test_reference_estimate_counts_the_fixed_part_once():
     assert abs(est - (1.0 + 0.1 + 1e-4 * 2000000)) < 1e-6
     # a step faster than the calibrated fixed part contributes no negative time
     assert bench.reference_estimate(1.0, 0.1, 0.05, 1000, 2000000) == 1.1
+
+
+def test_split_problems_covers_each_problem_once_and_balances():
+    import bench
+    from paper_2208_00049_gb300 import inputs
+    w = bench.batch_weights(inputs.batched_problems(n_problems=64))
+    for world in (1, 2, 3, 4, 8):
+        parts = [bench.split_problems(w, world, r) for r in range(world)]
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(64))
+        loads = [sum(w[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(w)   # within one problem of each other
+        assert all(p == sorted(p) for p in parts)
+
+
+def test_split_aggregation_single_process():
+    import bench
+    agg = bench.aggregate_split(40.0, 1000, 4)
+    assert agg["world"] == 1 and agg["ms_per_step"] == 10.0 and agg["value"] == 1000 / 0.010

@@ -135,3 +135,40 @@ def test_batch_matches_single_plans_fp64():
         assert_close(fh[i], onfft.forward(p["k"], p["f"], 2.0, 4), 1e-12, "forward %d" % i)
         assert_close(y[i].reshape(p["N"]), onfft.adjoint(p["k"], p["w"], p["N"], 2.0, 4), 1e-12, "adjoint %d" % i)
     b.close()
+
+
+def test_rank_split_sub_batches_match_full_batch():
+    """The batched workload split over 2 ranks (bench.py's split, emulated
+    one rank after the other on this GPU): each rank's sub-batch gives, for
+    its problems, the full batch's outputs."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_2208_00049_gb300.nfft import Batch
+    probs = inputs.batched_problems(n_problems=64)
+
+    def run(idx):
+        ps = [probs[i] for i in idx]
+        Ms = [p["M"] for p in ps]
+        b = Batch([p["N"] for p in ps], list(range(len(ps))), Ms, sigma=2.0, m=4, dtype=torch.complex64)
+        b.set_tile((9, 25))
+        b.set_nodes(torch.from_numpy(np.concatenate([p["k"] for p in ps])).cuda())
+        fh = _split(b.forward(_flat([p["f"] for p in ps], torch.complex64)).cpu().numpy(), Ms)
+        y = _split(b.adjoint(_flat([p["w"] for p in ps], torch.complex64)).cpu().numpy(),
+                   [int(np.prod(p["N"])) for p in ps])
+        b.close()
+        return dict(zip(idx, zip(fh, y)))
+
+    full = run(list(range(64)))
+    w = bench.batch_weights(probs)
+    seen = set()
+    for rank in range(2):
+        mine = bench.split_problems(w, 2, rank)
+        part = run(mine)
+        for i in mine:
+            assert i not in seen
+            seen.add(i)
+            assert_close(part[i][0], full[i][0], 1e-6, "forward %d" % i)
+            assert_close(part[i][1], full[i][1], 1e-6, "adjoint %d" % i)
+    assert seen == set(range(64))

@@ -13,7 +13,8 @@ from oracle import ndft as ondft
 from oracle import nfft as onfft
 from paper_2208_00049_gb300 import inputs
 
-from gpu_helpers import TOL, assert_close, cdtype, rel_l2, require_gpu, to_dev, tol_for, tol_max_for
+from gpu_helpers import (TOL, assert_close, cdtype, fp32_floor, oracle_spread_box, rel_l2, require_gpu, to_dev,
+                         tol_for, tol_max_for)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -63,9 +64,8 @@ def test_small_cases_match_oracle(N, M, sigma, m, dt):
     fh, y = _run(case, dt)
     want_f = onfft.forward(case["k"], case["f"], sigma, m)
     want_a = onfft.adjoint(case["k"], case["w"], N, sigma, m)
-    scale = 10 if (dt == "c128" and m <= 3) else 1
-    tol = tol_for(N, sigma, m, dt) * scale
-    tmax = tol_max_for(N, sigma, m, dt) * scale
+    tol = tol_for(N, sigma, m, dt)
+    tmax = tol_max_for(N, sigma, m, dt)
     assert_close(fh, want_f, tol, "forward", tol_max=tmax)
     assert_close(y, want_a, tol, "adjoint", tol_max=tmax)
 
@@ -123,10 +123,20 @@ def test_workload3_3d_full_size_sampled(name):
     and the adjoint identity over all nodes."""
     wl = inputs.workload(name)
     sigma, m = wl["sigma"], wl["m"]
-    tol = tol_for(wl["N"], sigma, m, "c64")
-    fh, y = _run(wl, "c64")
     rng = np.random.default_rng(6)
     sel = rng.choice(wl["M"], 4096, replace=False)
+    tol = tol_a = tol_for(wl["N"], sigma, m, "c64")
+    if tol > TOL["c64"]:
+        # sigma = 1.25: the deconvolution amplifies single-precision rounding
+        # (kappa ~ 1.7e5).  Forward: 3x the error of the oracle's own steps run
+        # in single precision on the same nodes (the kernels measured at about
+        # 2x of it).  The adjoint's floor depends on how many terms each grid
+        # point sums (all M nodes), which the oracle cannot afford at this size:
+        # its end-to-end bound stays u kappa here, and its steps are checked
+        # one by one, tightly, in test_workload3_adjoint_steps.
+        e_f, _ = fp32_floor(wl["N"], sigma, m, wl["k"][sel], wl["f"], wl["w"][sel])
+        tol = max(TOL["c64"], 3 * e_f)
+    fh, y = _run(wl, "c64")
     want = onfft.forward(wl["k"][sel], wl["f"], sigma, m)
     assert_close(fh[sel], want, tol, "forward (sampled) vs oracle")
     # exact NDFT on 64 of them
@@ -140,11 +150,55 @@ def test_workload3_3d_full_size_sampled(name):
         ph = n[s:s + 8] @ wl["k"].T
         ph -= np.floor(ph)
         exa[s:s + 8] = np.exp(2j * np.pi * ph) @ wl["w"]
-    assert rel_l2(y[idx], exa) <= tol
+    assert rel_l2(y[idx], exa) <= tol_a
     lhs = np.vdot(wl["w"], fh)
     rhs = np.vdot(y, wl["f"])
     # relative to the Cauchy-Schwarz scale (random vectors make <w, Af> itself small)
-    assert abs(lhs - rhs) <= tol * np.linalg.norm(wl["w"]) * np.linalg.norm(fh)
+    assert abs(lhs - rhs) <= max(tol, tol_a) * np.linalg.norm(wl["w"]) * np.linalg.norm(fh)
+
+
+@pytest.mark.parametrize("name", ["3d", "3d_lean"])
+def test_workload3_adjoint_steps(name):
+    """The full-size 3D adjoint in the bench's launch configuration, step by
+    step: the adjoint resampling step element by element on two 16^3 boxes of
+    the oversampled grid (one inside, one across the periodic corner; 8192
+    grid values against the oracle's step run on the nodes that reach each
+    box), then the inverse FFT + crop + correction steps on every output
+    against the oracle's FP64 steps applied to the GPU's own grid, within 3x
+    the error of numpy's single-precision inverse FFT on that grid."""
+    from paper_2208_00049_gb300.nfft import Plan
+    wl = inputs.workload(name)
+    N, sigma, m = wl["N"], wl["sigma"], wl["m"]
+    plan = Plan(N, wl["M"], sigma=sigma, m=m, dtype=torch.complex64)
+    plan.set_nodes(to_dev(wl["k"], torch.float64))
+    plan.step_scatter(to_dev(wl["w"], torch.complex64))
+    pruned = plan.paths()["pruned_fft"]
+    grid_t = plan.grid_tensor().clone()
+    grid = grid_t.cpu().numpy()
+    y = torch.empty(N, dtype=torch.complex64, device="cuda")
+    plan.step_fft_crop(y)
+    y = y.cpu().numpy()
+    plan.close()
+    p = onfft.Params(N, sigma, m)
+    peak = np.prod([float(onfft.psi(0.0, m, b)) for b in p.b])
+    w32 = wl["w"].astype(np.complex64).astype(np.complex128)
+    for lo in ((37, 101, 90), tuple(nt - 8 for nt in p.Nt)):
+        want, idx, n = oracle_spread_box(N, sigma, m, wl["k"], w32, lo, 16)
+        assert n > 1000
+        assert_close(grid[idx] * peak, want, TOL["c64"], "scatter grid box at %s" % (lo,))
+    want_y = onfft.crop_correction(p, onfft.fft_adjoint(grid.astype(np.complex128))) * peak
+    if pruned:
+        # the library's own FFT: within 3x numpy's single-precision inverse FFT
+        g32 = np.fft.ifftn(grid, norm="forward")
+        assert g32.dtype == np.complex64
+    else:
+        # the library form runs cuFFT in single precision, whose error at the
+        # band edges (amplified by the correction at sigma = 1.25) is far above
+        # numpy's: the floor is cuFFT's own inverse FFT of the same grid, and
+        # the crop and correction may add little to it
+        g32 = torch.fft.ifftn(grid_t, norm="forward").cpu().numpy()
+    floor = rel_l2(onfft.crop_correction(p, g32.astype(np.complex128)) * peak, want_y)
+    assert_close(y, want_y, max(TOL["c64"], (3 if pruned else 1.5) * floor), "inverse FFT + crop + correction")
 
 
 def test_radial_set_on_grid_nodes():
@@ -399,9 +453,14 @@ def test_fast_m6_tile_shapes(sigma, tile):
     fh = plan.forward(to_dev(case["f"], torch.complex64)).cpu().numpy()
     y = plan.adjoint(to_dev(case["w"], torch.complex64)).cpu().numpy()
     plan.close()
-    tol, tmax = tol_for(N, sigma, 6, "c64"), tol_max_for(N, sigma, 6, "c64")
+    tol = tol_a = TOL["c64"]
+    tmax = tol_max_for(N, sigma, 6, "c64")
+    if sigma < 2.0:
+        # 3x the error of the oracle's own steps run in single precision
+        e_f, e_a = fp32_floor(N, sigma, 6, case["k"], case["f"], case["w"])
+        tol, tol_a = max(tol, 3 * e_f), max(tol, 3 * e_a)
     assert_close(fh, onfft.forward(case["k"], case["f"], sigma, 6), tol, "forward", tmax)
-    assert_close(y, onfft.adjoint(case["k"], case["w"], N, sigma, 6), tol, "adjoint", tmax)
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, sigma, 6), tol_a, "adjoint", tmax)
 
 
 def test_fast_m6_hot_tile():
@@ -459,7 +518,7 @@ def test_full_matrix_form_matches_oracle(N, M, m, dt):
     from paper_2208_00049_gb300 import binding as B
     case = inputs.small_case(N, M, seed=67, m=m)
     fh, y = _run(case, dt, flags=B.NFFT_FLAG_FULL_MATRIX)
-    tol = TOL[dt] * (10 if dt == "c128" and m <= 3 else 1)
+    tol = TOL[dt]
     assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, m), tol, "forward")
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, m), tol, "adjoint")
 
@@ -471,7 +530,7 @@ def test_wide_window_matches_oracle(N, M, m, dt):
     from paper_2208_00049_gb300 import binding as B
     case = inputs.small_case(N, M, seed=71, m=m)
     fh, y = _run(case, dt, flags=B.NFFT_FLAG_WIDE_WINDOW)
-    tol = TOL[dt] * (10 if dt == "c128" and m <= 3 else 1)
+    tol = TOL[dt]
     assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, m, wide=True), tol, "forward")
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, m, wide=True), tol, "adjoint")
 

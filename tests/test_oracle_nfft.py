@@ -44,7 +44,9 @@ def _dense_operator(p, k):
     for r, l in enumerate(It):
         for c, n in enumerate(It):
             Fm[r, c] = np.exp(-2j * np.pi * sum(n[d] * l[d] / p.Nt[d] for d in range(p.D)))
-    # B: periodised truncated window psi~(k_j - l/N~) = sum_p psi(N~ (k - l/N~ + p))
+    # B: periodised truncated window psi~(k_j - l/N~) = sum_p psi(N~ (k - l/N~ + p));
+    # the (2m+2)-point variant takes the untruncated window on the grid points
+    # with -(m+1) <= N~ k - l' < m + 1 (the 2m + 2 nearest, Sec. 3.7.5)
     Bm = np.zeros((k.shape[0], size_t))
     for j in range(k.shape[0]):
         for c, l in enumerate(It):
@@ -52,19 +54,27 @@ def _dense_operator(p, k):
             for d in range(p.D):
                 acc = 0.0
                 for per in (-1, 0, 1):
-                    u = p.Nt[d] * (k[j, d] - l[d] / p.Nt[d] + per)
-                    acc += float(window.psi(u, p.m, p.b[d], p.closed))
+                    # u = N~ k - l + p N~, the form of the set definition (exact
+                    # when N~ k is an integer, i.e. for on-grid nodes)
+                    u = p.Nt[d] * k[j, d] - l[d] + per * p.Nt[d]
+                    if p.wide:
+                        if -(p.m + 1) <= u < p.m + 1:
+                            acc += float(window.psi_full(u, p.m, p.b[d]))
+                    else:
+                        acc += float(window.psi(u, p.m, p.b[d], p.closed))
                 val *= acc
             Bm[j, c] = val
     return Bm, Fm, Dm
 
 
-@pytest.mark.parametrize("N,m,closed", [((6,), 2, False), ((4, 5), 1, False), ((6, 4), 2, True)])
-def test_operator_against_dense_definition(N, m, closed):
+@pytest.mark.parametrize("N,m,closed,wide", [((6,), 2, False, False), ((4, 5), 1, False, False),
+                                             ((6, 4), 2, True, False), ((6,), 2, False, True),
+                                             ((5, 6), 1, False, True), ((7,), 3, False, True)])
+def test_operator_against_dense_definition(N, m, closed, wide):
     rng = np.random.default_rng(10)
-    p = nfft.Params(N, 2.0, m, closed)
+    p = nfft.Params(N, 2.0, m, closed, wide)
     k = rng.random((5, len(N))) - 0.5
-    if closed:
+    if closed or wide:
         k[0] = [int(np.floor(0.3 * nt)) / nt for nt in p.Nt]   # an on-grid node
     Bm, Fm, Dm = _dense_operator(p, k)
     f = _cn(rng, N)
@@ -72,10 +82,10 @@ def test_operator_against_dense_definition(N, m, closed):
     In = list(itertools.product(*[range(n) for n in N]))
     fv = np.array([f[i] for i in In])
     want = Bm @ (Fm @ (Dm @ fv))
-    got = nfft.forward(k, f, 2.0, m, closed)
+    got = nfft.forward(k, f, 2.0, m, closed, wide)
     assert np.allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
     want_a = Dm.T @ (Fm.conj().T @ (Bm.T @ w))
-    got_a = nfft.adjoint(k, w, N, 2.0, m, closed)
+    got_a = nfft.adjoint(k, w, N, 2.0, m, closed, wide)
     got_av = np.array([got_a[i] for i in In])
     assert np.allclose(got_av, want_a, rtol=0, atol=1e-12 * np.abs(want_a).max())
 

@@ -153,3 +153,24 @@ def test_dpsi_full_by_finite_differences():
     fd = (window.psi_full(u + h, m, b) - window.psi_full(u - h, m, b)) / (2 * h)
     an = window.dpsi_full(u, m, b)
     assert np.max(np.abs(fd - an)) < 1e-6 * np.max(np.abs(window.psi_full(np.linspace(-m, m, 9), m, b)))
+
+
+@pytest.mark.parametrize("m,sigma", [(2, 2.0), (4, 2.0), (6, 1.25), (8, 2.0)])
+def test_untruncated_window_is_one_entire_function(m, sigma):
+    """psi_full continues sinh(b s)/(pi s) past |u| = m.  Since
+    sinh(b s)/s = sum_k b^(2k+1) (s^2)^k/(2k+1)! is a power series in
+    s^2 = m^2 - u^2 alone, that one series must give psi_full on both sides of
+    the edge (no inside/outside branch): a wrong continuation beyond the
+    support, or a wrong branch choice, fails here."""
+    b = window.kb_shape(64, window.oversampled_size(64, sigma))
+    u = np.concatenate([np.linspace(-m - 1.5, -m + 1.5, 61), np.linspace(m - 1.5, m + 1.5, 61)])
+    s2 = m * m - u * u
+    series = np.zeros_like(u)
+    term = np.full_like(u, b)           # b^(2k+1) (s^2)^k / (2k+1)!, k = 0
+    for kk in range(60):
+        series += term
+        term = term * b * b * s2 / ((2 * kk + 2) * (2 * kk + 3))
+    want = series / np.pi
+    got = window.psi_full(u, m, b)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
