@@ -810,6 +810,42 @@ def run_diff(args):
     print(json.dumps(line))
 
 
+def api_timing(plan, f, w, fh, y, steps, flush, stream):
+    """One forward + one adjoint through the public calls (nfft_forward,
+    nfft_adjoint) on device buffers, from an idle GPU (synchronised before
+    each pair), so that the time includes the host's launch latency: direct
+    launches against one graph replay per call (nfft_plan_set_graph), and
+    the relative L2 difference of the two modes' results."""
+    import torch
+    out = {}
+    res = {}
+    for mode in ("direct", "graph"):
+        plan.set_graph(mode == "graph")
+        for _ in range(3):
+            plan.forward(f, out=fh)
+            plan.adjoint(w, out=y)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.forward(f, out=fh)
+            plan.adjoint(w, out=y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out[mode + "_ms"] = round(statistics.median(ms), 4)
+        res[mode] = (fh.clone(), y.clone())
+    plan.set_graph(False)
+    # atomics make the adjoint's summation order vary between runs
+    out["graph_vs_direct_rel_l2"] = max(
+        float((res["graph"][i] - res["direct"][i]).abs().pow(2).sum().sqrt()
+              / res["direct"][i].abs().pow(2).sum().sqrt()) for i in range(2))
+    return out
+
+
 def measure_single(name, steps, warmup, flush, clock_gpu=None, cpu_oracle=False):
     """One single-problem workload through the step ABI (correction + pad +
     FFT, gather, scatter, inverse FFT + crop + correction), like the default
@@ -873,6 +909,7 @@ def measure_single(name, steps, warmup, flush, clock_gpu=None, cpu_oracle=False)
     step_ms = statistics.mean(e[0].elapsed_time(e[-1]) for e in evs)
     kern = {n: round(statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs), 4) for j, n in enumerate(names)}
     fh_np, y_np = fh.cpu().numpy().astype(np.complex128), y.cpu().numpy().astype(np.complex128)
+    api = api_timing(plan, f_d, w_d, fh, y, steps, flush, stream)
     plan.close()
     # accuracy: exact NDFT on sampled nodes and outputs
     rng = np.random.default_rng(11)
@@ -898,7 +935,7 @@ def measure_single(name, steps, warmup, flush, clock_gpu=None, cpu_oracle=False)
         acc["rel_l2_fwd_fp32_vs_fp64_form"] = float(np.linalg.norm(fh_np - ref) / np.linalg.norm(ref))
     out = {"workload": workload_desc(wl), "steps": steps, "ms_per_step": round(step_ms, 4),
            "nodes_per_s": M / (step_ms * 1e-3), "kernels_ms": kern, "accuracy": acc, "clocks": clocks,
-           "dtype": "f32" if dt == torch.complex64 else "f64"}
+           "dtype": "f32" if dt == torch.complex64 else "f64", "api_forward_adjoint": api}
     if cpu_oracle:
         t0 = time.perf_counter()
         onfft.forward(wl["k"], wl["f"], wl["sigma"], wl["m"])
@@ -907,6 +944,75 @@ def measure_single(name, steps, warmup, flush, clock_gpu=None, cpu_oracle=False)
         out["cpu_oracle"] = {"value": M / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "full workload (all %d nodes), forward + adjoint" % M}
     del fp64
+    return out
+
+
+def compensated_form(name, steps, warmup, flush):
+    """NFFT_FLAG_COMPENSATED beside the plain form on one workload: the
+    scatter step's time (L2 flushed) and the spread grid's relative L2
+    distance to the complex128 plan's grid (FP64 sums of the same terms)."""
+    import numpy as np
+    import torch
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300 import inputs
+    from paper_2208_00049_gb300.nfft import Plan
+    wl = inputs.workload(name)
+    stream = torch.cuda.current_stream()
+    k = torch.from_numpy(wl["k"]).cuda()
+    w32 = torch.from_numpy(wl["w"]).to(torch.complex64).cuda()
+    ref = Plan(wl["N"], wl["M"], sigma=wl["sigma"], m=wl["m"], dtype=torch.complex128)
+    ref.set_nodes(k)
+    ref.step_scatter(w32.to(torch.complex128))
+    g64 = ref.grid_tensor().cpu().numpy()
+    ref.close()
+    out = {"workload": workload_desc(wl)}
+    for label, flags in (("plain", 0), ("compensated", B.NFFT_FLAG_COMPENSATED)):
+        plan = Plan(wl["N"], wl["M"], sigma=wl["sigma"], m=wl["m"], dtype=torch.complex64, flags=flags)
+        plan.set_nodes(k)
+        h = plan.handle
+        ms = time_steps(lambda: B.check(B.nfft_step_scatter(h, w32.data_ptr())), steps, warmup, stream, flush)
+        g = plan.grid_tensor().cpu().numpy().astype(np.complex128)
+        out[label] = {"scatter_ms": round(ms, 4), "fast_kernel": plan.paths()["fast_scatter"],
+                      "grid_rel_l2_vs_fp64_sums": float(np.linalg.norm(g - g64) / np.linalg.norm(g64))}
+        plan.close()
+    return out
+
+
+def window_modes_form(wl, steps, warmup, flush, ref64=None):
+    """The window modes of Sec. 3.7.4 on one workload: DIRECT, LINEAR and
+    POLYNOMIAL on the same (generic) kernels (plan flags), beside the default
+    plan's specialised kernels (POLYNOMIAL): gather and scatter step times
+    and the forward's relative L2 distance to the FP64 form (if given)."""
+    import numpy as np
+    import torch
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300.nfft import Plan
+    dt = torch.complex64 if wl["dtype"] == "c64" else torch.complex128
+    stream = torch.cuda.current_stream()
+    k = torch.from_numpy(wl["k"]).cuda()
+    f = torch.from_numpy(wl["f"]).to(dt).cuda()
+    w = torch.from_numpy(wl["w"]).to(dt).cuda()
+    fh = torch.empty(wl["M"], dtype=dt, device="cuda")
+    out = {"workload": workload_desc(wl)}
+    modes = (("default (specialised kernels, POLYNOMIAL)", 0), ("DIRECT", B.NFFT_FLAG_WINDOW_DIRECT),
+             ("LINEAR", B.NFFT_FLAG_WINDOW_LINEAR), ("POLYNOMIAL", B.NFFT_FLAG_WINDOW_POLYNOMIAL))
+    for name, flag in modes:
+        try:
+            plan = Plan(wl["N"], wl["M"], sigma=wl["sigma"], m=wl["m"], dtype=dt, flags=flag)
+        except Exception as exc:
+            out[name] = {"unavailable": str(exc)}
+            continue
+        plan.set_nodes(k)
+        h = plan.handle
+        B.check(B.nfft_step_pad_fft(h, f.data_ptr()))
+        tg = time_steps(lambda: B.check(B.nfft_step_gather(h, fh.data_ptr())), steps, warmup, stream, flush)
+        res = fh.cpu().numpy().astype(np.complex128)
+        ts = time_steps(lambda: B.check(B.nfft_step_scatter(h, w.data_ptr())), steps, warmup, stream, flush)
+        entry = {"gather_ms": round(tg, 4), "scatter_ms": round(ts, 4), "paths": plan.paths()}
+        if ref64 is not None:
+            entry["rel_l2_fwd_vs_fp64_form"] = float(np.linalg.norm(res - ref64) / np.linalg.norm(ref64))
+        out[name] = entry
+        plan.close()
     return out
 
 
@@ -921,6 +1027,10 @@ def other_configs(steps, warmup, flush, gpu):
         except Exception as exc:
             out[name] = {"unavailable": str(exc)}
         torch.cuda.synchronize()
+    try:
+        out["2d_c64"]["compensated_form"] = compensated_form("2d_c64", steps, 2, flush)
+    except Exception as exc:
+        out["2d_c64"]["compensated_form"] = {"unavailable": str(exc)}
     try:
         r = measure_batched(steps, warmup, flush, clock_gpu=gpu)
         out["batched"] = {"workload": "64 uneven 2D problems, graph replay, autotuned tile %s" % (r["tile"],),
@@ -942,8 +1052,10 @@ def other_configs(steps, warmup, flush, gpu):
 def run_accuracy(args):
     """Figs. 1-2 analogue on the GPU: relative errors (L2 and the paper's
     infinity norm) of the direct and adjoint NFFT against the exact NDFT for
-    m = 2..8, 2D N = 128^2 with M = |I_N| random nodes, sigma = 2, complex64
-    and complex128, 2m points and the (2m+2)-point variant."""
+    m = 2..10, 2D N = 128^2 with M = |I_N| random nodes, sigma = 2, complex64
+    and complex128: 2m points (default kernels, and the DIRECT, LINEAR and
+    POLYNOMIAL window modes on the generic kernels) and the (2m+2)-point
+    variant (m <= 8)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -963,16 +1075,19 @@ def run_accuracy(args):
     ph -= np.floor(ph)
     exa = np.exp(2j * np.pi * ph) @ case["w"]
     rows = []
+    variants = [("2m", 0), ("2m+2", B.NFFT_FLAG_WIDE_WINDOW), ("2m LINEAR", B.NFFT_FLAG_WINDOW_LINEAR),
+                ("2m POLYNOMIAL", B.NFFT_FLAG_WINDOW_POLYNOMIAL), ("2m DIRECT", B.NFFT_FLAG_WINDOW_DIRECT)]
     for dt, name in ((torch.complex64, "c64"), (torch.complex128, "c128")):
-        for wide in (False, True):
-            for m in range(2, 9):
-                flags = B.NFFT_FLAG_WIDE_WINDOW if wide else 0
+        for taps, flags in variants:
+            for m in range(2, 11):
+                if m > 8 and flags == B.NFFT_FLAG_WIDE_WINDOW:
+                    continue  # K = 2m + 2 > 18: not built
                 plan = Plan(N, case["M"], sigma=2.0, m=m, dtype=dt, flags=flags)
                 plan.set_nodes(torch.from_numpy(case["k"]).cuda())
                 fh = plan.forward(torch.from_numpy(case["f"]).to(dt).cuda()).cpu().numpy()[sel]
                 y = plan.adjoint(torch.from_numpy(case["w"]).to(dt).cuda()).cpu().numpy()[idx]
                 plan.close()
-                rows.append({"dtype": name, "taps": "2m+2" if wide else "2m", "m": m,
+                rows.append({"dtype": name, "taps": taps, "m": m,
                              "fwd_l2": float(np.linalg.norm(fh - ex) / np.linalg.norm(ex)),
                              "fwd_inf": float(np.max(np.abs(fh - ex)) / np.max(np.abs(ex))),
                              "adj_l2": float(np.linalg.norm(y - exa) / np.linalg.norm(exa)),
@@ -1213,10 +1328,17 @@ def run_gpu(args):
     # FP64 form on the same workload, and the FP32 result's accuracy
     fhat32 = fhat_d.cpu().numpy()
     fp64 = None
+    ref64 = None
     accuracy = {}
     if rank == 0 and not args.no_fp64_form and dt == torch.complex64:
         fp64, ref64, err = fp64_form(wl, fhat32, min(10, max(3, args.steps // 4)), 2, flush)
         accuracy["rel_l2_fp32_vs_fp64_form"] = err
+    wmodes = None
+    if rank == 0 and world == 1 and not args.no_other_configs:
+        try:
+            wmodes = window_modes_form(wl, min(5, max(3, args.steps // 4)), 1, flush, ref64)
+        except Exception as exc:
+            wmodes = {"unavailable": str(exc)}
     full = None
     if rank == 0 and not args.no_full_form:
         try:
@@ -1224,6 +1346,12 @@ def run_gpu(args):
         except Exception as exc:  # e.g. too many nonzeros for 32-bit CSR indices
             full = {"unavailable": str(exc)}
 
+    comp = None
+    if rank == 0 and world == 1 and dt == torch.complex64 and not args.no_other_configs:
+        try:
+            comp = compensated_form(args.workload, min(10, max(3, args.steps // 4)), 2, flush)
+        except Exception as exc:
+            comp = {"unavailable": str(exc)}
     other = None
     if rank == 0 and world == 1 and not args.no_other_configs and args.workload == "3d":
         other = other_configs(max(3, args.other_steps), 3, flush, local)
@@ -1280,6 +1408,8 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
+            "compensated_form": comp,
+            "window_modes": wmodes,
             "other_configs": other,
         }
         print(json.dumps(line))

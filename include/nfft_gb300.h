@@ -60,8 +60,10 @@ extern "C" {
 /* Support [-m, m] instead of [-m, m): nodes exactly on a grid line get the
    extra tap at u = +m, i.e. the (2m+1)^D footprint discussed in Sec. 3.7.5. */
 #define NFFT_FLAG_CLOSED_SUPPORT  0x1u
-/* FP32 scatter: each shared-memory tile sum also accumulates the rounding
-   error of every addition (TwoSum) and adds it back at the flush. */
+/* FP32 scatter with compensated summation: every accumulator (a register of
+   the 2D and 3D complex64 kernels, a shared-memory tile element of the
+   generic kernels) also accumulates the rounding error of each addition
+   (TwoSum) and adds it back at the flush. */
 #define NFFT_FLAG_COMPENSATED     0x2u
 /* FULL precomputation (Sec. 3.7.4 item 2; the paper's GPU prototype of
    Sec. 6): nfft_set_nodes also builds the sparse matrix B of Eq. Bmatrix
@@ -81,6 +83,28 @@ extern "C" {
    qualifies for the pruned FFT (see nfft_step_pad_fft). */
 #define NFFT_FLAG_LIBRARY_FFT     0x10u
 
+/* Window values (Sec. 3.7.4).  Without these flags complex64 plans use the
+   specialised 1D-3D kernels, which take the window from its POLYNOMIAL
+   representation, and every other plan the generic kernels, which evaluate
+   it.  Each flag below selects the generic kernels (any D, m, dtype) with one
+   way of obtaining the window values, so that the three can be compared on
+   the same kernels; at most one may be given:
+     DIRECT      the window evaluated per tap (sinh, sqrt);
+     LINEAR      the lookup table psi_s = psi_Base(s/(S-2)), s < S,
+                 S = m 2^{c_min(m,8)} + 2 with NFFT3's c = (3, 7, 9, 14, 17,
+                 20, 23, 24), read with linear interpolation (Eq. linInterp);
+                 built in FP64 at plan creation, one table per dimension in
+                 the plan's real type (m = 8: 1.3e8 entries per dimension);
+                 not with NFFT_FLAG_WIDE_WINDOW; NFFT_ERR_UNSUPPORTED beyond
+                 8 GB of tables;
+     POLYNOMIAL  per-tap polynomials of degree 2m (Chebyshev interpolation
+                 in FP64) evaluated by Horner; not with
+                 NFFT_FLAG_CLOSED_SUPPORT or NFFT_FLAG_WIDE_WINDOW.
+   None of them with NFFT_FLAG_FULL_MATRIX. */
+#define NFFT_FLAG_WINDOW_DIRECT     0x20u
+#define NFFT_FLAG_WINDOW_LINEAR     0x40u
+#define NFFT_FLAG_WINDOW_POLYNOMIAL 0x80u
+
 typedef struct nfft_plan nfft_plan;
 
 /* ---- plan ------------------------------------------------------------- */
@@ -92,7 +116,8 @@ typedef struct nfft_plan nfft_plan;
  *   N      : N[0..D-1], each >= 2 (even or odd).
  *   M      : number of nodes, >= 0 (0 gives empty transforms).
  *   sigma  : oversampling factor > 1; N~_d = sigma N_d rounded up to even.
- *   m      : window half-width, 1..8, with 2m < N~_d.
+ *   m      : window half-width, 1..10 (1..8 for D = 3: NFFT_ERR_UNSUPPORTED
+ *            beyond), with 2m < N~_d.
  *   dtype  : NFFT_C64 or NFFT_C128.
  *   flags  : NFFT_FLAG_* bits.
  *   stream : cudaStream_t on which every later call enqueues its work
@@ -216,6 +241,15 @@ int nfft_step_pad_fft(nfft_plan *p, const void *f);
  * grid is used as scratch and does not hold the full inverse FFT
  * afterwards); otherwise nfft_step_fft(+1) + nfft_step_crop_deconv. */
 int nfft_step_fft_crop(nfft_plan *p, void *y);
+
+/* Graph mode for small transforms, whose time is mostly kernel launches:
+ * with enable != 0, nfft_forward and nfft_adjoint called with device
+ * buffers are captured into a CUDA graph (on an internal stream) the first
+ * time a pair of buffers is seen and replayed on the plan's stream with one
+ * launch afterwards; new buffers re-capture, and nfft_plan_set_tile drops the
+ * graphs (nfft_set_nodes keeps them: the node buffers stay in place).  Host
+ * buffers take the direct path.  enable = 0 drops the graphs. */
+int nfft_plan_set_graph(nfft_plan *p, int enable);
 
 /* Which kernels the plan's transforms use (set by nfft_plan_create and
  * nfft_plan_set_tile): *fast_resample bit 0 = the 3D m = 4 complex64

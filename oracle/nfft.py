@@ -28,7 +28,9 @@ the set definition by brute force.  With ``closed=True`` the support is
 [-m, m] and the footprint has 2m + 1 points l' = floor(N~k) - m + i,
 i = 0, ..., 2m (the (2m+1)^D variant).  With ``wide=True`` the footprint has
 2m + 2 points l' = floor(N~k) - m + i, i = 0, ..., 2m + 1, weighted with the
-untruncated window (the NFFT3 variant of Sec. 3.7.5).
+untruncated window (the NFFT3 variant of Sec. 3.7.5).  With
+``window="linear"`` the window values come from the LINEAR table of Sec. 3.7.4
+(lookup with linear interpolation) instead of being evaluated.
 
 N~ k is formed in FP64 and its floor taken in FP64.
 """
@@ -36,14 +38,14 @@ import itertools
 
 import numpy as np
 
-from .window import (deconv_factor, dpsi, dpsi_full, index_set, kb_shape,
-                     oversampled_size, psi, psi_full)
+from .window import (deconv_factor, dpsi, dpsi_full, dpsi_linear, index_set, kb_shape,
+                     oversampled_size, psi, psi_full, psi_linear)
 
 
 class Params:
     """Sizes and window shape of one transform (plan-time quantities)."""
 
-    def __init__(self, N, sigma=2.0, m=4, closed=False, wide=False):
+    def __init__(self, N, sigma=2.0, m=4, closed=False, wide=False, window="direct"):
         self.N = tuple(int(v) for v in N)
         self.D = len(self.N)
         self.sigma = float(sigma)
@@ -52,6 +54,12 @@ class Params:
         self.wide = bool(wide)
         if self.closed and self.wide:
             raise ValueError("closed and wide are exclusive")
+        # "direct": the window evaluated; "linear": looked up in the LINEAR
+        # table with linear interpolation (Sec. 3.7.4; needs |u| <= m, so not
+        # with the (2m+2)-point footprint)
+        if window not in ("direct", "linear") or (window == "linear" and self.wide):
+            raise ValueError("window must be 'direct' or 'linear' (not with wide)")
+        self.window_mode = window
         self.Nt = tuple(oversampled_size(n, sigma) for n in self.N)
         self.b = tuple(kb_shape(n, nt) for n, nt in zip(self.N, self.Nt))
         for n, nt in zip(self.N, self.Nt):
@@ -64,9 +72,13 @@ class Params:
         return 2 * self.m + 1 if self.closed else 2 * self.m
 
     def window(self, u, b):
+        if self.window_mode == "linear":
+            return psi_linear(u, self.m, b, self.closed)
         return psi_full(u, self.m, b) if self.wide else psi(u, self.m, b, self.closed)
 
     def dwindow(self, u, b):
+        if self.window_mode == "linear":
+            return dpsi_linear(u, self.m, b, self.closed)
         return dpsi_full(u, self.m, b) if self.wide else dpsi(u, self.m, b, self.closed)
 
 
@@ -164,18 +176,18 @@ def fft_adjoint(ghat):
     return np.fft.ifftn(ghat, norm="forward")
 
 
-def forward(k, f, sigma=2.0, m=4, closed=False, wide=False):
+def forward(k, f, sigma=2.0, m=4, closed=False, wide=False, window="direct"):
     """Direct NFFT, Algorithm 1: fhat ~= A f."""
     f = np.asarray(f, dtype=np.complex128)
-    p = Params(f.shape, sigma, m, closed, wide)
+    p = Params(f.shape, sigma, m, closed, wide, window)
     g = correction_pad(p, f)
     ghat = fft_forward(g)
     return resample(p, k, ghat)
 
 
-def adjoint(k, fhat, N, sigma=2.0, m=4, closed=False, wide=False):
+def adjoint(k, fhat, N, sigma=2.0, m=4, closed=False, wide=False, window="direct"):
     """Adjoint NFFT, Algorithm 2: y ~= A^H fhat."""
-    p = Params(N, sigma, m, closed, wide)
+    p = Params(N, sigma, m, closed, wide, window)
     ghat = resample_adjoint(p, k, fhat)
     g = fft_adjoint(ghat)
     return crop_correction(p, g)
@@ -205,12 +217,12 @@ def resample_node_derivative(p, k, ghat):
     return out
 
 
-def node_grad(k, f, cot, sigma=2.0, m=4, closed=False, wide=False):
+def node_grad(k, f, cot, sigma=2.0, m=4, closed=False, wide=False, window="direct"):
     """Node gradient of a real loss through the NFFT fhat = A f:
     g[j, d] = Re(conj(cot_j) d fhat_j / d k_{j,d}) (PyTorch's convention for a
     real loss of complex outputs)."""
     f = np.asarray(f, dtype=np.complex128)
-    p = Params(f.shape, sigma, m, closed, wide)
+    p = Params(f.shape, sigma, m, closed, wide, window)
     ghat = fft_forward(correction_pad(p, f))
     dk = resample_node_derivative(p, k, ghat)
     return np.real(np.conj(np.asarray(cot, dtype=np.complex128))[:, None] * dk)

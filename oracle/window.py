@@ -21,7 +21,8 @@ Sources (arXiv 2208.00049, NFFT.jl):
     the tests (Gauss-Legendre quadrature), not assumed.
   * Sec. 3.7.4 (LINEAR precomputation): table size S = m 2^{c_min(m,8)} + 2
     with C = (3, 7, 9, 14, 17, 20, 23, 24); the paper prints S = 134217730
-    for m = 8.
+    for m = 8; entries psi_s = psi_Base(s/(S-2)) read with linear
+    interpolation (Eq. linInterp).
 
 Plain numpy, FP64.  Library primitives used: numpy.sinh, numpy.cosh,
 numpy.sqrt, numpy.i0.
@@ -158,10 +159,50 @@ def deconv_factor(n, Ntilde, m, b):
 
 
 def lut_size(m):
-    """LINEAR table size S = m 2^{c_min(m,8)} + 2 (Sec. 3.7.4)."""
+    """LINEAR table size S = m 2^{c_min(m,8)} + 2 (Sec. 3.7.4); m > 8 keeps c_8."""
     if m < 1:
         raise ValueError("m >= 1")
     return m * 2 ** LUT_EXPONENTS[min(m, 8) - 1] + 2
+
+
+def lut_entry(s, m, b):
+    """Entry s of the LINEAR table of Sec. 3.7.4, psi_s = psi_Base(s/(S-2)):
+    the window at u = m s / (S - 2) in grid units on its closed support
+    [-m, m] (entry S - 2 is the edge value b/pi that the tap at u = -m reads
+    through |u|), 0 beyond it (entry S - 1, outside the support)."""
+    S = lut_size(m)
+    s = np.asarray(s)
+    return psi(m * s / (S - 2.0), m, b, closed=True)
+
+
+def psi_linear(u, m, b, closed=False):
+    """The window looked up in the LINEAR table with linear interpolation
+    (Eq. linInterp, Sec. 3.7.4): kappa = |(S-2)/m u|, s = floor(kappa),
+    alpha = kappa - s, value = psi_s + alpha (psi_{s+1} - psi_s), on the
+    support of psi (0 outside it).  The table entries are evaluated where the
+    lookup reads them (S reaches 1.3e8 at m = 8)."""
+    u = np.asarray(u, dtype=np.float64)
+    S = lut_size(m)
+    kappa = np.abs(u) * ((S - 2.0) / m)
+    s = np.floor(kappa)
+    alpha = kappa - s
+    lo = lut_entry(s, m, b)
+    hi = lut_entry(s + 1, m, b)
+    val = lo + alpha * (hi - lo)
+    inside = (u >= -m) & ((u <= m) if closed else (u < m))
+    return np.where(inside, val, 0.0)
+
+
+def dpsi_linear(u, m, b, closed=False):
+    """d psi_linear / du: the slope of the interpolant's segment,
+    sign(u) (S-2)/m (psi_{s+1} - psi_s), 0 outside the support."""
+    u = np.asarray(u, dtype=np.float64)
+    S = lut_size(m)
+    kappa = np.abs(u) * ((S - 2.0) / m)
+    s = np.floor(kappa)
+    slope = (lut_entry(s + 1, m, b) - lut_entry(s, m, b)) * ((S - 2.0) / m)
+    inside = (u >= -m) & ((u <= m) if closed else (u < m))
+    return np.where(inside, np.sign(u) * slope, 0.0)
 
 
 def index_set(N):

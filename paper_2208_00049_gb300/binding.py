@@ -28,6 +28,9 @@ NFFT_FLAG_COMPENSATED = 0x2
 NFFT_FLAG_FULL_MATRIX = 0x4
 NFFT_FLAG_WIDE_WINDOW = 0x8
 NFFT_FLAG_LIBRARY_FFT = 0x10
+NFFT_FLAG_WINDOW_DIRECT = 0x20
+NFFT_FLAG_WINDOW_LINEAR = 0x40
+NFFT_FLAG_WINDOW_POLYNOMIAL = 0x80
 
 _p = ctypes.c_void_p
 _i = ctypes.c_int
@@ -54,6 +57,7 @@ SIGNATURES = {
     "nfft_step_crop_deconv": (_i, [_p, _p]),
     "nfft_step_pad_fft": (_i, [_p, _p]),
     "nfft_step_fft_crop": (_i, [_p, _p]),
+    "nfft_plan_set_graph": (_i, [_p, _i]),
     "nfft_plan_paths": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nfft_step_grad_gather": (_i, [_p, _p, _p]),
     "nfft_plan_autotune": (_i, [_p, _p, _i, _i64p]),
@@ -196,6 +200,10 @@ def nfft_step_pad_fft(plan, f_ptr):
 
 def nfft_step_fft_crop(plan, y_ptr):
     return lib().nfft_step_fft_crop(_p(plan), _p(y_ptr))
+
+
+def nfft_plan_set_graph(plan, enable):
+    return lib().nfft_plan_set_graph(_p(plan), int(bool(enable)))
 
 
 def nfft_plan_paths(plan):

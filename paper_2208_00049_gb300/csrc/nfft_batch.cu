@@ -488,6 +488,7 @@ int nfft_batch_create(nfft_batch** out, int D, int B, const int64_t* N, const in
   *out = nullptr;
   if (D < 1 || D > kMaxD || B < 1 || S < 1 || S > B || !N || !set_of || !M_set) return NFFT_ERR_INVALID_ARG;
   if (!(sigma > 1.0) || m < 1 || m > kMaxM) return NFFT_ERR_INVALID_ARG;
+  if (m > 8) return NFFT_ERR_UNSUPPORTED;  // the batched kernels are built for m <= 8
   if (dtype != NFFT_C64 && dtype != NFFT_C128) return NFFT_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW)) return NFFT_ERR_INVALID_ARG;
   if ((flags & NFFT_FLAG_CLOSED_SUPPORT) && (flags & NFFT_FLAG_WIDE_WINDOW)) return NFFT_ERR_INVALID_ARG;

@@ -57,7 +57,8 @@ __global__ void build_rows_kernel(Geometry g, NodeArrays na, int* __restrict__ c
       int nwrap_hi = 0;
 #pragma unroll
       for (int i = 0; i < K; ++i) nwrap_hi += (c + g.off + i >= g.Nt[d]) ? 1 : 0;
-      const R b = R(g.b[d]), norm = R(g.norm[d]);
+      const R b = R(g.b[d]), norm = R(g.norm[d]), mr = R(mi);
+      const R normx = sizeof(R) == 4 ? kb_normx<R>(b, mr) : R(0);
 #pragma unroll
       for (int s = 0; s < K; ++s) {
         // ascending order: taps with l' < 0 wrap to the top, l' >= N~ to the bottom
@@ -72,9 +73,10 @@ __global__ void build_rows_kernel(Geometry g, NodeArrays na, int* __restrict__ c
         }
         int l = c + g.off + i;
         l = l < 0 ? l + g.Nt[d] : (l >= g.Nt[d] ? l - g.Nt[d] : l);
+        const R u = R(-g.off - i) + t;
         const R mm_u = R(mi + g.off + i) - t;
         const R mp_u = R(mi - g.off - i) + t;
-        R v = kb_window<R>(mm_u, mp_u, b, norm);
+        R v = kb_window<R>(u, mm_u, mp_u, b, norm, mr, normx);
         if (g.closed && ((i == 0 && t != R(0)) || i == K - 1)) v = R(0);
         pos[d][s] = l;
         w[d][s] = v;

@@ -20,7 +20,14 @@ namespace nfftgb {
 
 constexpr int kMaxD = 3;
 constexpr int kResampleThreads = 128;
-constexpr int kMaxM = 8;
+constexpr int kMaxM = 10;
+
+// How the generic resampling kernels obtain window values (Sec. 3.7.4):
+// evaluated (sinh, sqrt), looked up in the LINEAR table with linear
+// interpolation, or from the POLYNOMIAL coefficients (Horner).
+constexpr int kWinDirect = 0;
+constexpr int kWinLinear = 1;
+constexpr int kWinPoly = 2;
 
 // Everything a resampling kernel needs about the plan, passed by value.
 // Dimension d = D-1 is the contiguous one.
@@ -37,6 +44,13 @@ struct Geometry {
   double m;          // window half-width
   double b[kMaxD];   // Kaiser-Bessel shape per dimension
   double norm[kMaxD];  // m / sinh(b m): scales the window to 1 at u = 0
+  // window values of the generic kernels: kWinDirect (wtab unused),
+  // kWinLinear (wtab = D tables of wS entries of the scaled window in the
+  // plan's real type, table d at d * wS), kWinPoly (wtab = [D][K][2m + 1]
+  // coefficients in the plan's real type)
+  int wmode;
+  int wS;
+  const void* wtab;
 };
 
 // Kaiser-Bessel window in grid units, scaled to 1 at u = 0:
@@ -46,17 +60,38 @@ struct Geometry {
 // (2m+2)-point footprint).  s^2 is formed as (m - u)(m + u) from the integer
 // and fractional parts of u so that it stays accurate near the support
 // edges.  At s = 0 both forms tend to b * m/sinh(b m).
+//
+// In single precision the ratio sinh(b s)/sinh(b m) loses about b m ulps
+// (the rounding of the argument b s, up to b m ~ 47 at m = 10, is amplified
+// by the exponential), and it loses them at the largest taps.  There the
+// same value is taken as
+//   w(u) = exp(b (s - m)) (1 - exp(-2 b s)) / s * m/(1 - exp(-2 b m)),
+//   b (s - m) = -b u^2 / (s + m),
+// whose exponent is small where the window is large, so the error of each
+// tap scales with its own size.
 template <typename R>
-__device__ __forceinline__ R kb_window(R mm_u, R mp_u, R b, R norm) {
+__device__ __forceinline__ R kb_window(R u, R mm_u, R mp_u, R b, R norm, R m, R normx) {
   const R s2 = mm_u * mp_u;
   const R s = sqrt(s2 > R(0) ? s2 : -s2);
   const R z = b * s;
   R r;
-  if (s2 >= R(0))
-    r = (z < R(1e-3)) ? b * (R(1) + z * z * R(1.0 / 6.0)) : sinh(z) / s;
-  else
+  if (s2 >= R(0)) {
+    if (z < R(1e-3))
+      r = b * (R(1) + z * z * R(1.0 / 6.0));
+    else if (sizeof(R) == 4)
+      return exp(-b * (u * u) / (s + m)) * (-expm1(R(-2) * z)) / s * normx;
+    else
+      r = sinh(z) / s;
+  } else {
     r = (z < R(1e-3)) ? b * (R(1) - z * z * R(1.0 / 6.0)) : sin(z) / s;
+  }
   return r * norm;
+}
+
+// m/(1 - exp(-2 b m)): the scale of the single-precision form above.
+template <typename R>
+__device__ __forceinline__ R kb_normx(R b, R m) {
+  return m / (-expm1(R(-2) * b * m));
 }
 
 // Derivative of the scaled window with respect to u:
@@ -64,18 +99,25 @@ __device__ __forceinline__ R kb_window(R mm_u, R mp_u, R b, R norm) {
 //   |u| > m:  w'(u) = +u (b s' cos(b s') - sin(b s')) / s'^3 * m/sinh(b m)
 // with the series b^3 (1/3 + z^2/30 + z^4/840 + z^6/45360) inside and
 // b^3 (-1/3 + z^2/30 - z^4/840 + z^6/45360) outside for small z = b s.
+// Single precision takes z cosh z - sinh z = e^z ((z - 1) + (z + 1) e^{-2z}) / 2
+// inside, scaled as in kb_window (normx carries the factor N~ of norm).
 template <typename R>
-__device__ __forceinline__ R kb_window_deriv(R u, R mm_u, R mp_u, R b, R norm, R zsmall) {
+__device__ __forceinline__ R kb_window_deriv(R u, R mm_u, R mp_u, R b, R norm, R zsmall, R m, R normx) {
   const R s2 = mm_u * mp_u;
   const R s = sqrt(s2 > R(0) ? s2 : -s2);
   const R z = b * s;
   const R z2 = z * z;
   R h;
   if (s2 >= R(0)) {
-    if (z < zsmall)
+    if (z < zsmall) {
       h = b * b * b * (R(1.0 / 3.0) + z2 * (R(1.0 / 30.0) + z2 * (R(1.0 / 840.0) + z2 * R(1.0 / 45360.0))));
-    else
+    } else if (sizeof(R) == 4) {
+      const R e = -b * (u * u) / (s + m);
+      const R g = (z - R(1)) + (z + R(1)) * exp(R(-2) * z);
+      return -u * exp(e) * g / (s * s * s) * normx;
+    } else {
       h = (z * cosh(z) - sinh(z)) / (s * s * s);
+    }
     return -u * h * norm;
   }
   if (z < zsmall)
@@ -145,15 +187,16 @@ cudaError_t launch_grad3d_fast(const Geometry& g, const void* grid, const NodeAr
 // 3D complex64 register-accumulating scatter, m = 4 or 6 (any tile of at
 // most 17 - 2m cells per dimension); kind 1 of the two functions below.
 bool fast_scatter_supported(const Geometry& g, int cmax);
-int fast3d_ctas_per_sm(const Geometry& g, int kind);  // kind 0 gather, 1 scatter
+int fast3d_ctas_per_sm(const Geometry& g, int kind);  // kind 0 gather, 1 scatter, 2 compensated scatter
 // 1 if a CTA of the 3D gather / node gradient gave up its bounded wait for a
 // region copy since the last call (the flag is cleared), 0 if not, -1 if the
 // flag could not be read.  Synchronous; call with the plan's device current.
 int fast3d_take_wait_timeout();
 cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na,
                                  const float* poly, void* fhat, int ctas, cudaStream_t s);
+// compensated != 0: TwoSum-compensated accumulation (NFFT_FLAG_COMPENSATED)
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
-                                  const float* poly, const void* fhat, int ctas, cudaStream_t s);
+                                  const float* poly, const void* fhat, int compensated, int ctas, cudaStream_t s);
 
 // Pruned 3D FFT with the resampling correction fused in, N~_d = 2 N_d = 256,
 // complex64 (fft_pruned.cu).  `tw` holds kPrunedFftTwiddles inter-stage
@@ -169,7 +212,7 @@ cudaError_t launch_pruned_adjoint(void* grid, const float* const* beta, const fl
 // gather (resample2d.cu): tiles of at most 9 cells in dimension 0 and
 // regions of at most 32 in dimension 1.
 bool scatter2d_supported(const Geometry& g);
-int scatter2d_ctas_per_sm();
+int scatter2d_ctas_per_sm(int compensated = 0);
 int gather2d_ctas_per_sm();
 // poly: POLYNOMIAL coefficients [D][K][2m + 1] of the plan, or of all
 // problems of a batch (problem p's table at poly + probs[p].poly_off).
@@ -178,7 +221,7 @@ cudaError_t launch_gather2d_fast(const Geometry& g, const void* grid, const Node
 cudaError_t launch_gather2d_fast_batch(const BatchProblem* probs, const void* grid, const BatchNodes& nb,
                                        const float* poly, void* fhat, int ctas, cudaStream_t s);
 cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArrays& na, const float* poly,
-                                  const void* fhat, int ctas, cudaStream_t s);
+                                  const void* fhat, int compensated, int ctas, cudaStream_t s);
 cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb,
                                         const float* poly, const void* fhat, int ctas, cudaStream_t s);
 
@@ -209,7 +252,15 @@ struct PolyArgs {
   int m;
   double b[kMaxD];
 };
-cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s);
+// coef64 (may be null) receives the FP64 coefficients as well.
+cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s, double* coef64 = nullptr);
+
+// LINEAR window tables (Sec. 3.7.4): for each dimension d, entries
+// s = 0 .. S - 1 of the window scaled to 1 at u = 0, at u = m s / (S - 2) on
+// its closed support and 0 beyond (entry S - 1), S = m 2^{c_min(m,8)} + 2;
+// computed in FP64, stored in FP32 (lut32) and/or FP64 (lut64).
+int64_t lut_table_size(int m);
+cudaError_t launch_build_lut(int D, int m, const double* b, int64_t S, float* lut32, double* lut64, cudaStream_t s);
 
 // Batched correction kernels: one 1D grid of `blocks` blocks of
 // kBatchDeconvThreads threads, problem p owning blocks

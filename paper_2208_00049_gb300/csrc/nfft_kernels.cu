@@ -97,7 +97,7 @@ cudaError_t launch_build_beta(int D, const int* N, const int* Nt, int m, const d
 // ---------------------------------------------------------------------------
 constexpr int kMaxPolyCoef = 2 * kMaxM + 1;
 
-__global__ void build_poly_kernel(PolyArgs a, float* coef) {
+__global__ void build_poly_kernel(PolyArgs a, float* coef, double* coef64) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= a.D * a.K) return;
   const int d = idx / a.K, i = idx % a.K;
@@ -139,12 +139,64 @@ __global__ void build_poly_kernel(PolyArgs a, float* coef) {
     for (int c = r + 1; c < Z; ++c) acc -= V[r][c] * V[c][Z];
     V[r][Z] = acc / V[r][r];
   }
-  for (int z = 0; z < Z; ++z) coef[(d * a.K + i) * Z + z] = (float)V[z][Z];
+  for (int z = 0; z < Z; ++z) {
+    coef[(d * a.K + i) * Z + z] = (float)V[z][Z];
+    if (coef64) coef64[(d * a.K + i) * Z + z] = V[z][Z];
+  }
 }
 
-cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s) {
+cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s, double* coef64) {
   if (a.deg + 1 > kMaxPolyCoef) return cudaErrorInvalidValue;
-  build_poly_kernel<<<1, 64, 0, s>>>(a, coef);
+  build_poly_kernel<<<1, 64, 0, s>>>(a, coef, coef64);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// LINEAR window tables (Sec. 3.7.4): psi_s = psi_Base(s / (S - 2)), i.e. the
+// window (scaled to 1 at u = 0) at u = m s / (S - 2) in grid units, on the
+// closed support [-m, m] (entry S - 2 is the edge value read by the tap at
+// u = -m) and 0 beyond it (entry S - 1), S = m 2^{c_min(m, 8)} + 2 with NFFT3's
+// exponents C = (3, 7, 9, 14, 17, 20, 23, 24).  FP64 arithmetic.
+// ---------------------------------------------------------------------------
+int64_t lut_table_size(int m) {
+  static const int C[8] = {3, 7, 9, 14, 17, 20, 23, 24};
+  if (m < 1) return 0;
+  return (int64_t)m * ((int64_t)1 << C[(m < 8 ? m : 8) - 1]) + 2;
+}
+
+struct LutArgs {
+  int D;
+  int m;
+  int64_t S;
+  double b[kMaxD];
+};
+
+__global__ void build_lut_kernel(LutArgs a, float* lut32, double* lut64) {
+  const int64_t n = (int64_t)a.D * a.S;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int d = (int)(e / a.S);
+    const int64_t sidx = e - (int64_t)d * a.S;
+    const double m = (double)a.m, b = a.b[d];
+    double v = 0.0;
+    if (sidx <= a.S - 2) {
+      const double u = m * (double)sidx / (double)(a.S - 2);
+      const double s2 = (m - u) * (m + u);
+      const double sq = sqrt(s2 > 0.0 ? s2 : 0.0);
+      const double z = b * sq;
+      v = (z < 1e-4 ? b * (1.0 + z * z / 6.0) : sinh(z) / sq) * (m / sinh(b * m));
+    }
+    if (lut32) lut32[e] = (float)v;
+    if (lut64) lut64[e] = v;
+  }
+}
+
+cudaError_t launch_build_lut(int D, int m, const double* b, int64_t S, float* lut32, double* lut64, cudaStream_t s) {
+  LutArgs a{};
+  a.D = D;
+  a.m = m;
+  a.S = S;
+  for (int d = 0; d < D; ++d) a.b[d] = b[d];
+  build_lut_kernel<<<launch_blocks((int64_t)D * S, 256), 256, 0, s>>>(a, lut32, lut64);
   return cudaGetLastError();
 }
 

@@ -53,6 +53,10 @@ struct nfft_plan {
   double* beta64 = nullptr;
   float* beta32 = nullptr;
   float* poly = nullptr;  // POLYNOMIAL window coefficients [D][K][2m + 1] (FP32)
+  double* poly64 = nullptr;  // the same in FP64 (complex128 plans with NFFT_FLAG_WINDOW_POLYNOMIAL)
+  int wmode = kWinDirect;    // window values of the generic kernels
+  void* lut = nullptr;       // LINEAR tables, D x lut_S entries of the plan's real type
+  int64_t lut_S = 0;
   int* cell = nullptr;
   void* frac = nullptr;
   int* perm = nullptr;
@@ -70,6 +74,12 @@ struct nfft_plan {
 
   cufftHandle fft = 0;
   bool fft_ok = false;
+  // graph mode: nfft_forward / nfft_adjoint captured once per pair of device
+  // buffers on capture_stream and replayed on `stream`
+  bool graph_mode = false;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // forward, adjoint
+  const void* graph_ptr[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool has_nodes = false;
   int err = NFFT_OK;
 };
@@ -208,6 +218,11 @@ Geometry make_geometry(const nfft_plan* p) {
   g.closed = (p->flags & NFFT_FLAG_CLOSED_SUPPORT) ? 1 : 0;
   g.M = (int)p->M;
   g.m = (double)p->m;
+  g.wmode = p->wmode;
+  g.wS = (int)p->lut_S;
+  g.wtab = p->wmode == kWinLinear ? (const void*)p->lut
+           : p->wmode == kWinPoly ? (p->dtype == NFFT_C128 ? (const void*)p->poly64 : (const void*)p->poly)
+                                  : nullptr;
   for (int d = 0; d < p->D; ++d) {
     g.Nt[d] = (int)p->Nt[d];
     g.T[d] = (int)p->T[d];
@@ -262,21 +277,21 @@ void default_tile(const nfft_plan* p, int64_t* T) {
   // (regions of 16 x 16 x 15) measured 3.5 % faster than 8^3 for gather +
   // scatter at 0.125 nodes per cell, with fewer halo reductions per node.
   const bool fast_shape = p->D == 3 && p->m == 4 && p->K == 8 && p->dtype == NFFT_C64 &&
-                          !(p->flags & (NFFT_FLAG_COMPENSATED | NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
+                          !(p->flags & (NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
   const int64_t pref[kMaxD] = {9, 9, 8};
   // 3D m = 6 complex64: the K = 12 gather and the register-accumulating
   // scatter need tiles of at most 5 cells per dimension; 5^3 measured best
   // for gather + scatter at the sigma = 1.25 lean variant (2.50 ms against
   // 18.9 ms for the generic kernels at 8^3)
   const bool m6_shape = p->D == 3 && p->m == 6 && p->K == 12 && p->dtype == NFFT_C64 &&
-                        !(p->flags & (NFFT_FLAG_COMPENSATED | NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
+                        !(p->flags & (NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
   const int64_t pref6[kMaxD] = {5, 5, 5};
   // 2D m = 4 complex64: the warp-per-item kernels take regions of at most
   // 16 x 32 cells; 9 x 25 tiles for large grids (measured best on the batched
   // workload), 8 x 8 when that would leave fewer than 32 items per SM (512^2:
   // 1.31 against 1.16 G nodes/s for gather + scatter)
   const bool m4_2d = p->D == 2 && p->m == 4 && p->K == 8 && p->dtype == NFFT_C64 &&
-                     !(p->flags & (NFFT_FLAG_COMPENSATED | NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
+                     !(p->flags & (NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
   const bool big2d = p->D == 2 && (double)p->Nt[0] * (double)p->Nt[1] >= 225.0 * 32.0 * (double)p->sms;
   const int64_t pref2[kMaxD] = {big2d ? 9 : 8, big2d ? 25 : 8, 1};
   for (int d = 0; d < p->D; ++d) {
@@ -290,7 +305,20 @@ void default_tile(const nfft_plan* p, int64_t* T) {
   }
 }
 
+constexpr uint32_t kWindowFlags = NFFT_FLAG_WINDOW_DIRECT | NFFT_FLAG_WINDOW_LINEAR | NFFT_FLAG_WINDOW_POLYNOMIAL;
+
+// Captured graphs hold the launch configuration and buffers of the moment;
+// dropped when either changes.
+void drop_graphs(nfft_plan* p) {
+  for (int k = 0; k < 2; ++k) {
+    if (p->graph[k]) cudaGraphExecDestroy(p->graph[k]);
+    p->graph[k] = nullptr;
+    p->graph_ptr[k][0] = p->graph_ptr[k][1] = nullptr;
+  }
+}
+
 int configure_tiles(nfft_plan* p, const int64_t* T) {
+  drop_graphs(p);
   int64_t n_tiles = 1;
   for (int d = 0; d < p->D; ++d) {
     p->T[d] = T[d];
@@ -319,10 +347,15 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
     p->items_cap = p->max_items;
   }
   Geometry g = make_geometry(p);
-  const bool plain_c64 = p->dtype == NFFT_C64 && !(p->flags & NFFT_FLAG_COMPENSATED);
-  p->fast_gather = plain_c64 && fast3d_supported(g, p->cmax);
-  p->fast_scatter = plain_c64 && (p->fast_gather || fast_scatter_supported(g, p->cmax));
-  if (p->D == 2) p->fast_gather = p->fast_scatter = plain_c64 && scatter2d_supported(g);
+  // complex64 plans use the specialised kernels where the tile allows; with
+  // NFFT_FLAG_COMPENSATED their scatter runs in its TwoSum-compensated form
+  // a window flag selects the generic kernels (the window modes compared on
+  // the same kernels); otherwise complex64 plans use the specialised ones
+  const bool c64 = p->dtype == NFFT_C64 && !(p->flags & kWindowFlags);
+  const int comp = (p->flags & NFFT_FLAG_COMPENSATED) && c64 ? 1 : 0;
+  p->fast_gather = c64 && fast3d_supported(g, p->cmax);
+  p->fast_scatter = c64 && (p->fast_gather || fast_scatter_supported(g, p->cmax));
+  if (p->D == 2) p->fast_gather = p->fast_scatter = c64 && scatter2d_supported(g);
   if (p->fast_gather) {
     const int per_sm = p->D == 2 ? gather2d_ctas_per_sm() : fast3d_ctas_per_sm(g, 0);
     p->fast_gather = per_sm > 0;
@@ -331,15 +364,20 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
   p->grad_ctas = 0;
   if (p->fast_gather && p->D == 3 && p->K == 8) p->grad_ctas = grad3d_ctas_per_sm(g) * p->sms;
   if (p->fast_scatter) {
-    const int per_sm = p->D == 2 ? scatter2d_ctas_per_sm() : fast3d_ctas_per_sm(g, 1);
+    const int per_sm = p->D == 2 ? scatter2d_ctas_per_sm(comp) : fast3d_ctas_per_sm(g, comp ? 2 : 1);
     p->fast_scatter = per_sm > 0;
     p->fast_ctas[1] = per_sm * p->sms;
   }
+  // generic kernels: gather and scatter are required; the compensated scatter
+  // where the plan asks for it and no fast scatter serves it; the node
+  // gradient is optional (m = 9, 10 have none: nfft_grad reports UNSUPPORTED)
   for (int kind = 0; kind < 4; ++kind) {
     int per_sm = p->dtype == NFFT_C128 ? resample_ctas_per_sm<double>(g, kind)
                                        : resample_ctas_per_sm<float>(g, kind);
-    if (per_sm <= 0) return NFFT_ERR_UNSUPPORTED;
-    p->ctas[kind] = per_sm * p->sms;
+    const bool comp_req = (p->flags & NFFT_FLAG_COMPENSATED) && p->dtype == NFFT_C64;
+    const bool needed = kind < 2 || (kind == 2 && comp_req && !p->fast_scatter);
+    if (per_sm <= 0 && needed) return NFFT_ERR_UNSUPPORTED;
+    p->ctas[kind] = per_sm > 0 ? per_sm * p->sms : 0;
   }
   return NFFT_OK;
 }
@@ -406,8 +444,8 @@ int run_scatter(nfft_plan* p, const void* fhat) {
   const int comp = (p->flags & NFFT_FLAG_COMPENSATED) && p->dtype == NFFT_C64 ? 1 : 0;
   cudaError_t e =
       p->fast_scatter
-          ? (p->D == 2 ? launch_scatter2d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[1], p->stream)
-                       : launch_scatter3d_fast(g, p->grid, na, p->poly, fhat, p->fast_ctas[1], p->stream))
+          ? (p->D == 2 ? launch_scatter2d_fast(g, p->grid, na, p->poly, fhat, comp, p->fast_ctas[1], p->stream)
+                       : launch_scatter3d_fast(g, p->grid, na, p->poly, fhat, comp, p->fast_ctas[1], p->stream))
       : p->dtype == NFFT_C128
           ? launch_scatter<double>(g, p->grid, na, fhat, 0, p->ctas[1], p->stream)
           : launch_scatter<float>(g, p->grid, na, fhat, comp, p->ctas[comp ? 2 : 1], p->stream);
@@ -455,7 +493,48 @@ int run_crop_deconv(nfft_plan* p, void* y) {
   return cuda_status(p, e);
 }
 
+// Algorithm 1 (dir 0: correction + pad + FFT, gather) or Algorithm 2 (dir 1:
+// scatter, inverse FFT + crop + correction) on device buffers.
+int run_plain(nfft_plan* p, int dir, const void* in, void* out) {
+  int s = dir == 0 ? run_pad_fft(p, in) : run_scatter(p, in);
+  if (s != NFFT_OK) return s;
+  return dir == 0 ? run_gather(p, out) : run_fft_crop(p, out);
+}
+
+// The same through a CUDA graph in graph mode: captured on the internal
+// stream (cuFFT pointed at it meanwhile) the first time a pair of buffers is
+// seen, replayed on the plan's stream afterwards.
+int run_direction(nfft_plan* p, int dir, const void* in, void* out) {
+  if (!p->graph_mode) return run_plain(p, dir, in, out);
+  if (!p->graph[dir] || p->graph_ptr[dir][0] != in || p->graph_ptr[dir][1] != out) {
+    if (p->graph[dir]) cudaGraphExecDestroy(p->graph[dir]);
+    p->graph[dir] = nullptr;
+    if (!p->capture_stream) NFFT_CK(p, cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = p->stream;
+    p->stream = p->capture_stream;
+    if (p->fft_ok && cufftSetStream(p->fft, p->capture_stream) != CUFFT_SUCCESS) {
+      p->stream = saved;
+      return latch(p, NFFT_ERR_CUFFT);
+    }
+    cudaError_t e = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal);
+    int s = e == cudaSuccess ? run_plain(p, dir, in, out) : NFFT_OK;
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(p->capture_stream, &graph);
+    p->stream = saved;
+    if (p->fft_ok && cufftSetStream(p->fft, saved) != CUFFT_SUCCESS) s = latch(p, NFFT_ERR_CUFFT);
+    if (s == NFFT_OK && e == cudaSuccess) e = cudaGraphInstantiate(&p->graph[dir], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (s != NFFT_OK) return s;
+    NFFT_CK(p, e);
+    p->graph_ptr[dir][0] = in;
+    p->graph_ptr[dir][1] = out;
+  }
+  NFFT_CK(p, cudaGraphLaunch(p->graph[dir], p->stream));
+  return NFFT_OK;
+}
+
 int run_grad_gather(nfft_plan* p, const void* cot, void* gk) {
+  if (p->grad_ctas <= 0 && p->ctas[3] <= 0) return NFFT_ERR_UNSUPPORTED;
   Geometry g = make_geometry(p);
   NodeArrays na = node_arrays(p);
   cudaError_t e =
@@ -489,9 +568,12 @@ int nfft_plan_destroy(nfft_plan* p) {
   if (!p) return NFFT_OK;
   DeviceGuard guard(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
+  drop_graphs(p);
+  if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   if (p->fft_ok) cufftDestroy(p->fft);
   full_destroy(p->full);
-  void* bufs[] = {p->grid, p->fft_tw, p->beta64, p->beta32, p->poly, p->cell, p->frac, p->perm, p->key, p->rank,
+  void* bufs[] = {p->grid, p->fft_tw, p->beta64, p->beta32, p->poly, p->poly64, p->lut, p->cell, p->frac, p->perm,
+                  p->key, p->rank,
                   p->tile_count, p->tile_offset, p->items, p->n_items,
                   p->stage[0], p->stage[1], p->stage[2]};
   for (void* b : bufs) dfree(b);
@@ -507,10 +589,19 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
   if (!(sigma > 1.0) || m < 1 || m > kMaxM) return NFFT_ERR_INVALID_ARG;
   if (dtype != NFFT_C64 && dtype != NFFT_C128) return NFFT_ERR_INVALID_ARG;
   if (M < 0 || M >= ((int64_t)1 << 31)) return NFFT_ERR_INVALID_ARG;
+  if (D == 3 && m > 8) return NFFT_ERR_UNSUPPORTED;  // m = 9, 10 are built for 1D and 2D
   if (flags & ~(uint32_t)(NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_COMPENSATED | NFFT_FLAG_FULL_MATRIX |
-                          NFFT_FLAG_WIDE_WINDOW | NFFT_FLAG_LIBRARY_FFT))
+                          NFFT_FLAG_WIDE_WINDOW | NFFT_FLAG_LIBRARY_FFT | kWindowFlags))
     return NFFT_ERR_INVALID_ARG;
   if ((flags & NFFT_FLAG_CLOSED_SUPPORT) && (flags & NFFT_FLAG_WIDE_WINDOW)) return NFFT_ERR_INVALID_ARG;
+  {
+    const uint32_t wf = flags & kWindowFlags;
+    if (wf & (wf - 1)) return NFFT_ERR_INVALID_ARG;  // at most one window mode
+    if (wf && (flags & NFFT_FLAG_FULL_MATRIX)) return NFFT_ERR_INVALID_ARG;
+    if ((wf & NFFT_FLAG_WINDOW_LINEAR) && (flags & NFFT_FLAG_WIDE_WINDOW)) return NFFT_ERR_INVALID_ARG;
+    if ((wf & NFFT_FLAG_WINDOW_POLYNOMIAL) && (flags & (NFFT_FLAG_WIDE_WINDOW | NFFT_FLAG_CLOSED_SUPPORT)))
+      return NFFT_ERR_INVALID_ARG;
+  }
   int64_t total = 1;
   for (int d = 0; d < D; ++d) {
     if (N[d] < 2 || N[d] > ((int64_t)1 << 28)) return NFFT_ERR_INVALID_ARG;
@@ -583,6 +674,19 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
     }
     s = cuda_status(p, launch_build_beta(D, Ni, Nti, m, p->b, p->beta64, p->beta32, p->stream));
   }
+  if (s == NFFT_OK && (flags & NFFT_FLAG_WINDOW_LINEAR)) {
+    p->wmode = kWinLinear;
+    p->lut_S = lut_table_size(m);
+    if ((double)p->lut_S * D * real_size(p) > 8e9) s = NFFT_ERR_UNSUPPORTED;
+    if (s == NFFT_OK) s = dalloc(p, &p->lut, (size_t)(p->lut_S * D) * real_size(p));
+    if (s == NFFT_OK)
+      s = cuda_status(p, launch_build_lut(D, m, p->b, p->lut_S, dtype == NFFT_C128 ? nullptr : (float*)p->lut,
+                                          dtype == NFFT_C128 ? (double*)p->lut : nullptr, p->stream));
+  }
+  if (s == NFFT_OK && (flags & NFFT_FLAG_WINDOW_POLYNOMIAL)) {
+    p->wmode = kWinPoly;
+    if (dtype == NFFT_C128) s = dalloc(p, &p->poly64, sizeof(double) * D * p->K * (2 * m + 1));
+  }
   if (s == NFFT_OK && !closed && !wide) {
     PolyArgs pa{};
     pa.D = D;
@@ -591,7 +695,7 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
     pa.deg = 2 * m;
     pa.m = m;
     for (int d = 0; d < D; ++d) pa.b[d] = p->b[d];
-    s = cuda_status(p, launch_build_poly(pa, p->poly, p->stream));
+    s = cuda_status(p, launch_build_poly(pa, p->poly, p->stream, p->poly64));
   }
   if (s == NFFT_OK && dtype == NFFT_C64 && !(flags & NFFT_FLAG_LIBRARY_FFT)) {
     int Ni[kMaxD], Nti[kMaxD];
@@ -658,8 +762,8 @@ int nfft_forward(nfft_plan* p, const void* f, void* fhat) {
   OutputBinding ob;
   if ((s = device_input(p, 0, f, (size_t)prod_N(p) * cplx_size(p), &fd)) != NFFT_OK) return s;
   if ((s = device_output(p, 1, fhat, (size_t)p->M * cplx_size(p), &ob)) != NFFT_OK) return s;
-  if ((s = run_pad_fft(p, fd)) != NFFT_OK) return s;
-  if ((s = run_gather(p, ob.dev)) != NFFT_OK) return s;
+  if (fd == f && !ob.host) return run_direction(p, 0, fd, ob.dev);
+  if ((s = run_plain(p, 0, fd, ob.dev)) != NFFT_OK) return s;
   return finish_output(p, ob);
 }
 
@@ -673,8 +777,8 @@ int nfft_adjoint(nfft_plan* p, const void* fhat, void* y) {
   OutputBinding ob;
   if ((s = device_input(p, 0, fhat, (size_t)p->M * cplx_size(p), &fd)) != NFFT_OK) return s;
   if ((s = device_output(p, 1, y, (size_t)prod_N(p) * cplx_size(p), &ob)) != NFFT_OK) return s;
-  if ((s = run_scatter(p, fd)) != NFFT_OK) return s;
-  if ((s = run_fft_crop(p, ob.dev)) != NFFT_OK) return s;
+  if (fd == fhat && !ob.host) return run_direction(p, 1, fd, ob.dev);
+  if ((s = run_plain(p, 1, fd, ob.dev)) != NFFT_OK) return s;
   return finish_output(p, ob);
 }
 
@@ -904,6 +1008,15 @@ int nfft_step_fft_crop(nfft_plan* p, void* y) {
   if (!y) return NFFT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
   return run_fft_crop(p, y);
+}
+
+int nfft_plan_set_graph(nfft_plan* p, int enable) {
+  int s;
+  if (!ready(p, &s)) return s;
+  DeviceGuard guard(p->device);
+  if (!enable) drop_graphs(p);
+  p->graph_mode = enable != 0;
+  return NFFT_OK;
 }
 
 int nfft_plan_paths(nfft_plan* p, int* fast_resample, int* pruned_fft) {

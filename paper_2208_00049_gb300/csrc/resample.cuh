@@ -77,32 +77,103 @@ __device__ __forceinline__ int64_t region_to_grid(const Geometry& g, const int* 
   return lin;
 }
 
+// LINEAR window (Sec. 3.7.4, Eq. linInterp): kappa = |u| (S - 2)/m, s =
+// floor(kappa), alpha = kappa - s, w = tab[s] + alpha (tab[s + 1] - tab[s]);
+// (S - 2)/m is a power of two, so kappa is |u| scaled exactly.  Also returns
+// the slope of the segment in *slope (d w / d|u|).
+template <typename R>
+__device__ __forceinline__ R lut_window(const R* __restrict__ tab, int S, R scale, R u, R* slope) {
+  const R kappa = fabs(u) * scale;
+  int s = (int)kappa;
+  s = s < S - 2 ? s : S - 2;
+  const R alpha = kappa - R(s);
+  const R lo = tab[s], hi = tab[s + 1];
+  if (slope) *slope = (hi - lo) * scale;
+  return lo + alpha * (hi - lo);
+}
+
+// Window values of the table modes (kWinLinear, kWinPoly) for the K taps of
+// one dimension, and their derivatives d/dk if dw != nullptr.  Out of line:
+// the modes share one copy instead of being inlined at every call site of
+// the unrolled kernels.
+template <int K, typename R>
+__device__ __noinline__ void table_weights(const Geometry& g, int d, int mi, R t, R* w, R* dw) {
+  if (g.wmode == kWinLinear) {
+    const R* tab = (const R*)g.wtab + (int64_t)d * g.wS;
+    const R scale = R(g.wS - 2) / R(mi);
+    for (int i = 0; i < K; ++i) {
+      const R u = R(-g.off - i) + t;
+      R slope;
+      R v = lut_window<R>(tab, g.wS, scale, u, &slope);
+      R dv = (u < R(0) ? -slope : slope) * R(g.Nt[d]);
+      if (g.closed && ((i == 0 && t != R(0)) || i == K - 1)) v = dv = R(0);
+      w[i] = v;
+      if (dw) dw[i] = dv;
+    }
+  } else {
+    const int Z = 2 * mi + 1;
+    const R* pc = (const R*)g.wtab + (int64_t)d * K * Z;
+    const R zeta = t - R(0.5);
+    for (int i = 0; i < K; ++i) {
+      R v = pc[i * Z + Z - 1], dv = R(0);
+      for (int z = Z - 2; z >= 0; --z) {
+        dv = dv * zeta + v;
+        v = v * zeta + pc[i * Z + z];
+      }
+      w[i] = v;
+      if (dw) dw[i] = dv * R(g.Nt[d]);
+    }
+  }
+}
+
 // Local weight vector psi^local_{d,j} (Eq. InnerTensorStructure) for one
-// dimension: tap i sits at l' = c + off + i, u = t - off - i.
+// dimension: tap i sits at l' = c + off + i, u = t - off - i.  The window
+// values are evaluated (kWinDirect), looked up in the LINEAR table
+// (kWinLinear) or taken from the POLYNOMIAL coefficients of tap i
+// (kWinPoly, Horner in zeta = t - 1/2).
 template <int K, typename R>
 __device__ __forceinline__ void node_weights(const Geometry& g, int d, int mi, R t, R* w) {
-  const R b = R(g.b[d]), norm = R(g.norm[d]);
+  if (g.wmode != kWinDirect) {
+    R tmp[K];
+    table_weights<K, R>(g, d, mi, t, tmp, nullptr);
+#pragma unroll
+    for (int i = 0; i < K; ++i) w[i] = tmp[i];
+    return;
+  }
+  const R b = R(g.b[d]), norm = R(g.norm[d]), mr = R(mi);
+  const R normx = sizeof(R) == 4 ? kb_normx<R>(b, mr) : R(0);
 #pragma unroll
   for (int i = 0; i < K; ++i) {
+    R u = R(-g.off - i) + t;
     R mm_u = R(mi + g.off + i) - t;  // m - u
     R mp_u = R(mi - g.off - i) + t;  // m + u
-    R v = kb_window<R>(mm_u, mp_u, b, norm);
+    R v = kb_window<R>(u, mm_u, mp_u, b, norm, mr, normx);
     if (g.closed && ((i == 0 && t != R(0)) || i == K - 1)) v = R(0);
     w[i] = v;
   }
 }
 
-// d/dk of the local weights: N~_d * w'(u).
+// d/dk of the local weights: N~_d * w'(u) (for the LINEAR window the slope
+// of the interpolant's segment, for the POLYNOMIAL one the derivative of the
+// polynomial, d/du = d/dzeta).
 template <int K, typename R>
 __device__ __forceinline__ void node_weight_derivs(const Geometry& g, int d, int mi, R t, R* dw) {
-  const R b = R(g.b[d]), norm = R(g.norm[d]) * R(g.Nt[d]);
+  if (g.wmode != kWinDirect) {
+    R tmp[K], dtmp[K];
+    table_weights<K, R>(g, d, mi, t, tmp, dtmp);
+#pragma unroll
+    for (int i = 0; i < K; ++i) dw[i] = dtmp[i];
+    return;
+  }
+  const R b = R(g.b[d]), norm = R(g.norm[d]) * R(g.Nt[d]), mr = R(mi);
+  const R normx = sizeof(R) == 4 ? kb_normx<R>(b, mr) * R(g.Nt[d]) : R(0);
   const R zsmall = sizeof(R) == 4 ? R(0.5) : R(0.05);
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     R u = R(-g.off - i) + t;
     R mm_u = R(mi + g.off + i) - t;
     R mp_u = R(mi - g.off - i) + t;
-    R v = kb_window_deriv<R>(u, mm_u, mp_u, b, norm, zsmall);
+    R v = kb_window_deriv<R>(u, mm_u, mp_u, b, norm, zsmall, mr, normx);
     if (g.closed && ((i == 0 && t != R(0)) || i == K - 1)) v = R(0);
     dw[i] = v;
   }
@@ -485,12 +556,17 @@ __global__ void __launch_bounds__(kResampleThreads)
   X(1, 2) X(1, 4) X(1, 6) X(1, 8) X(1, 10) X(1, 12) X(1, 14) X(1, 16) X(1, 18) \
   X(2, 2) X(2, 4) X(2, 6) X(2, 8) X(2, 10) X(2, 12) X(2, 14) X(2, 16) X(2, 18) \
   X(3, 2) X(3, 4) X(3, 6) X(3, 8) X(3, 10) X(3, 12) X(3, 14) X(3, 16) X(3, 18)
+// m = 9, 10 (K = 20, 22) for the plain gather and scatter in 1D and 2D only,
+// where the paper's accuracy study runs: instantiating every kind and 3D as
+// well would triple the build time.
+#define NFFTGB_FOR_EACH_DK_HIGH_M(X) X(1, 20) X(1, 22) X(2, 20) X(2, 22)
 
 template <typename R>
 void* pick_gather(int D, int K) {
 #define NFFTGB_PICK(DD, KK) \
   if (D == DD && K == KK) return (void*)gather_kernel<DD, KK, R>;
   NFFTGB_FOR_EACH_DK(NFFTGB_PICK)
+  NFFTGB_FOR_EACH_DK_HIGH_M(NFFTGB_PICK)
 #undef NFFTGB_PICK
   return nullptr;
 }
@@ -505,6 +581,10 @@ void* pick_scatter(int D, int K, int compensated) {
     return compensated ? nullptr : (void*)scatter_kernel<DD, KK, R, false>;  \
   }
   NFFTGB_FOR_EACH_DK(NFFTGB_PICK)
+#undef NFFTGB_PICK
+#define NFFTGB_PICK(DD, KK) \
+  if (D == DD && K == KK && !compensated) return (void*)scatter_kernel<DD, KK, R, false>;
+  NFFTGB_FOR_EACH_DK_HIGH_M(NFFTGB_PICK)
 #undef NFFTGB_PICK
   return nullptr;
 }

@@ -96,9 +96,15 @@ struct Stage2d {
   Poly2d pc;
 };
 
-template <int A0>
+// Compensation terms (COMP: one per accumulator, TwoSum; else unused).
+template <bool COMP>
+struct Comp2d {
+  f32x2 c[COMP ? k2Lines : 1];
+};
+
+template <int A0, bool COMP>
 __device__ __forceinline__ void scatter2d_bin(const Stage2d& st, int s0, int s1, int lane,
-                                              f32x2 (&acc)[k2Lines]) {
+                                              f32x2 (&acc)[k2Lines], Comp2d<COMP>& cp) {
   if constexpr (A0 + k2Taps <= k2Lines) {
     for (int s = s0; s < s1; ++s) {
       const int i1 = lane - st.a1[s];
@@ -109,16 +115,21 @@ __device__ __forceinline__ void scatter2d_bin(const Stage2d& st, int s0, int s1,
 #pragma unroll
       for (int q = 0; q < k2Taps / 4; ++q) {
         const float4 x = wq[q];
-        acc[A0 + 4 * q] = fma2(vp, pack2(x.x, x.x), acc[A0 + 4 * q]);
-        acc[A0 + 4 * q + 1] = fma2(vp, pack2(x.y, x.y), acc[A0 + 4 * q + 1]);
-        acc[A0 + 4 * q + 2] = fma2(vp, pack2(x.z, x.z), acc[A0 + 4 * q + 2]);
-        acc[A0 + 4 * q + 3] = fma2(vp, pack2(x.w, x.w), acc[A0 + 4 * q + 3]);
+        const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if constexpr (COMP)
+            two_sum_acc2(acc[A0 + 4 * q + j], cp.c[A0 + 4 * q + j], mul2(vp, pack2(xs[j], xs[j])));
+          else
+            acc[A0 + 4 * q + j] = fma2(vp, pack2(xs[j], xs[j]), acc[A0 + 4 * q + j]);
+        }
       }
     }
   }
 }
 
 // One work item of one problem, by one warp.
+template <bool COMP>
 __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __restrict__ grid,
                                                const int* __restrict__ cell, const float* __restrict__ frac,
                                                const int* __restrict__ perm, const float2* __restrict__ fhat,
@@ -130,8 +141,13 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
   const int start0 = tc[0] * g.T[0] + g.off, start1 = tc[1] * g.T[1] + g.off;
   const unsigned lt = (1u << lane) - 1u;
   f32x2 acc[k2Lines];
+  Comp2d<COMP> cp;
 #pragma unroll
   for (int r = 0; r < k2Lines; ++r) acc[r] = pack2(0.f, 0.f);
+  if constexpr (COMP) {
+#pragma unroll
+    for (int r = 0; r < k2Lines; ++r) cp.c[r] = pack2(0.f, 0.f);
+  }
   Chunk2d next;
   next.load(cell, frac, perm, M, item, 0, lane);
   __syncwarp();  // the previous item's coefficients are no longer read
@@ -168,15 +184,19 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
       st.a1[slot] = cur.c1 - tc[1] * g.T[1];
     }
     __syncwarp();
-    scatter2d_bin<0>(st, bs[0], bs[1], lane, acc);
-    scatter2d_bin<1>(st, bs[1], bs[2], lane, acc);
-    scatter2d_bin<2>(st, bs[2], bs[3], lane, acc);
-    scatter2d_bin<3>(st, bs[3], bs[4], lane, acc);
-    scatter2d_bin<4>(st, bs[4], bs[5], lane, acc);
-    scatter2d_bin<5>(st, bs[5], bs[6], lane, acc);
-    scatter2d_bin<6>(st, bs[6], bs[7], lane, acc);
-    scatter2d_bin<7>(st, bs[7], bs[8], lane, acc);
-    scatter2d_bin<8>(st, bs[8], bs[9], lane, acc);
+    scatter2d_bin<0, COMP>(st, bs[0], bs[1], lane, acc, cp);
+    scatter2d_bin<1, COMP>(st, bs[1], bs[2], lane, acc, cp);
+    scatter2d_bin<2, COMP>(st, bs[2], bs[3], lane, acc, cp);
+    scatter2d_bin<3, COMP>(st, bs[3], bs[4], lane, acc, cp);
+    scatter2d_bin<4, COMP>(st, bs[4], bs[5], lane, acc, cp);
+    scatter2d_bin<5, COMP>(st, bs[5], bs[6], lane, acc, cp);
+    scatter2d_bin<6, COMP>(st, bs[6], bs[7], lane, acc, cp);
+    scatter2d_bin<7, COMP>(st, bs[7], bs[8], lane, acc, cp);
+    scatter2d_bin<8, COMP>(st, bs[8], bs[9], lane, acc, cp);
+  }
+  if constexpr (COMP) {
+#pragma unroll
+    for (int r = 0; r < k2Lines; ++r) acc[r] = add2(acc[r], cp.c[r]);
   }
 
   if (lane < g.L[1]) {
@@ -192,8 +212,10 @@ __device__ __forceinline__ void scatter2d_item(const Geometry& g, float2* __rest
 }
 
 // 5 CTAs per SM (96 registers): measured faster than the 4 the compiler
-// would otherwise allow with the chunk prefetch's registers.
-__global__ void __launch_bounds__(k2Threads, 5)
+// would otherwise allow with the chunk prefetch's registers.  The compensated
+// form (NFFT_FLAG_COMPENSATED) holds twice the accumulators: 3 CTAs per SM.
+template <bool COMP>
+__global__ void __launch_bounds__(k2Threads, COMP ? 3 : 5)
     scatter2d_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na, const float* __restrict__ poly,
                             const float2* __restrict__ fhat) {
   __shared__ Stage2d stage[k2Warps];
@@ -201,7 +223,7 @@ __global__ void __launch_bounds__(k2Threads, 5)
   const int nitems = *na.n_items;
   const float* frac = reinterpret_cast<const float*>(na.frac);
   for (int it = blockIdx.x * k2Warps + warp; it < nitems; it += gridDim.x * k2Warps)
-    scatter2d_item(g, grid, na.cell, frac, na.perm, fhat, poly, na.items[it], stage[warp], lane);
+    scatter2d_item<COMP>(g, grid, na.cell, frac, na.perm, fhat, poly, na.items[it], stage[warp], lane);
 }
 
 __global__ void __launch_bounds__(k2Threads, 5)
@@ -214,8 +236,8 @@ __global__ void __launch_bounds__(k2Threads, 5)
   for (int it = blockIdx.x * k2Warps + warp; it < nitems; it += gridDim.x * k2Warps) {
     const int4 item = nb.items[it];
     const BatchProblem& P = probs[item.w];
-    scatter2d_item(P.g, grid + P.grid_off, nb.cell + 2 * P.node_off, frac + 2 * P.node_off,
-                   nb.perm + P.node_off, fhat + P.out_off, poly + P.poly_off, item, stage[warp], lane);
+    scatter2d_item<false>(P.g, grid + P.grid_off, nb.cell + 2 * P.node_off, frac + 2 * P.node_off,
+                          nb.perm + P.node_off, fhat + P.out_off, poly + P.poly_off, item, stage[warp], lane);
   }
 }
 
@@ -311,16 +333,19 @@ bool scatter2d_supported(const Geometry& g) {
          g.T[1] <= g.Nt[1] - k2Taps + 1;
 }
 
-int scatter2d_ctas_per_sm() {
+int scatter2d_ctas_per_sm(int compensated) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scatter2d_regacc_kernel, k2Threads, 0) != cudaSuccess)
-    return 0;
+  const void* k = compensated ? (const void*)scatter2d_regacc_kernel<true> : (const void*)scatter2d_regacc_kernel<false>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, k2Threads, 0) != cudaSuccess) return 0;
   return n;
 }
 
 cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArrays& na, const float* poly,
-                                  const void* fhat, int ctas, cudaStream_t s) {
-  scatter2d_regacc_kernel<<<ctas, k2Threads, 0, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
+                                  const void* fhat, int compensated, int ctas, cudaStream_t s) {
+  if (compensated)
+    scatter2d_regacc_kernel<true><<<ctas, k2Threads, 0, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
+  else
+    scatter2d_regacc_kernel<false><<<ctas, k2Threads, 0, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
   return cudaGetLastError();
 }
 

@@ -741,9 +741,16 @@ struct RegAccStage {
   f32x2 coef[3][kPairs][K + 1];          // (tap 2 tp, tap 2 tp + 1) coefficient pairs, degree K
 };
 
-template <int A0, int K>
+// Compensation terms of the accumulators (COMP: one per accumulator; else
+// one unused register pair).
+template <bool COMP>
+struct RegAccComp {
+  f32x2 c[COMP ? 2 : 1][COMP ? kRegAccLines : 1];
+};
+
+template <int A0, int K, bool COMP>
 __device__ __forceinline__ void regacc_node(const RegAccStage<K>& st, int s, int r1, int cc,
-                                            f32x2 (&acc)[2][kRegAccLines]) {
+                                            f32x2 (&acc)[2][kRegAccLines], RegAccComp<COMP>& cp) {
   const f32x2 vw = st.vw1[s][r1];
   const float2 w2 = st.w2s[s][cc];
   const f32x2 vp0 = mul2(vw, pack2(w2.x, w2.x));
@@ -756,28 +763,36 @@ __device__ __forceinline__ void regacc_node(const RegAccStage<K>& st, int s, int
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const f32x2 wa = pack2(xs[j], xs[j]);
-      acc[0][A0 + 4 * q + j] = fma2(vp0, wa, acc[0][A0 + 4 * q + j]);
-      acc[1][A0 + 4 * q + j] = fma2(vp1, wa, acc[1][A0 + 4 * q + j]);
+      if constexpr (COMP) {
+        two_sum_acc2(acc[0][A0 + 4 * q + j], cp.c[0][A0 + 4 * q + j], mul2(vp0, wa));
+        two_sum_acc2(acc[1][A0 + 4 * q + j], cp.c[1][A0 + 4 * q + j], mul2(vp1, wa));
+      } else {
+        acc[0][A0 + 4 * q + j] = fma2(vp0, wa, acc[0][A0 + 4 * q + j]);
+        acc[1][A0 + 4 * q + j] = fma2(vp1, wa, acc[1][A0 + 4 * q + j]);
+      }
     }
   }
 }
 
-template <int A0, int K>
+template <int A0, int K, bool COMP>
 __device__ __forceinline__ void regacc_bin(const RegAccStage<K>& st, int lo, int hi, int r1, int cc,
-                                           f32x2 (&acc)[2][kRegAccLines]) {
+                                           f32x2 (&acc)[2][kRegAccLines], RegAccComp<COMP>& cp) {
   if constexpr (A0 + K <= kRegAccLines) {  // a0 < T0 <= 17 - K
     const int s0 = st.start[A0 * kRegAccA + lo], s1 = st.start[A0 * kRegAccA + hi + 1];
     int s = s0;
     for (; s + 1 < s1; s += 2) {
-      regacc_node<A0, K>(st, s, r1, cc, acc);
-      regacc_node<A0, K>(st, s + 1, r1, cc, acc);
+      regacc_node<A0, K, COMP>(st, s, r1, cc, acc, cp);
+      regacc_node<A0, K, COMP>(st, s + 1, r1, cc, acc, cp);
     }
-    if (s < s1) regacc_node<A0, K>(st, s, r1, cc, acc);
+    if (s < s1) regacc_node<A0, K, COMP>(st, s, r1, cc, acc, cp);
   }
 }
 
-template <int K>
-__global__ void __launch_bounds__(kRegAccThreads, 4)
+// COMP (NFFT_FLAG_COMPENSATED): every accumulator carries the running sum of
+// the rounding errors of its additions (TwoSum), added back at the flush;
+// twice the accumulator registers, so two CTAs per SM instead of four.
+template <int K, bool COMP>
+__global__ void __launch_bounds__(kRegAccThreads, COMP ? 2 : 4)
     scatter3d_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na,
                             const float* __restrict__ poly, const float2* __restrict__ fhat) {
   using Stage = RegAccStage<K>;
@@ -897,19 +912,32 @@ __global__ void __launch_bounds__(kRegAccThreads, 4)
     for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;  // for the next item
 
     f32x2 acc[2][kRegAccLines];
+    RegAccComp<COMP> cp;
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int r = 0; r < kRegAccLines; ++r) acc[h][r] = pack2(0.f, 0.f);
-    regacc_bin<0, K>(st, lo, hi, r1, cc, acc);
-    regacc_bin<1, K>(st, lo, hi, r1, cc, acc);
-    regacc_bin<2, K>(st, lo, hi, r1, cc, acc);
-    regacc_bin<3, K>(st, lo, hi, r1, cc, acc);
-    regacc_bin<4, K>(st, lo, hi, r1, cc, acc);
-    regacc_bin<5, K>(st, lo, hi, r1, cc, acc);
-    regacc_bin<6, K>(st, lo, hi, r1, cc, acc);
-    regacc_bin<7, K>(st, lo, hi, r1, cc, acc);
-    regacc_bin<8, K>(st, lo, hi, r1, cc, acc);
+    if constexpr (COMP) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < kRegAccLines; ++r) cp.c[h][r] = pack2(0.f, 0.f);
+    }
+    regacc_bin<0, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    regacc_bin<1, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    regacc_bin<2, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    regacc_bin<3, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    regacc_bin<4, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    regacc_bin<5, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    regacc_bin<6, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    regacc_bin<7, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    regacc_bin<8, K, COMP>(st, lo, hi, r1, cc, acc, cp);
+    if constexpr (COMP) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < kRegAccLines; ++r) acc[h][r] = add2(acc[h][r], cp.c[h][r]);
+    }
 
     // add the region to the grid (periodic wrap only here)
 #pragma unroll
@@ -955,8 +983,9 @@ bool fast_scatter_supported(const Geometry& g, int cmax) { return cmax <= kItemC
 
 namespace {
 
-void* regacc_kernel(int K) {
-  return K == 12 ? (void*)scatter3d_regacc_kernel<12> : (void*)scatter3d_regacc_kernel<8>;
+void* regacc_kernel(int K, bool comp) {
+  if (comp) return K == 12 ? (void*)scatter3d_regacc_kernel<12, true> : (void*)scatter3d_regacc_kernel<8, true>;
+  return K == 12 ? (void*)scatter3d_regacc_kernel<12, false> : (void*)scatter3d_regacc_kernel<8, false>;
 }
 size_t regacc_smem(int K) { return K == 12 ? sizeof(RegAccStage<12>) : sizeof(RegAccStage<8>); }
 
@@ -1076,9 +1105,18 @@ bool fast3d_supported(const Geometry& g, int cmax) {
 }
 
 int fast3d_ctas_per_sm(const Geometry& g, int kind) {
+  if (kind == 2) {  // compensated scatter: the register-accumulating form only
+    if (!regacc_supported(g)) return 0;
+    const size_t smem = regacc_smem(g.K);
+    void* k = regacc_kernel(g.K, true);
+    if (set_smem(k, smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
+    return n;
+  }
   if (kind == 1 && use_regacc(g)) {
     const size_t smem = regacc_smem(g.K);
-    void* k = regacc_kernel(g.K);
+    void* k = regacc_kernel(g.K, false);
     if (set_smem(k, smem) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
@@ -1145,10 +1183,10 @@ int grad3d_ctas_per_sm(const Geometry& g) {
 }
 
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
-                                  const float* poly, const void* fhat, int ctas, cudaStream_t s) {
-  if (use_regacc(g)) {
+                                  const float* poly, const void* fhat, int compensated, int ctas, cudaStream_t s) {
+  if (compensated || use_regacc(g)) {
     const size_t smem = regacc_smem(g.K);
-    void* k = regacc_kernel(g.K);
+    void* k = regacc_kernel(g.K, compensated != 0);
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
     auto kern = reinterpret_cast<void (*)(Geometry, float2*, NodeArrays, const float*, const float2*)>(k);

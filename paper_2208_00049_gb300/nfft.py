@@ -184,6 +184,10 @@ class Plan:
         B.check(B.nfft_step_fft_crop(self.handle, _ptr(out)), "nfft_step_fft_crop")
         return out
 
+    def set_graph(self, enable=True):
+        """Replay nfft_forward / nfft_adjoint from captured CUDA graphs (device buffers)."""
+        B.check(B.nfft_plan_set_graph(self.handle, enable), "nfft_plan_set_graph")
+
     def paths(self):
         """{'fast_gather', 'fast_scatter', 'pruned_fft'}: which specialised
         kernels this plan's transforms run."""

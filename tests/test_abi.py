@@ -57,15 +57,22 @@ def test_status_strings_and_argument_validation(built_lib):
         dict(D=1, N=(1,), M=4, sigma=2.0, m=4, dtype=0, flags=0),
         dict(D=1, N=(16,), M=4, sigma=1.0, m=4, dtype=0, flags=0),
         dict(D=1, N=(16,), M=4, sigma=2.0, m=0, dtype=0, flags=0),
-        dict(D=1, N=(16,), M=4, sigma=2.0, m=9, dtype=0, flags=0),
+        dict(D=1, N=(40,), M=4, sigma=2.0, m=11, dtype=0, flags=0),
         dict(D=1, N=(4,), M=4, sigma=2.0, m=4, dtype=0, flags=0),   # 2m >= N~
         dict(D=1, N=(16,), M=-1, sigma=2.0, m=4, dtype=0, flags=0),
         dict(D=1, N=(16,), M=4, sigma=2.0, m=4, dtype=7, flags=0),
-        dict(D=1, N=(16,), M=4, sigma=2.0, m=4, dtype=0, flags=0x80),
+        dict(D=1, N=(16,), M=4, sigma=2.0, m=4, dtype=0, flags=0x100),
+        dict(D=1, N=(16,), M=4, sigma=2.0, m=4, dtype=0, flags=0x60),   # two window modes
+        dict(D=1, N=(16,), M=4, sigma=2.0, m=4, dtype=0, flags=0x48),   # LINEAR with the wide window
+        dict(D=1, N=(16,), M=4, sigma=2.0, m=4, dtype=0, flags=0x81),   # POLYNOMIAL with closed support
+        dict(D=1, N=(16,), M=4, sigma=2.0, m=4, dtype=0, flags=0x24),   # window mode with FULL_MATRIX
     ]
     for a in bad:
         s, h = B.nfft_plan_create(a["D"], a["N"], a["M"], a["sigma"], a["m"], a["dtype"], a["flags"], None)
         assert s == B.NFFT_ERR_INVALID_ARG and h is None, a
+    # m = 9, 10 are built for 1D and 2D only
+    s, h = B.nfft_plan_create(3, (24, 24, 24), 4, 2.0, 9, 0, 0, None)
+    assert s == B.NFFT_ERR_UNSUPPORTED and h is None
     # null plan handles are rejected, destroy(NULL) is a no-op
     assert B.nfft_forward(None, None, None) == B.NFFT_ERR_INVALID_ARG
     assert B.nfft_set_nodes(None, None, 1) == B.NFFT_ERR_INVALID_ARG

@@ -11,10 +11,11 @@ import pytest
 
 from oracle import ndft as ondft
 from oracle import nfft as onfft
+from oracle import window as owin
 from paper_2208_00049_gb300 import inputs
 
-from gpu_helpers import (TOL, assert_close, cdtype, fp32_floor, oracle_spread_box, rel_l2, require_gpu, to_dev,
-                         tol_for, tol_max_for)
+from gpu_helpers import (TOL, assert_close, cdtype, fp32_floor, oracle_spread_box, rel_l2, rel_max, require_gpu,
+                         to_dev, tol_for, tol_max_for)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -197,8 +198,10 @@ def test_workload3_adjoint_steps(name):
         # numpy's: the floor is cuFFT's own inverse FFT of the same grid, and
         # the crop and correction may add little to it
         g32 = torch.fft.ifftn(grid_t, norm="forward").cpu().numpy()
-    floor = rel_l2(onfft.crop_correction(p, g32.astype(np.complex128)) * peak, want_y)
-    assert_close(y, want_y, max(TOL["c64"], (3 if pruned else 1.5) * floor), "inverse FFT + crop + correction")
+    y_floor = onfft.crop_correction(p, g32.astype(np.complex128)) * peak
+    f = 3 if pruned else 1.5
+    assert_close(y, want_y, max(TOL["c64"], f * rel_l2(y_floor, want_y)), "inverse FFT + crop + correction",
+                 tol_max=max(10 * TOL["c64"], f * rel_max(y_floor, want_y)))
 
 
 def test_radial_set_on_grid_nodes():
@@ -335,6 +338,37 @@ def test_compensated_scatter():
     e1 = assert_close(y1, want, 1e-5, "compensated")
     assert_close(y2, want, 1e-5, "default plan")
     assert e1 <= 1.5 * e0 + 1e-7
+
+
+@pytest.mark.parametrize("N,M", [((32, 32), 200000), ((16, 16, 16), 100000)])
+def test_compensated_fast_scatter(N, M):
+    """NFFT_FLAG_COMPENSATED on the register-accumulating complex64 scatters
+    (2D and 3D, m = 4), with thousands of terms per grid point: the
+    compensated grid is closer to the FP64 oracle's adjoint resampling step
+    than the plain one, and both adjoint transforms are within the target.
+    (Only the sums held in registers are compensated: the partial sums of
+    neighbouring tiles still meet in FP32 global reductions, and the FP32
+    products and window values set a floor, so the gain is bounded.)"""
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300.nfft import Plan
+    case = inputs.small_case(N, M, seed=17, m=4)
+    p = onfft.Params(N, 2.0, 4)
+    peak = np.prod([float(onfft.psi(0.0, 4, b)) for b in p.b])
+    w32 = case["w"].astype(np.complex64)
+    want = onfft.resample_adjoint(p, case["k"], w32.astype(np.complex128))
+    want_y = onfft.adjoint(case["k"], w32.astype(np.complex128), N, 2.0, 4)
+    errs = {}
+    for flags in (0, B.NFFT_FLAG_COMPENSATED):
+        plan = Plan(N, M, sigma=2.0, m=4, dtype=torch.complex64, flags=flags)
+        plan.set_nodes(to_dev(case["k"], torch.float64))
+        assert plan.paths()["fast_scatter"]
+        w = torch.from_numpy(w32).cuda()
+        plan.step_scatter(w)
+        errs[flags] = rel_l2(plan.grid_tensor().cpu().numpy() * peak, want)
+        y = plan.adjoint(w).cpu().numpy()
+        plan.close()
+        assert_close(y, want_y, 1e-5, "adjoint flags=%d" % flags)
+    assert errs[B.NFFT_FLAG_COMPENSATED] <= 0.85 * errs[0], errs
 
 
 def test_steps_match_oracle_steps():
@@ -561,3 +595,99 @@ def test_accuracy_study_against_ndft():
     for m in range(2, 6):
         assert wide[m] < errs[m]
         assert errs[m + 1] < wide[m]
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("N,M,m", [((300,), 700, 4), ((40, 36), 2500, 4), ((20, 18, 16), 3000, 4),
+                                   ((24, 20), 2000, 6)])
+def test_window_modes_match_oracle(N, M, m, dt):
+    """The three window modes of Sec. 3.7.4 on the same (generic) kernels:
+    DIRECT and LINEAR against the oracle with the same window reading (the
+    LINEAR table read with linear interpolation on both sides), POLYNOMIAL
+    against the evaluated window within its fit error (degree 2m: about
+    1e-8 of the peak at m = 4, FP64-level from m = 6)."""
+    from paper_2208_00049_gb300 import binding as B
+    case = inputs.small_case(N, M, seed=83, m=m)
+    for flag, win, tol in ((B.NFFT_FLAG_WINDOW_DIRECT, "direct", TOL[dt]),
+                           (B.NFFT_FLAG_WINDOW_LINEAR, "linear", TOL[dt]),
+                           (B.NFFT_FLAG_WINDOW_POLYNOMIAL, "direct", max(TOL[dt], 1e-7 if m < 6 else 1e-12))):
+        fh, y = _run(case, dt, flags=flag)
+        assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, m, window=win), tol, "forward %s" % win)
+        assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, m, window=win), tol, "adjoint %s" % win)
+
+
+def test_linear_window_node_gradient():
+    """The node gradient with the LINEAR window: the derivative of the
+    interpolant (its segment's slope), as in the oracle's reading."""
+    from paper_2208_00049_gb300 import binding as B
+    N, M = (24, 20), 1500
+    case = inputs.small_case(N, M, seed=89, m=4)
+    plan = _plan(N, M, 2.0, 4, "c128", flags=B.NFFT_FLAG_WINDOW_LINEAR)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    gk = plan.grad(to_dev(case["f"], torch.complex128), to_dev(case["w"], torch.complex128)).cpu().numpy()
+    plan.close()
+    want = onfft.node_grad(case["k"], case["f"], case["w"], 2.0, 4, window="linear")
+    # The slope is the difference of two adjacent table entries divided by
+    # the spacing m / (S - 2): last-bit differences between the two tables
+    # (CUDA's and numpy's sinh) grow by (S - 2) / m, S = 4 * 2^14 + 2.
+    S = owin.lut_size(4)
+    tol = 4 * np.finfo(np.float64).eps * (S - 2) / 4
+    assert_close(gk, want, tol, "node gradient (LINEAR)")
+
+
+@pytest.mark.parametrize("N,M,m", [((40, 36), 2000, 9), ((44, 40), 2000, 10), ((300,), 600, 10)])
+def test_high_m_against_oracle(N, M, m):
+    """m = 9, 10 (the end of the paper's accuracy curves) in 1D and 2D,
+    complex128, against the oracle; 3D reports NFFT_ERR_UNSUPPORTED there,
+    and so does the node gradient at m = 10 (2m = 20 taps)."""
+    from paper_2208_00049_gb300 import binding as B
+    case = inputs.small_case(N, M, seed=97, m=m)
+    fh, y = _run(case, "c128")
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, m), 1e-12, "forward m=%d" % m)
+    assert_close(y, onfft.adjoint(case["k"], case["w"], N, 2.0, m), 1e-12, "adjoint m=%d" % m)
+    s, h = B.nfft_plan_create(3, (24, 24, 24), 100, 2.0, 9, B.NFFT_C128, 0, None)
+    assert s == B.NFFT_ERR_UNSUPPORTED and not h
+    plan = _plan(N, M, 2.0, m, "c128")
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    fd, wd = to_dev(case["f"], torch.complex128), to_dev(case["w"], torch.complex128)
+    if m == 9:
+        gk = plan.grad(fd, wd).cpu().numpy()
+        assert_close(gk, onfft.node_grad(case["k"], case["f"], case["w"], 2.0, m), 1e-12, "node gradient m=9")
+    else:
+        with pytest.raises(B.NFFTError):
+            plan.grad(fd, wd)
+    plan.close()
+
+
+@pytest.mark.parametrize("N,M,dt", [((256,), 1024, "c128"), ((64, 48), 3000, "c64"), ((20, 18, 16), 3000, "c64"),
+                                    ((128, 128, 128), 20000, "c64")])
+def test_graph_replay_matches_direct_path(N, M, dt):
+    """nfft_plan_set_graph: forward and adjoint replayed from captured graphs
+    give the direct path's results, follow new input data in the same
+    buffers, re-capture for new buffers, and survive nfft_set_nodes."""
+    case = inputs.small_case(N, M, seed=101, m=4)
+    plan = _plan(N, M, 2.0, 4, dt)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    f = to_dev(case["f"], cdtype(dt))
+    w = to_dev(case["w"], cdtype(dt))
+    want_f = plan.forward(f).cpu().numpy()
+    want_a = plan.adjoint(w).cpu().numpy()
+    plan.set_graph(True)
+    fh = torch.empty(M, dtype=cdtype(dt), device="cuda")
+    y = torch.empty(N, dtype=cdtype(dt), device="cuda")
+    for _ in range(3):
+        plan.forward(f, out=fh)
+        plan.adjoint(w, out=y)
+    assert_close(fh.cpu().numpy(), want_f, 1e-6 if dt == "c64" else 1e-14, "graph forward")
+    assert_close(y.cpu().numpy(), want_a, 1e-6 if dt == "c64" else 1e-14, "graph adjoint")
+    f.mul_(2)                                   # new data, same buffers: the replay reads it
+    plan.forward(f, out=fh)
+    assert_close(fh.cpu().numpy(), 2 * want_f, 1e-6 if dt == "c64" else 1e-14, "graph forward, new data")
+    fh2 = torch.empty_like(fh)                  # new buffers: re-captured
+    plan.forward(f, out=fh2)
+    assert_close(fh2.cpu().numpy(), 2 * want_f, 1e-6 if dt == "c64" else 1e-14, "graph forward, new buffers")
+    k2 = inputs.small_case(N, M, seed=103, m=4)["k"]
+    plan.set_nodes(to_dev(k2, torch.float64))   # new nodes, same node buffers
+    plan.forward(f, out=fh)
+    assert_close(fh.cpu().numpy(), onfft.forward(k2, 2 * case["f"], 2.0, 4), TOL[dt], "graph after set_nodes")
+    plan.close()

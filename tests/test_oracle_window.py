@@ -174,3 +174,47 @@ def test_untruncated_window_is_one_entire_function(m, sigma):
     got = window.psi_full(u, m, b)
     assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
 
+
+
+@pytest.mark.parametrize("m", [2, 3, 4, 5])
+def test_linear_table_lookup(m):
+    """LINEAR (Sec. 3.7.4): exact at the table's sample points u = m s/(S-2),
+    linear between them, the edge entry S-2 holds b/pi (read by the tap at
+    u = -m through |u|), entry S-1 is 0, and the interpolation error stays
+    within the linear-interpolation bound h^2/8 max|psi''| (h = m/(S-2))."""
+    b = window.kb_shape(32, 64)
+    S = window.lut_size(m)
+    h = m / (S - 2.0)
+    s = np.array([0, 1, 7, (S - 2) // 3, S - 3, S - 2])
+    assert np.allclose(window.psi_linear(s * h, m, b), window.psi(s * h, m, b), rtol=0, atol=1e-15)
+    assert window.lut_entry(S - 2, m, b) == pytest.approx(b / np.pi, rel=1e-15)
+    assert window.lut_entry(S - 1, m, b) == 0.0
+    assert window.psi_linear(-float(m), m, b) == pytest.approx(b / np.pi, rel=1e-15)
+    mid = (s[:-1] + 0.5) * h
+    avg = 0.5 * (window.psi(s[:-1] * h, m, b, closed=True) + window.psi((s[:-1] + 1) * h, m, b, closed=True))
+    assert np.allclose(window.psi_linear(mid, m, b), avg, rtol=0, atol=1e-15)
+    assert np.allclose(window.psi_linear(-mid, m, b), avg, rtol=0, atol=1e-15)
+    u = np.linspace(-m, m, 200001)[:-1]
+    fd2 = np.abs(np.diff(window.psi(u, m, b), 2)) / (u[1] - u[0]) ** 2
+    bound = h * h / 8 * fd2.max() * 1.01 + 1e-15
+    assert np.max(np.abs(window.psi_linear(u, m, b) - window.psi(u, m, b))) <= bound
+
+
+def test_linear_window_nfft_error_matches_direct():
+    """Sec. 3.7.4: the table sizes keep the window's interpolation error below
+    the NFFT's own error: with the LINEAR window the NFFT is as accurate
+    against the exact NDFT as with the evaluated window (m = 2..6), and the
+    NFFT operator stays adjoint to its adjoint."""
+    from oracle import ndft, nfft
+    rng = np.random.default_rng(30)
+    k = rng.random((200, 2)) - 0.5
+    f = rng.standard_normal((24, 20)) + 1j * rng.standard_normal((24, 20))
+    w = rng.standard_normal(200) + 1j * rng.standard_normal(200)
+    ex = ndft.ndft(k, f)
+    for m in range(2, 7):
+        e_dir = np.linalg.norm(nfft.forward(k, f, 2.0, m) - ex) / np.linalg.norm(ex)
+        e_lin = np.linalg.norm(nfft.forward(k, f, 2.0, m, window="linear") - ex) / np.linalg.norm(ex)
+        assert e_lin <= 1.05 * e_dir
+    lhs = np.vdot(w, nfft.forward(k, f, 2.0, 4, window="linear"))
+    rhs = np.vdot(nfft.adjoint(k, w, (24, 20), 2.0, 4, window="linear"), f)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(f) * np.linalg.norm(w)
