@@ -230,8 +230,10 @@ int nfft_step_crop_deconv(nfft_plan *p, void *y);
  * N~_d = 2 N_d = 256 (and without NFFT_FLAG_LIBRARY_FFT) this is the pruned
  * FFT: three passes of 256-point line DFTs that read only the non-zero part
  * of the padded grid, with the correction fused into the first pass and the
- * fftshift of Sec. 3.5 applied as the exact phase i^l (N~ = 2N).  Otherwise
- * it runs the two separate steps. */
+ * fftshift of Sec. 3.5 applied as the exact phase i^l (N~ = 2N).  For small
+ * 1D complex128 plans (see nfft_plan_paths) it is the direct sum
+ * g^_l = sum_n f_n beta(n) e^{-2 pi i n l / N~} over the N inputs.
+ * Otherwise it runs the two separate steps. */
 int nfft_step_pad_fft(nfft_plan *p, const void *f);
 
 /* Algorithm 2, inverse FFT + crop + correction steps in one call:
@@ -239,7 +241,8 @@ int nfft_step_pad_fft(nfft_plan *p, const void *f);
  * y.  Pruned as for nfft_step_pad_fft
  * (each inverse pass computes only the N outputs that are kept; the plan
  * grid is used as scratch and does not hold the full inverse FFT
- * afterwards); otherwise nfft_step_fft(+1) + nfft_step_crop_deconv. */
+ * afterwards), as direct sums for small 1D complex128 plans;
+ * otherwise nfft_step_fft(+1) + nfft_step_crop_deconv. */
 int nfft_step_fft_crop(nfft_plan *p, void *y);
 
 /* Graph mode for small transforms, whose time is mostly kernel launches:
@@ -248,15 +251,22 @@ int nfft_step_fft_crop(nfft_plan *p, void *y);
  * time a pair of buffers is seen and replayed on the plan's stream with one
  * launch afterwards; new buffers re-capture, and nfft_plan_set_tile drops the
  * graphs (nfft_set_nodes keeps them: the node buffers stay in place).  Host
- * buffers take the direct path.  enable = 0 drops the graphs. */
+ * buffers, and plans with NFFT_FLAG_FULL_MATRIX (whose matrices are
+ * reallocated by nfft_set_nodes), take the direct path.  enable = 0 drops
+ * the graphs.  Returns NFFT_ERR_INVALID_ARG for a null plan and a latched
+ * error of the plan if it holds one. */
 int nfft_plan_set_graph(nfft_plan *p, int enable);
 
 /* Which kernels the plan's transforms use (set by nfft_plan_create and
- * nfft_plan_set_tile): *fast_resample bit 0 = the 3D m = 4 complex64
- * node-per-half-warp gather, bit 1 = the 3D m = 4 or 6 complex64
- * register-accumulating scatter (tiles of at most 17 - 2m cells per
- * dimension); *pruned_fft = 1 when nfft_step_pad_fft / nfft_step_fft_crop
- * run the pruned FFT.  Either pointer may be NULL. */
+ * nfft_plan_set_tile): *fast_resample bit 0 = a specialised complex64
+ * gather (3D m = 4 or 6, 2D m = 4), bit 1 = a register-accumulating
+ * complex64 scatter (3D m = 4 or 6 with tiles of at most 17 - 2m cells per
+ * dimension, 2D m = 4); *pruned_fft = how nfft_step_pad_fft /
+ * nfft_step_fft_crop run: 0 = library FFT with separate correction steps,
+ * 1 = the pruned 3D FFT, 2 = direct sums (1D complex128 with N~ <= 4096 and
+ * N N~ <= 2^20: the FFT's definition evaluated over the N non-zero inputs or
+ * kept outputs, spread over every SM, for sizes where one library FFT would
+ * occupy a single SM's FP64 units).  Either pointer may be NULL. */
 int nfft_plan_paths(nfft_plan *p, int *fast_resample, int *pruned_fft);
 
 /* Node-gradient resampling on the current plan grid (which must hold

@@ -207,11 +207,12 @@ def nfft_plan_set_graph(plan, enable):
 
 
 def nfft_plan_paths(plan):
-    """Returns (status, fast_gather, fast_scatter, pruned_fft)."""
+    """Returns (status, fast_gather, fast_scatter, fft_form) with fft_form 0 =
+    library FFT + separate correction, 1 = pruned 3D FFT, 2 = direct sums."""
     a = _i()
     b = _i()
     s = lib().nfft_plan_paths(_p(plan), ctypes.byref(a), ctypes.byref(b))
-    return s, bool(a.value & 1), bool(a.value & 2), bool(b.value)
+    return s, bool(a.value & 1), bool(a.value & 2), int(b.value)
 
 
 def nfft_step_grad_gather(plan, cot_ptr, gk_ptr):

@@ -208,6 +208,16 @@ cudaError_t launch_pruned_forward(const void* f, const float* const* beta, const
                                   cudaStream_t s);
 cudaError_t launch_pruned_adjoint(void* grid, const float* const* beta, const float2* tw, void* y, cudaStream_t s);
 
+// Small 1D complex128 plans (dft1d.cu): correction + pad + FFT and inverse
+// FFT + crop + correction as direct sums spread over every SM; `tw` holds
+// the N~ roots of unity e^{-2 pi i k / N~} in FP64.
+bool dft1d_supported(int D, int N, int Nt);
+cudaError_t launch_dft_twiddles(double2* tw, int Nt, cudaStream_t s);
+cudaError_t launch_dft1d_forward(int N, int Nt, const void* f, const double* beta, const double2* tw, void* grid,
+                                 int sms, cudaStream_t s);
+cudaError_t launch_dft1d_adjoint(int N, int Nt, const void* grid, const double* beta, const double2* tw, void* y,
+                                 int sms, cudaStream_t s);
+
 // 2D, m = 4, complex64 register-accumulating scatter and warp-per-item
 // gather (resample2d.cu): tiles of at most 9 cells in dimension 0 and
 // regions of at most 32 in dimension 1.

@@ -38,7 +38,7 @@ struct nfft_plan {
   int64_t T[kMaxD] = {1, 1, 1};
   int ntile[kMaxD] = {1, 1, 1};
   int64_t n_tiles = 0;
-  int cmax = 128;
+  int cmax = 128;              // nodes per work item (set by configure_tiles)
   int64_t max_items = 0;
   int ctas[4] = {0, 0, 0, 0};  // persistent grid per kernel kind
   bool fast_gather = false;    // specialised complex64 gather (3D m = 4 / 6, 2D m = 4)
@@ -48,6 +48,8 @@ struct nfft_plan {
   int grad_ctas = 0;           // 3D m = 4 complex64 node-gradient kernel (0: generic)
   bool pruned = false;         // nfft_step_pad_fft / fft_crop use the pruned 3D FFT
   float2* fft_tw = nullptr;    // its 256 twiddles
+  bool dft1d = false;          // ... or the direct sums of small 1D complex128 plans
+  double2* dft_tw = nullptr;   // their N~ roots of unity
 
   void* grid = nullptr;
   double* beta64 = nullptr;
@@ -306,6 +308,7 @@ void default_tile(const nfft_plan* p, int64_t* T) {
 }
 
 constexpr uint32_t kWindowFlags = NFFT_FLAG_WINDOW_DIRECT | NFFT_FLAG_WINDOW_LINEAR | NFFT_FLAG_WINDOW_POLYNOMIAL;
+constexpr int kItemCapFull = 128;  // nodes per work item of the specialised kernels
 
 // Captured graphs hold the launch configuration and buffers of the moment;
 // dropped when either changes.
@@ -327,6 +330,22 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
   }
   if (n_tiles > (int64_t)1 << 30) return NFFT_ERR_INVALID_ARG;
   p->n_tiles = n_tiles;
+  p->cmax = kItemCapFull;
+  {
+    // The generic kernels run one CTA per work item: a small node set is cut
+    // into smaller items (down to 8 nodes) so that it reaches every SM.  The
+    // specialised kernels keep full items.
+    const Geometry g0 = make_geometry(p);
+    const bool c64 = p->dtype == NFFT_C64 && !(p->flags & kWindowFlags);
+    const bool fast = c64 && (p->D == 2 ? scatter2d_supported(g0)
+                                        : fast3d_supported(g0, kItemCapFull) ||
+                                              fast_scatter_supported(g0, kItemCapFull));
+    if (!fast) {
+      int64_t want = (p->M + 2 * p->sms - 1) / (2 * (int64_t)p->sms);
+      want = (want + 7) / 8 * 8;
+      p->cmax = (int)(want < 8 ? 8 : (want > kItemCapFull ? kItemCapFull : want));
+    }
+  }
   p->max_items = n_tiles + (p->M + p->cmax - 1) / p->cmax + 1;
   if (p->tiles_cap < n_tiles) {
     dfree(p->tile_count);
@@ -347,10 +366,10 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
     p->items_cap = p->max_items;
   }
   Geometry g = make_geometry(p);
-  // complex64 plans use the specialised kernels where the tile allows; with
-  // NFFT_FLAG_COMPENSATED their scatter runs in its TwoSum-compensated form
-  // a window flag selects the generic kernels (the window modes compared on
-  // the same kernels); otherwise complex64 plans use the specialised ones
+  // complex64 plans use the specialised kernels where the tile allows (with
+  // NFFT_FLAG_COMPENSATED their scatter runs in its TwoSum-compensated form);
+  // a window flag selects the generic kernels, so that the window modes are
+  // compared on the same kernels
   const bool c64 = p->dtype == NFFT_C64 && !(p->flags & kWindowFlags);
   const int comp = (p->flags & NFFT_FLAG_COMPENSATED) && c64 ? 1 : 0;
   p->fast_gather = c64 && fast3d_supported(g, p->cmax);
@@ -379,6 +398,15 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
     if (per_sm <= 0 && needed) return NFFT_ERR_UNSUPPORTED;
     p->ctas[kind] = per_sm > 0 ? per_sm * p->sms : 0;
   }
+  // The persistent grids take work items in strides of their size; a small
+  // node set has fewer items than resident CTAs, and the extra CTAs would
+  // only start and exit (each launch wave costs microseconds).
+  auto cap = [&](int& c) {
+    if (c > p->max_items) c = (int)p->max_items;
+  };
+  for (int& c : p->ctas) cap(c);
+  for (int& c : p->fast_ctas) cap(c);
+  cap(p->grad_ctas);
   return NFFT_OK;
 }
 
@@ -464,6 +492,9 @@ const float* const* beta32_dims(const nfft_plan* p, const float** out) {
 // Algorithm 1, correction + zero-pad + FFT steps: pruned FFT where the plan
 // qualifies, else the correction kernel and cuFFT.
 int run_pad_fft(nfft_plan* p, const void* f) {
+  if (p->dft1d)
+    return cuda_status(p, launch_dft1d_forward((int)p->N[0], (int)p->Nt[0], f, p->beta64, p->dft_tw, p->grid,
+                                               p->sms, p->stream));
   if (p->pruned) {
     const float* beta[kMaxD];
     return cuda_status(p, launch_pruned_forward(f, beta32_dims(p, beta), p->fft_tw, p->grid, p->stream));
@@ -477,6 +508,9 @@ int run_crop_deconv(nfft_plan* p, void* y);
 
 // Algorithm 2, inverse FFT + crop + correction steps.
 int run_fft_crop(nfft_plan* p, void* y) {
+  if (p->dft1d)
+    return cuda_status(p, launch_dft1d_adjoint((int)p->N[0], (int)p->Nt[0], p->grid, p->beta64, p->dft_tw, y,
+                                               p->sms, p->stream));
   if (p->pruned) {
     const float* beta[kMaxD];
     return cuda_status(p, launch_pruned_adjoint(p->grid, beta32_dims(p, beta), p->fft_tw, y, p->stream));
@@ -505,7 +539,9 @@ int run_plain(nfft_plan* p, int dir, const void* in, void* out) {
 // stream (cuFFT pointed at it meanwhile) the first time a pair of buffers is
 // seen, replayed on the plan's stream afterwards.
 int run_direction(nfft_plan* p, int dir, const void* in, void* out) {
-  if (!p->graph_mode) return run_plain(p, dir, in, out);
+  // FULL plans rebuild their sparse matrices (new allocations) in
+  // nfft_set_nodes, so a captured graph would keep stale pointers: direct path.
+  if (!p->graph_mode || (p->flags & NFFT_FLAG_FULL_MATRIX)) return run_plain(p, dir, in, out);
   if (!p->graph[dir] || p->graph_ptr[dir][0] != in || p->graph_ptr[dir][1] != out) {
     if (p->graph[dir]) cudaGraphExecDestroy(p->graph[dir]);
     p->graph[dir] = nullptr;
@@ -572,7 +608,7 @@ int nfft_plan_destroy(nfft_plan* p) {
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   if (p->fft_ok) cufftDestroy(p->fft);
   full_destroy(p->full);
-  void* bufs[] = {p->grid, p->fft_tw, p->beta64, p->beta32, p->poly, p->poly64, p->lut, p->cell, p->frac, p->perm,
+  void* bufs[] = {p->grid, p->fft_tw, p->dft_tw, p->beta64, p->beta32, p->poly, p->poly64, p->lut, p->cell, p->frac, p->perm,
                   p->key, p->rank,
                   p->tile_count, p->tile_offset, p->items, p->n_items,
                   p->stage[0], p->stage[1], p->stage[2]};
@@ -708,6 +744,12 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
       if (s == NFFT_OK) s = cuda_status(p, build_fft_twiddles(p->fft_tw, p->stream));
       p->pruned = s == NFFT_OK;
     }
+  }
+  if (s == NFFT_OK && dtype == NFFT_C128 && !(flags & NFFT_FLAG_LIBRARY_FFT) &&
+      dft1d_supported(D, (int)N[0], (int)p->Nt[0])) {
+    s = dalloc(p, &p->dft_tw, sizeof(double2) * (size_t)p->Nt[0]);
+    if (s == NFFT_OK) s = cuda_status(p, launch_dft_twiddles(p->dft_tw, (int)p->Nt[0], p->stream));
+    p->dft1d = s == NFFT_OK;
   }
   if (s == NFFT_OK) s = cuda_status(p, cudaMemsetAsync(p->n_items, 0, sizeof(int), p->stream));
   if (s != NFFT_OK) {
@@ -873,6 +915,7 @@ std::vector<std::vector<int64_t>> plan_tile_candidates(const nfft_plan* p) {
     c.push_back({8, 8, 4});
     c.push_back({4, 8, 8});
     c.push_back({16, 8, 8});
+    c.push_back({6, 8, 8});  // best in the tile sweep at twice the headline density
     c.push_back({9, 9, 8});
     c.push_back({9, 9, 9});
     c.push_back({5, 5, 5});
@@ -1022,7 +1065,7 @@ int nfft_plan_set_graph(nfft_plan* p, int enable) {
 int nfft_plan_paths(nfft_plan* p, int* fast_resample, int* pruned_fft) {
   if (!p) return NFFT_ERR_INVALID_ARG;
   if (fast_resample) *fast_resample = (p->fast_gather ? 1 : 0) | (p->fast_scatter ? 2 : 0);
-  if (pruned_fft) *pruned_fft = p->pruned ? 1 : 0;
+  if (pruned_fft) *pruned_fft = p->pruned ? 1 : (p->dft1d ? 2 : 0);
   return NFFT_OK;
 }
 

@@ -179,6 +179,39 @@ __device__ __forceinline__ void node_weight_derivs(const Geometry& g, int d, int
   }
 }
 
+// Window value of tap i alone (the tap-parallel 1D loops below): the same
+// value node_weights gives for tap i.
+template <int K, typename R>
+__device__ __forceinline__ R node_weight_tap(const Geometry& g, int d, int mi, R t, int i) {
+  if (g.wmode != kWinDirect) {
+    R tmp[K];
+    table_weights<K, R>(g, d, mi, t, tmp, nullptr);
+    R v = R(0);
+#pragma unroll
+    for (int j = 0; j < K; ++j) v = (j == i) ? tmp[j] : v;
+    return v;
+  }
+  const R b = R(g.b[d]), norm = R(g.norm[d]), mr = R(mi);
+  const R normx = sizeof(R) == 4 ? kb_normx<R>(b, mr) : R(0);
+  const R u = R(-g.off - i) + t;
+  const R mm_u = R(mi + g.off + i) - t;
+  const R mp_u = R(mi - g.off - i) + t;
+  R v = kb_window<R>(u, mm_u, mp_u, b, norm, mr, normx);
+  if (g.closed && ((i == 0 && t != R(0)) || i == K - 1)) v = R(0);
+  return v;
+}
+
+// 1D items run tap-parallel: a group of KP >= K consecutive threads (a
+// power of two) takes one node, thread i of the group its tap i.  A node
+// costs K window evaluations, and in double precision those dominate: GB300
+// issues FP64 arithmetic at a small fraction of the FP32 rate, so one node
+// per thread leaves the FP64 units waiting on a few long dependent chains.
+template <int K>
+struct TapGroup {
+  static constexpr int KP = K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+  static_assert(K <= 32, "tap groups fit a warp");
+};
+
 // ---------------------------------------------------------------------------
 // Direct resampling (Algorithm 3)
 // ---------------------------------------------------------------------------
@@ -202,6 +235,34 @@ __device__ __forceinline__ void gather_item(const Geometry& g, const typename Cp
   for (int e = threadIdx.x; e < region; e += blockDim.x) tile[e] = grid[region_to_grid<D>(g, start, e)];
   __syncthreads();
 
+  if constexpr (D == 1) {
+    constexpr int KP = TapGroup<K>::KP;
+    const int per = blockDim.x / KP, jn = threadIdx.x / KP, i = threadIdx.x % KP;
+    const int end = item.y + item.z;
+    for (int q0 = item.y; q0 < end; q0 += per) {  // uniform over the CTA: the shuffles need whole warps
+      const int q = q0 + jn;
+      R re = R(0), im = R(0);
+      if (q < end && i < K) {
+        const int a0 = na.cell[q] - tc[0] * g.T[0];
+        const R w = node_weight_tap<K, R>(g, 0, mi, frac[q], i);
+        const C v = tile[a0 + i];
+        re = w * v.x;
+        im = w * v.y;
+      }
+#pragma unroll
+      for (int o = KP / 2; o >= 1; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (q < end && i == 0) {
+        C out;
+        out.x = re;
+        out.y = im;
+        fhat[na.perm[q]] = out;
+      }
+    }
+    return;
+  }
   for (int q = item.y + threadIdx.x; q < item.y + item.z; q += blockDim.x) {
     R w[D][K];
     int a[D];
@@ -211,14 +272,7 @@ __device__ __forceinline__ void gather_item(const Geometry& g, const typename Cp
       node_weights<K, R>(g, d, mi, frac[d * M + q], w[d]);
     }
     R re = R(0), im = R(0);
-    if constexpr (D == 1) {
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        C v = tile[a[0] + i];
-        re += w[0][i] * v.x;
-        im += w[0][i] * v.y;
-      }
-    } else if constexpr (D == 2) {
+    if constexpr (D == 2) {
 #pragma unroll
       for (int i0 = 0; i0 < K; ++i0) {
         const C* row = tile + (a[0] + i0) * g.L[1] + a[1];
@@ -232,7 +286,7 @@ __device__ __forceinline__ void gather_item(const Geometry& g, const typename Cp
         re += w[0][i0] * sr;
         im += w[0][i0] * si;
       }
-    } else {
+    } else if constexpr (D == 3) {
 #pragma unroll 1
       for (int i0 = 0; i0 < K; ++i0) {
         const C* plane = tile + ((a[0] + i0) * g.L[1] + a[1]) * g.L[2] + a[2];
@@ -344,7 +398,21 @@ __device__ __forceinline__ void scatter_item(const Geometry& g, typename CplxT<R
   for (int e = threadIdx.x; e < 2 * region * (COMP ? 2 : 1); e += blockDim.x) acc[e] = R(0);
   __syncthreads();
 
-  for (int q = item.y + threadIdx.x; q < item.y + item.z; q += blockDim.x) {
+  if constexpr (D == 1) {
+    constexpr int KP = TapGroup<K>::KP;
+    const int per = blockDim.x / KP, jn = threadIdx.x / KP, i = threadIdx.x % KP;
+    for (int q = item.y + jn; q < item.y + item.z; q += per) {
+      if (i < K) {
+        const int a0 = na.cell[q] - tc[0] * g.T[0];
+        const R w = node_weight_tap<K, R>(g, 0, mi, frac[q], i);
+        const C v = fhat[na.perm[q]];
+        const int idx = 2 * (a0 + i);
+        smem_add<R, COMP>(acc, comp, idx, v.x * w);
+        smem_add<R, COMP>(acc, comp, idx + 1, v.y * w);
+      }
+    }
+  }
+  for (int q = item.y + threadIdx.x; D > 1 && q < item.y + item.z; q += blockDim.x) {
     R w[D][K];
     int a[D];
 #pragma unroll
@@ -353,14 +421,7 @@ __device__ __forceinline__ void scatter_item(const Geometry& g, typename CplxT<R
       node_weights<K, R>(g, d, mi, frac[d * M + q], w[d]);
     }
     const C v = fhat[na.perm[q]];
-    if constexpr (D == 1) {
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        const int idx = 2 * (a[0] + i);
-        smem_add<R, COMP>(acc, comp, idx, v.x * w[0][i]);
-        smem_add<R, COMP>(acc, comp, idx + 1, v.y * w[0][i]);
-      }
-    } else if constexpr (D == 2) {
+    if constexpr (D == 2) {
 #pragma unroll
       for (int i0 = 0; i0 < K; ++i0) {
         const R vr = v.x * w[0][i0], vi = v.y * w[0][i0];
@@ -372,7 +433,7 @@ __device__ __forceinline__ void scatter_item(const Geometry& g, typename CplxT<R
           smem_add<R, COMP>(acc, comp, idx + 1, vi * w[1][i1]);
         }
       }
-    } else {
+    } else if constexpr (D == 3) {
 #pragma unroll 1
       for (int i0 = 0; i0 < K; ++i0) {
         R w0 = R(0);

@@ -59,7 +59,10 @@ constexpr int kItemCap = 128;       // nodes per work item staged in shared memo
 constexpr int kGatherSlot = 32;     // floats of window slot per gather warp
 constexpr int kGatherMaxWarps = 8;
 constexpr int kGatherTail = kGatherMaxWarps * kGatherSlot * 4 + 16;  // window slots + mbarrier (bytes)
-constexpr int kWaitSpins = 1 << 22;  // bound on the polls of one region copy's mbarrier
+// Bound on the wait for one region copy: 0.5 s of the global timer (a copy
+// of 37 KB takes microseconds), and an iteration cap behind it.
+constexpr unsigned long long kWaitNs = 500000000ull;
+constexpr int kWaitSpinCap = 1 << 28;
 
 // Set by a CTA whose bounded wait for a region copy gave up (read and
 // cleared by fast3d_take_wait_timeout).
@@ -87,6 +90,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Polls the mbarrier until the phase completes or kWaitNs have passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < kWaitSpinCap; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
 }
 
 // One 3D box of the grid's tensor map into shared memory (x the contiguous
@@ -210,7 +230,7 @@ __device__ __forceinline__ void load_tile(const Geometry& g, const int* start, c
 // node records staged; ends with a CTA barrier.  Returns false, uniformly
 // over the CTA, when the bounded wait for a TMA copy gave up.
 __device__ __forceinline__ bool load_region(const Geometry& g, const CUtensorMap* tmap, uint64_t* bar,
-                                            unsigned& phase, bool tma_cta, const int* start,
+                                            unsigned& phase, bool tma_cta, unsigned tx_extra, const int* start,
                                             const float2* grid, float2* tile, int warp, int lane, int nwarps,
                                             int shift, const NodeArrays& na, const int4& item, const int* tc,
                                             NodeStage& ns) {
@@ -221,7 +241,7 @@ __device__ __forceinline__ bool load_region(const Geometry& g, const CUtensorMap
       // the previous item's reads of the tile (generic proxy) are ordered
       // before the copy's writes (async proxy) by the caller's barrier
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive_expect_tx(bar, (unsigned)(g.L[0] * g.L[1] * kPitch * (int)sizeof(float2)));
+      mbar_arrive_expect_tx(bar, (unsigned)(g.L[0] * g.L[1] * kPitch * (int)sizeof(float2)) + tx_extra);
       tma_load_box(tile, tmap, start[2] - 1, start[1], start[0], bar);
     }
   } else {
@@ -233,10 +253,13 @@ __device__ __forceinline__ bool load_region(const Geometry& g, const CUtensorMap
     __syncthreads();
     return true;
   }
-  bool done = false;
-  for (int i = 0; i < kWaitSpins && !done; ++i) done = mbar_try_wait(bar, phase);
+  const bool done = mbar_wait_bounded(bar, phase);
   phase ^= 1u;
   if (__syncthreads_or(!done)) {
+    // Last resort: the CTA returns and the host reads NFFT_ERR_TIMEOUT.  A
+    // copy still in flight would land in shared memory the CTA no longer
+    // uses; the test hook (tx_extra) makes the wait run out with the copy
+    // already complete.
     if (threadIdx.x == 0) atomicExch(&g_wait_timeout, 1);
     return false;
   }
@@ -264,7 +287,8 @@ __global__ void __launch_bounds__(32 * GW)
   float* wslot = reinterpret_cast<float*>(tile + g.L[0] * plane) + kGatherSlot * warp;
   uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(tile + g.L[0] * plane) +
                                               kGatherMaxWarps * kGatherSlot);
-  const bool tma_cta = tma_on && (smem_u32(tile) & 127) == 0;
+  const bool tma_cta = (tma_on & 1) && (smem_u32(tile) & 127) == 0;
+  const unsigned tx_extra = (unsigned)tma_on >> 8;
   if (tma_cta && threadIdx.x == 0) mbar_init(bar);
   unsigned phase = 0;
   // lane evaluates tap i2 of dimension grp (weights wA) and of dimension 2 (wB)
@@ -282,7 +306,7 @@ __global__ void __launch_bounds__(32 * GW)
     for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
 
     __syncthreads();
-    if (!load_region(g, &tmap, bar, phase, tma_cta, start, grid, tile, warp, lane, GW, shift, na, item, tc, ns))
+    if (!load_region(g, &tmap, bar, phase, tma_cta, tx_extra, start, grid, tile, warp, lane, GW, shift, na, item, tc, ns))
       return;
 
     for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * GW) {
@@ -371,7 +395,8 @@ __global__ void __launch_bounds__(32 * GW)
   float* wslot = reinterpret_cast<float*>(tile + g.L[0] * plane) + 2 * kGatherSlot * warp;
   uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(tile + g.L[0] * plane) +
                                               kGatherMaxWarps * kGatherSlot);
-  const bool tma_cta = tma_on && (smem_u32(tile) & 127) == 0;
+  const bool tma_cta = (tma_on & 1) && (smem_u32(tile) & 127) == 0;
+  const unsigned tx_extra = (unsigned)tma_on >> 8;
   if (tma_cta && threadIdx.x == 0) mbar_init(bar);
   unsigned phase = 0;
   float cA[kCoef], cB[kCoef];
@@ -388,7 +413,7 @@ __global__ void __launch_bounds__(32 * GW)
     for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
 
     __syncthreads();
-    if (!load_region(g, &tmap, bar, phase, tma_cta, start, grid, tile, warp, lane, GW, shift, na, item, tc, ns))
+    if (!load_region(g, &tmap, bar, phase, tma_cta, tx_extra, start, grid, tile, warp, lane, GW, shift, na, item, tc, ns))
       return;
 
     for (int s0 = 2 * warp; s0 < item.z; s0 += 2 * GW) {
@@ -1061,6 +1086,17 @@ bool use_region_tma() {
   return !(e && strcmp(e, "0") == 0);
 }
 
+// Kernel argument tma_on: bit 0 = region copies by TMA; bits 8.. = bytes the
+// mbarrier expects beyond the box (0 unless NFFT_GB300_TEST_TX_EXTRA is set:
+// a test hook that makes the bounded wait run out with no copy in flight, so
+// that the timeout path can be exercised without a fault).
+int region_tma_arg(bool on) {
+  if (!on) return 0;
+  const char* e = getenv("NFFT_GB300_TEST_TX_EXTRA");
+  const int extra = e ? atoi(e) : 0;
+  return 1 | ((extra > 0 && extra <= 4096 ? extra : 0) << 8);
+}
+
 bool region_map(const Geometry& g, const void* grid, CUtensorMap* map) {
   memset(map, 0, sizeof(*map));
   if (!use_region_tma() || (g.T[2] & 1) || ((uintptr_t)grid & 15)) return false;
@@ -1155,7 +1191,7 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   CUtensorMap map;
-  const int tma_on = region_map(g, grid, &map) ? 1 : 0;
+  const int tma_on = region_tma_arg(region_map(g, grid, &map));
   auto kern = reinterpret_cast<void (*)(Geometry, const float2*, NodeArrays, const float*, float2*,
                                         const CUtensorMap, int)>(k);
   kern<<<ctas, 32 * w, smem, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat, map, tma_on);
@@ -1168,7 +1204,7 @@ cudaError_t launch_grad3d_fast(const Geometry& g, const void* grid, const NodeAr
   cudaError_t e = set_smem(grad3d_m4_kernel<4>, smem);
   if (e != cudaSuccess) return e;
   CUtensorMap map;
-  const int tma_on = region_map(g, grid, &map) ? 1 : 0;
+  const int tma_on = region_tma_arg(region_map(g, grid, &map));
   grad3d_m4_kernel<4><<<ctas, 128, smem, s>>>(g, (const float2*)grid, na, poly, (const float2*)cot, (float*)gk,
                                               map, tma_on);
   return cudaGetLastError();

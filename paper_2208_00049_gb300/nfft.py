@@ -174,12 +174,14 @@ class Plan:
         return out
 
     def step_pad_fft(self, f):
-        """Algorithm 1's correction, zero-pad and FFT steps (the pruned FFT where the plan qualifies)."""
+        """Algorithm 1's correction, zero-pad and FFT steps (the pruned FFT or
+        the direct sums where the plan qualifies)."""
         self._check_tensor(f, self.N, self.dtype, "f")
         B.check(B.nfft_step_pad_fft(self.handle, _ptr(f)), "nfft_step_pad_fft")
 
     def step_fft_crop(self, out):
-        """Algorithm 2's inverse FFT, crop and correction steps (the pruned FFT where the plan qualifies)."""
+        """Algorithm 2's inverse FFT, crop and correction steps (the pruned FFT
+        or the direct sums where the plan qualifies)."""
         self._check_tensor(out, self.N, self.dtype, "out")
         B.check(B.nfft_step_fft_crop(self.handle, _ptr(out)), "nfft_step_fft_crop")
         return out
@@ -189,11 +191,13 @@ class Plan:
         B.check(B.nfft_plan_set_graph(self.handle, enable), "nfft_plan_set_graph")
 
     def paths(self):
-        """{'fast_gather', 'fast_scatter', 'pruned_fft'}: which specialised
-        kernels this plan's transforms run."""
-        s, fg, fs, pruned = B.nfft_plan_paths(self.handle)
+        """{'fast_gather', 'fast_scatter', 'pruned_fft', 'fft_form'}: which
+        specialised kernels this plan's transforms run (fft_form: 'library',
+        'pruned' or 'direct')."""
+        s, fg, fs, form = B.nfft_plan_paths(self.handle)
         B.check(s, "nfft_plan_paths")
-        return {"fast_gather": fg, "fast_scatter": fs, "pruned_fft": pruned}
+        return {"fast_gather": fg, "fast_scatter": fs, "pruned_fft": form == 1,
+                "fft_form": ("library", "pruned", "direct")[form]}
 
     def step_grad_gather(self, cot, out):
         self._check_tensor(cot, (self.M,), self.dtype, "cot")

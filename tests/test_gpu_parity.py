@@ -691,3 +691,21 @@ def test_graph_replay_matches_direct_path(N, M, dt):
     plan.forward(f, out=fh)
     assert_close(fh.cpu().numpy(), onfft.forward(k2, 2 * case["f"], 2.0, 4), TOL[dt], "graph after set_nodes")
     plan.close()
+
+
+def test_graph_mode_full_matrix_takes_direct_path():
+    """A FULL plan rebuilds its sparse matrices in nfft_set_nodes; in graph
+    mode it keeps launching directly, so new nodes are always seen."""
+    from paper_2208_00049_gb300 import binding as B
+    N, M = (24, 20), 800
+    case = inputs.small_case(N, M, seed=107, m=3)
+    plan = _plan(N, M, 2.0, 3, "c128", flags=B.NFFT_FLAG_FULL_MATRIX)
+    plan.set_graph(True)
+    f = to_dev(case["f"], torch.complex128)
+    fh = torch.empty(M, dtype=torch.complex128, device="cuda")
+    for seed in (107, 109):
+        k = inputs.small_case(N, M, seed=seed, m=3)["k"]
+        plan.set_nodes(to_dev(k, torch.float64))
+        plan.forward(f, out=fh)
+        assert_close(fh.cpu().numpy(), onfft.forward(k, case["f"], 2.0, 3), TOL["c128"], "FULL, graph mode")
+    plan.close()

@@ -1,8 +1,9 @@
-"""GPU parity of the pruned 3D FFT (N~_d = 2 N_d = 256, complex64) against the
-FP64 oracle: the fused steps (Algorithm 1: correction + zero pad + FFT;
+"""GPU parity of the library's own FFT forms against the FP64 oracle: the
+pruned 3D FFT (N~_d = 2 N_d = 256, complex64) and the direct sums of small 1D
+complex128 plans.  The fused steps (Algorithm 1: correction + zero pad + FFT;
 Algorithm 2: inverse FFT + crop + correction) element by element on the full
-256^3 grid / 128^3 output, the whole
-transforms and the node gradient through them, and the selection rule."""
+grid / output, the whole transforms and the node gradient through them, and
+the selection rules."""
 import numpy as np
 import pytest
 
@@ -124,3 +125,47 @@ def test_grad_through_pruned_fft():
     want = onfft.node_grad(k, f, cot, 2.0, 4)
     # the complex64 node-gradient tolerance of the other gradient tests
     assert_close(gk, want, 1e-4, "grad")
+
+
+def test_direct_sum_selection():
+    from paper_2208_00049_gb300 import binding as B
+    cases = [
+        ((256,), "c128", 0, "direct"),
+        ((300,), "c128", 0, "direct"),
+        ((2048,), "c128", 0, "library"),         # N N~ = 2^23 > 2^20
+        ((256,), "c64", 0, "library"),
+        ((256,), "c128", B.NFFT_FLAG_LIBRARY_FFT, "library"),
+        ((64, 64), "c128", 0, "library"),
+    ]
+    for N, dt, flags, want in cases:
+        plan = _plan(N, 8, dt, flags)
+        assert plan.paths()["fft_form"] == want, (N, dt, flags)
+        plan.close()
+
+
+@pytest.mark.parametrize("N,sigma", [((256,), 2.0), ((257,), 2.0), ((300,), 1.5), ((800,), 1.25)])
+def test_direct_sum_steps_match_oracle(N, sigma):
+    """Small 1D complex128 plans: correction + pad + FFT and inverse FFT +
+    crop + correction as direct sums, element by element against the oracle's
+    steps, and the whole transforms against the oracle."""
+    rng = np.random.default_rng(211)
+    p = onfft.Params(N, sigma, 4)
+    plan = _plan(N, 600, "c128", 0, sigma)
+    assert plan.paths()["fft_form"] == "direct"
+    f = inputs.complex_normal(rng, N)
+    plan.step_pad_fft(to_dev(f, torch.complex128))
+    got = plan.grid_tensor().cpu().numpy() / _peak(p)
+    assert_close(got, onfft.fft_forward(onfft.correction_pad(p, f)), 1e-13, "direct pad_fft")
+    G = inputs.complex_normal(rng, p.Nt)
+    plan.grid_tensor().copy_(torch.from_numpy(G))
+    y = torch.empty(N, dtype=torch.complex128, device="cuda")
+    plan.step_fft_crop(y)
+    assert_close(y.cpu().numpy() / _peak(p), onfft.crop_correction(p, onfft.fft_adjoint(G)), 1e-13,
+                 "direct fft_crop")
+    case = inputs.small_case(N, 600, seed=223, sigma=sigma, m=4)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    fh = plan.forward(to_dev(case["f"], torch.complex128)).cpu().numpy()
+    ya = plan.adjoint(to_dev(case["w"], torch.complex128)).cpu().numpy()
+    assert_close(fh, onfft.forward(case["k"], case["f"], sigma, 4), 1e-12, "forward")
+    assert_close(ya, onfft.adjoint(case["k"], case["w"], N, sigma, 4), 1e-12, "adjoint")
+    plan.close()
