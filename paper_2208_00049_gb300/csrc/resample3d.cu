@@ -120,6 +120,24 @@ __device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, 
       : "memory");
 }
 
+// Bulk tensor reduction (add, element type of the map) of a shared-memory
+// box into global memory; completion tracked by the issuing thread's bulk
+// async-group.
+__device__ __forceinline__ void tma_reduce_add_box(const CUtensorMap* map, const void* src, int x, int y, int z) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group"
+      " [%0, {%1, %2, %3}], [%4];" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// The issuing thread's bulk operations have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// ... and are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // One staged node = 8 words {t0, t1, t2, a0 | a1 << 8 | a2 << 16, perm, re v, im v, 0}
 // (fractions, cell offsets in the tile, caller index, scatter input).  A warp
 // reads a node with one 32-bit load per lane (lane & 7 -> word) and hands the
@@ -747,8 +765,15 @@ bool g12_supported(const Geometry& g, int cmax) {
 //     (w, w) pairs: the main loop issues 2 + K/4 shared loads per thread
 //     and node;
 //  4. every warp runs over its node runs;
-//  5. the region is added to the grid with vector global reductions.
+//  5. the region is added to the grid: a region inside the grid is written
+//     to shared memory (over the weight arrays, which are done with) as a
+//     box 18 points wide and added by one bulk tensor reduction
+//     (cp.reduce.async.bulk.tensor, add, FP32) issued by one thread, whose
+//     read of shared memory is waited for only before the next item's
+//     weights are written; a region that wraps at a grid face is added with
+//     vector global reductions.
 constexpr int kRegAccLines = 16;                   // acc[h][r0], L0 <= 16
+constexpr int kFlushPitch = 18;                    // points per box row (x0 even, region at x0 + lead)
 constexpr int kRegAccThreads = 128;                // 16 rows r1 x 8 column pairs
 constexpr int kRegAccWarps = kRegAccThreads / 32;  // warp w owns rows 4w .. 4w + 3
 constexpr int kRegAccA = 9;                        // a_d < T_d <= 9
@@ -757,13 +782,18 @@ constexpr int kRegAccKeys = kRegAccA * kRegAccA;   // (a0, a1)
 template <int K>
 struct RegAccStage {
   static constexpr int kPairs = K / 2;   // tap pairs per dimension
+  static constexpr int kWeightBytes = kItemCap * (K * 4 + kRegAccLines * 8 + 8 * 8);
+  static constexpr int kBoxBytes = kRegAccLines * kRegAccLines * kFlushPitch * 8;
   float4 rec[kItemCap][2];               // {t0, t1, t2, pk}, {re v, im v, key, rank}
-  float w0s[kItemCap][K];                // w0, by slot
-  f32x2 vw1[kItemCap][kRegAccLines];     // v w1[r - a1], by slot
-  float2 w2s[kItemCap][8];               // cc -> (w2[cc - a2], w2[cc + 8 - a2]), by slot
   int count[kRegAccKeys];
   int start[kRegAccKeys + 1];
   f32x2 coef[3][kPairs][K + 1];          // (tap 2 tp, tap 2 tp + 1) coefficient pairs, degree K
+  // the weights of the current item; the flush box overlays them
+  alignas(128) float w0s[kItemCap][K];   // w0, by slot
+  f32x2 vw1[kItemCap][kRegAccLines];     // v w1[r - a1], by slot
+  float2 w2s[kItemCap][8];               // cc -> (w2[cc - a2], w2[cc + 8 - a2]), by slot
+  unsigned char pad[kBoxBytes > kWeightBytes ? kBoxBytes - kWeightBytes : 16];
+  __device__ float2* box() { return reinterpret_cast<float2*>(&w0s[0][0]); }
 };
 
 // Compensation terms of the accumulators (COMP: one per accumulator; else
@@ -819,7 +849,8 @@ __device__ __forceinline__ void regacc_bin(const RegAccStage<K>& st, int lo, int
 template <int K, bool COMP>
 __global__ void __launch_bounds__(kRegAccThreads, COMP ? 2 : 4)
     scatter3d_regacc_kernel(Geometry g, float2* __restrict__ grid, NodeArrays na,
-                            const float* __restrict__ poly, const float2* __restrict__ fhat) {
+                            const float* __restrict__ poly, const float2* __restrict__ fhat,
+                            const __grid_constant__ CUtensorMap rmap, int tma_on) {
   using Stage = RegAccStage<K>;
   constexpr int P = Stage::kPairs;
   constexpr int kPerIter = 32 / P;  // nodes per warp and weight iteration
@@ -842,6 +873,8 @@ __global__ void __launch_bounds__(kRegAccThreads, COMP ? 2 : 4)
   const int64_t M = g.M;
   const float* frac = reinterpret_cast<const float*>(na.frac);
   for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;
+  float2* box = st.box();
+  const bool tma_cta = tma_on && (smem_u32(box) & 127) == 0;
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 item = na.items[it];
@@ -866,6 +899,12 @@ __global__ void __launch_bounds__(kRegAccThreads, COMP ? 2 : 4)
       const int rank = atomicAdd(&st.count[key], 1);
       st.rec[i][0] = make_float4(t[0], t[1], t[2], __int_as_float(a[0] | (a[1] << 8) | (a[2] << 16)));
       st.rec[i][1] = make_float4(v.x, v.y, __int_as_float(key), __int_as_float(rank));
+    }
+    if (tma_cta) {
+      // the previous item's box reduction has read shared memory before the
+      // weight arrays it overlays are written again
+      if (tid == 0) bulk_wait_read();
+      __syncthreads();
     }
     {
       // clear the shifted rows of the slots in use (vw1: 8 float4, w2s: 4 float4 per slot)
@@ -964,7 +1003,31 @@ __global__ void __launch_bounds__(kRegAccThreads, COMP ? 2 : 4)
         for (int r = 0; r < kRegAccLines; ++r) acc[h][r] = add2(acc[h][r], cp.c[h][r]);
     }
 
-    // add the region to the grid (periodic wrap only here)
+    // add the region to the grid: one bulk tensor reduction of a box 18
+    // points wide starting at the even x0 = start[2] - lead (columns outside
+    // the region carry zeros) where the region lies inside the grid
+    const int lead = start[2] & 1, x0 = start[2] - lead;
+    const bool by_tma = tma_cta && x0 >= 0 && x0 + kFlushPitch <= g.Nt[2] && start[1] >= 0 &&
+                        start[1] + L1 <= g.Nt[1] && start[0] >= 0 && start[0] + L0 <= g.Nt[0];
+    if (by_tma) {
+      __syncthreads();  // every warp is done with the weight arrays the box overlays
+      if (r1 < L1) {
+#pragma unroll
+        for (int r = 0; r < kRegAccLines; ++r) {
+          if (r < L0) {
+            float2* row = box + (r * L1 + r1) * kFlushPitch;
+            row[cc + lead] = unpack2(acc[0][r]);
+            row[cc + 8 + lead] = unpack2(acc[1][r]);
+            if (cc == 0) row[lead ? 0 : 16] = make_float2(0.f, 0.f);
+            if (cc == 1) row[17] = make_float2(0.f, 0.f);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) tma_reduce_add_box(&rmap, box, 2 * x0, start[1], start[0]);
+      continue;
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int c = cc + 8 * h;
@@ -981,6 +1044,7 @@ __global__ void __launch_bounds__(kRegAccThreads, COMP ? 2 : 4)
       }
     }
   }
+  if (tma_cta && tid == 0) bulk_wait_all();
 }
 
 bool regacc_supported(const Geometry& g) {
@@ -1122,6 +1186,40 @@ bool region_map(const Geometry& g, const void* grid, CUtensorMap* map) {
   return true;
 }
 
+// NFFT_GB300_SCATTER_TMA=0 keeps every scatter flush on vector global
+// reductions (read at each launch, like NFFT_GB300_GATHER_TMA).
+bool use_flush_tma() {
+  const char* e = getenv("NFFT_GB300_SCATTER_TMA");
+  return !(e && strcmp(e, "0") == 0);
+}
+
+// The grid as FP32 (real, imaginary interleaved) for the scatter's box
+// reductions: box = 2 * kFlushPitch floats x L1 x L0.
+bool flush_map(const Geometry& g, const void* grid, CUtensorMap* map) {
+  memset(map, 0, sizeof(*map));
+  if (!use_flush_tma() || ((uintptr_t)grid & 15)) return false;
+  const int box[3] = {2 * kFlushPitch, g.L[1], g.L[0]};
+  const int dim[3] = {2 * g.Nt[2], g.Nt[1], g.Nt[0]};
+  for (int d = 0; d < 3; ++d)
+    if (box[d] > 256 || box[d] > dim[d]) return false;
+  if ((g.Nt[2] * sizeof(float2)) % 16 != 0) return false;
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t gdim[3] = {(cuuint64_t)dim[0], (cuuint64_t)dim[1], (cuuint64_t)dim[2]};
+  const cuuint64_t gstride[2] = {(cuuint64_t)g.Nt[2] * sizeof(float2),
+                                 (cuuint64_t)g.Nt[1] * g.Nt[2] * sizeof(float2)};
+  const cuuint32_t bdim[3] = {(cuuint32_t)box[0], (cuuint32_t)box[1], (cuuint32_t)box[2]};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(grid), gdim, gstride, bdim,
+                        estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    memset(map, 0, sizeof(*map));
+    return false;
+  }
+  return true;
+}
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t smem) {
   if (smem > 48 * 1024)
@@ -1225,8 +1323,11 @@ cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArray
     void* k = regacc_kernel(g.K, compensated != 0);
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
-    auto kern = reinterpret_cast<void (*)(Geometry, float2*, NodeArrays, const float*, const float2*)>(k);
-    kern<<<ctas, kRegAccThreads, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat);
+    CUtensorMap map;
+    const int tma_on = flush_map(g, grid, &map) ? 1 : 0;
+    auto kern = reinterpret_cast<void (*)(Geometry, float2*, NodeArrays, const float*, const float2*,
+                                          const CUtensorMap, int)>(k);
+    kern<<<ctas, kRegAccThreads, smem, s>>>(g, (float2*)grid, na, poly, (const float2*)fhat, map, tma_on);
     return cudaGetLastError();
   }
   const size_t smem = smem_bytes(g);
