@@ -289,12 +289,12 @@ void default_tile(const nfft_plan* p, int64_t* T) {
                         !(p->flags & (NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
   const int64_t pref6[kMaxD] = {5, 5, 5};
   // 2D m = 4 complex64: the warp-per-item kernels take regions of at most
-  // 16 x 32 cells; 9 x 25 tiles for large grids (measured best on the batched
-  // workload), 8 x 8 when that would leave fewer than 32 items per SM (512^2:
-  // 1.31 against 1.16 G nodes/s for gather + scatter)
+  // 16 x 32 cells; 9 x 25 tiles (measured best on the batched workload, and
+  // at 512^2 with 7.7 tiles per SM: 1.67 against 1.59 G nodes/s for gather +
+  // scatter), 8 x 8 when that would leave fewer than 7 tiles per SM
   const bool m4_2d = p->D == 2 && p->m == 4 && p->K == 8 && p->dtype == NFFT_C64 &&
                      !(p->flags & (NFFT_FLAG_CLOSED_SUPPORT | NFFT_FLAG_WIDE_WINDOW));
-  const bool big2d = p->D == 2 && (double)p->Nt[0] * (double)p->Nt[1] >= 225.0 * 32.0 * (double)p->sms;
+  const bool big2d = p->D == 2 && (double)p->Nt[0] * (double)p->Nt[1] >= 225.0 * 7.0 * (double)p->sms;
   const int64_t pref2[kMaxD] = {big2d ? 9 : 8, big2d ? 25 : 8, 1};
   for (int d = 0; d < p->D; ++d) {
     int64_t cap = p->Nt[d] - p->K + 1;  // keeps region coordinates within [-N~, 2 N~)
