@@ -80,15 +80,17 @@ extern "C" {
 /* Run the correction + zero-pad + FFT steps of Algorithm 1 and the inverse
    FFT + crop + correction steps of Algorithm 2 as the separate correction
    kernels around a full cuFFT transform even where the plan
-   qualifies for the pruned FFT (see nfft_step_pad_fft). */
+   qualifies for the pruned FFT or the direct sums (see nfft_step_pad_fft). */
 #define NFFT_FLAG_LIBRARY_FFT     0x10u
 
 /* Window values (Sec. 3.7.4).  Without these flags complex64 plans use the
-   specialised 1D-3D kernels, which take the window from its POLYNOMIAL
-   representation, and every other plan the generic kernels, which evaluate
-   it.  Each flag below selects the generic kernels (any D, m, dtype) with one
-   way of obtaining the window values, so that the three can be compared on
-   the same kernels; at most one may be given:
+   specialised 2D and 3D kernels where they apply (window from its
+   POLYNOMIAL representation), complex128 plans with m >= 6 the generic
+   kernels with the POLYNOMIAL window (its FP64 fit error is at the rounding
+   level there), and every other plan the generic kernels with the window
+   evaluated.  Each flag below selects the generic kernels (any D, m, dtype)
+   with one way of obtaining the window values, so that the three can be
+   compared on the same kernels; at most one may be given:
      DIRECT      the window evaluated per tap (sinh, sqrt);
      LINEAR      the lookup table psi_s = psi_Base(s/(S-2)), s < S,
                  S = m 2^{c_min(m,8)} + 2 with NFFT3's c = (3, 7, 9, 14, 17,

@@ -719,7 +719,14 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
       s = cuda_status(p, launch_build_lut(D, m, p->b, p->lut_S, dtype == NFFT_C128 ? nullptr : (float*)p->lut,
                                           dtype == NFFT_C128 ? (double*)p->lut : nullptr, p->stream));
   }
-  if (s == NFFT_OK && (flags & NFFT_FLAG_WINDOW_POLYNOMIAL)) {
+  // complex128 plans with m >= 6 and no window flag take the POLYNOMIAL
+  // window as well: there its FP64 fit error is about 1e-14 of the window
+  // peak, the rounding level of the direct form, and 2m + 1 Horner steps per
+  // tap cost GB300's narrow FP64 units less than the direct form's sqrt,
+  // exponential and division.  Below m = 6 the fit error (6e-9 at m = 4)
+  // would show against the exact window, so those keep direct evaluation.
+  const bool poly_default = dtype == NFFT_C128 && !(flags & kWindowFlags) && !closed && !wide && m >= 6;
+  if (s == NFFT_OK && ((flags & NFFT_FLAG_WINDOW_POLYNOMIAL) || poly_default)) {
     p->wmode = kWinPoly;
     if (dtype == NFFT_C128) s = dalloc(p, &p->poly64, sizeof(double) * D * p->K * (2 * m + 1));
   }
