@@ -85,7 +85,7 @@ extern "C" {
 
 /* Window values (Sec. 3.7.4).  Without these flags complex64 plans use the
    specialised 2D and 3D kernels where they apply (window from its
-   POLYNOMIAL representation), complex128 plans with m >= 6 the generic
+   POLYNOMIAL representation), complex128 plans with m >= 7 the generic
    kernels with the POLYNOMIAL window (its FP64 fit error is at the rounding
    level there), and every other plan the generic kernels with the window
    evaluated.  Each flag below selects the generic kernels (any D, m, dtype)
@@ -258,6 +258,22 @@ int nfft_step_fft_crop(nfft_plan *p, void *y);
  * the graphs.  Returns NFFT_ERR_INVALID_ARG for a null plan and a latched
  * error of the plan if it holds one. */
 int nfft_plan_set_graph(nfft_plan *p, int enable);
+
+/* Asynchronous host-buffer transforms: with enable != 0, nfft_forward and
+ * nfft_adjoint called with a HOST input and a HOST output return as soon as
+ * the work is enqueued: the input is copied to a plan-owned device buffer on
+ * a copy stream, the transform runs on the plan's stream, the result is
+ * copied back on a second copy stream, and the three are ordered by events.
+ * Two sets of device buffers alternate between calls, so consecutive calls
+ * overlap one call's copies with the previous call's kernels.  The host
+ * buffers must stay valid (inputs unchanged, outputs unread) until
+ * nfft_plan_sync returns, which waits for all three streams; page-locked
+ * host memory (cudaHostAlloc, torch pin_memory) is needed for the copies to
+ * overlap.  Calls with a device input or output keep the synchronous
+ * behaviour described at nfft_forward.  enable = 0 waits for the copy
+ * streams and restores it.  Returns NFFT_ERR_INVALID_ARG for a null plan and
+ * a latched error of the plan if it holds one. */
+int nfft_plan_set_async(nfft_plan *p, int enable);
 
 /* Which kernels the plan's transforms use (set by nfft_plan_create and
  * nfft_plan_set_tile): *fast_resample bit 0 = a specialised complex64

@@ -58,6 +58,7 @@ SIGNATURES = {
     "nfft_step_pad_fft": (_i, [_p, _p]),
     "nfft_step_fft_crop": (_i, [_p, _p]),
     "nfft_plan_set_graph": (_i, [_p, _i]),
+    "nfft_plan_set_async": (_i, [_p, _i]),
     "nfft_plan_paths": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "nfft_step_grad_gather": (_i, [_p, _p, _p]),
     "nfft_plan_autotune": (_i, [_p, _p, _i, _i64p]),
@@ -204,6 +205,10 @@ def nfft_step_fft_crop(plan, y_ptr):
 
 def nfft_plan_set_graph(plan, enable):
     return lib().nfft_plan_set_graph(_p(plan), int(bool(enable)))
+
+
+def nfft_plan_set_async(plan, enable):
+    return lib().nfft_plan_set_async(_p(plan), int(bool(enable)))
 
 
 def nfft_plan_paths(plan):

@@ -74,6 +74,15 @@ struct nfft_plan {
   void* stage[3] = {nullptr, nullptr, nullptr};
   size_t stage_bytes[3] = {0, 0, 0};
 
+  // asynchronous host-buffer transforms (nfft_plan_set_async): copies on
+  // their own streams, stage buffers double-buffered by call parity
+  bool async_mode = false;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  void* astage[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][in, out]
+  size_t astage_bytes[2][2] = {{0, 0}, {0, 0}};
+  int parity = 0;
+
   cufftHandle fft = 0;
   bool fft_ok = false;
   // graph mode: nfft_forward / nfft_adjoint captured once per pair of device
@@ -569,6 +578,42 @@ int run_direction(nfft_plan* p, int dir, const void* in, void* out) {
   return NFFT_OK;
 }
 
+// Asynchronous host-buffer transform: H2D on p->h2d, the transform on the
+// plan stream, D2H on p->d2h, ordered by events; the stage buffers of one
+// parity are reused only after the previous call of that parity has read
+// its input (ev_comp) and copied its output out (ev_out), so consecutive
+// calls overlap one call's copies with another's kernels.
+int run_async(nfft_plan* p, int dir, const void* in, size_t in_bytes, void* out, size_t out_bytes) {
+  const int k = p->parity;
+  const size_t need[2] = {in_bytes, out_bytes};
+  for (int b = 0; b < 2; ++b) {
+    if (p->astage_bytes[k][b] < need[b]) {
+      NFFT_CK(p, cudaStreamSynchronize(p->stream));  // a replaced buffer may still be in use
+      NFFT_CK(p, cudaStreamSynchronize(p->h2d));
+      NFFT_CK(p, cudaStreamSynchronize(p->d2h));
+      dfree(p->astage[k][b]);
+      p->astage[k][b] = nullptr;
+      p->astage_bytes[k][b] = 0;
+      int s = dalloc(p, &p->astage[k][b], need[b]);
+      if (s != NFFT_OK) return s;
+      p->astage_bytes[k][b] = need[b];
+    }
+  }
+  p->parity ^= 1;
+  NFFT_CK(p, cudaStreamWaitEvent(p->h2d, p->ev_comp[k], 0));
+  NFFT_CK(p, cudaMemcpyAsync(p->astage[k][0], in, in_bytes, cudaMemcpyHostToDevice, p->h2d));
+  NFFT_CK(p, cudaEventRecord(p->ev_in[k], p->h2d));
+  NFFT_CK(p, cudaStreamWaitEvent(p->stream, p->ev_in[k], 0));
+  NFFT_CK(p, cudaStreamWaitEvent(p->stream, p->ev_out[k], 0));
+  int s = run_plain(p, dir, p->astage[k][0], p->astage[k][1]);
+  if (s != NFFT_OK) return s;
+  NFFT_CK(p, cudaEventRecord(p->ev_comp[k], p->stream));
+  NFFT_CK(p, cudaStreamWaitEvent(p->d2h, p->ev_comp[k], 0));
+  NFFT_CK(p, cudaMemcpyAsync(out, p->astage[k][1], out_bytes, cudaMemcpyDeviceToHost, p->d2h));
+  NFFT_CK(p, cudaEventRecord(p->ev_out[k], p->d2h));
+  return NFFT_OK;
+}
+
 int run_grad_gather(nfft_plan* p, const void* cot, void* gk) {
   if (p->grad_ctas <= 0 && p->ctas[3] <= 0) return NFFT_ERR_UNSUPPORTED;
   Geometry g = make_geometry(p);
@@ -604,8 +649,19 @@ int nfft_plan_destroy(nfft_plan* p) {
   if (!p) return NFFT_OK;
   DeviceGuard guard(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->h2d) cudaStreamSynchronize(p->h2d);
+  if (p->d2h) cudaStreamSynchronize(p->d2h);
   drop_graphs(p);
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+  for (int k = 0; k < 2; ++k) {
+    if (p->ev_in[k]) cudaEventDestroy(p->ev_in[k]);
+    if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
+    if (p->ev_out[k]) cudaEventDestroy(p->ev_out[k]);
+    dfree(p->astage[k][0]);
+    dfree(p->astage[k][1]);
+  }
+  if (p->h2d) cudaStreamDestroy(p->h2d);
+  if (p->d2h) cudaStreamDestroy(p->d2h);
   if (p->fft_ok) cufftDestroy(p->fft);
   full_destroy(p->full);
   void* bufs[] = {p->grid, p->fft_tw, p->dft_tw, p->beta64, p->beta32, p->poly, p->poly64, p->lut, p->cell, p->frac, p->perm,
@@ -719,13 +775,15 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
       s = cuda_status(p, launch_build_lut(D, m, p->b, p->lut_S, dtype == NFFT_C128 ? nullptr : (float*)p->lut,
                                           dtype == NFFT_C128 ? (double*)p->lut : nullptr, p->stream));
   }
-  // complex128 plans with m >= 6 and no window flag take the POLYNOMIAL
+  // complex128 plans with m >= 7 and no window flag take the POLYNOMIAL
   // window as well: there its FP64 fit error is about 1e-14 of the window
   // peak, the rounding level of the direct form, and 2m + 1 Horner steps per
   // tap cost GB300's narrow FP64 units less than the direct form's sqrt,
-  // exponential and division.  Below m = 6 the fit error (6e-9 at m = 4)
-  // would show against the exact window, so those keep direct evaluation.
-  const bool poly_default = dtype == NFFT_C128 && !(flags & kWindowFlags) && !closed && !wide && m >= 6;
+  // exponential and division.  Below m = 7 the fit error would show against
+  // the exact window (6e-9 at m = 4; at m = 6 and sigma = 1.25 it put a 3D
+  // adjoint at 4.4e-11 against a rounding bound of 4.2e-11), so those keep
+  // direct evaluation.
+  const bool poly_default = dtype == NFFT_C128 && !(flags & kWindowFlags) && !closed && !wide && m >= 7;
   if (s == NFFT_OK && ((flags & NFFT_FLAG_WINDOW_POLYNOMIAL) || poly_default)) {
     p->wmode = kWinPoly;
     if (dtype == NFFT_C128) s = dalloc(p, &p->poly64, sizeof(double) * D * p->K * (2 * m + 1));
@@ -807,6 +865,8 @@ int nfft_forward(nfft_plan* p, const void* f, void* fhat) {
   if (!p->has_nodes) return NFFT_ERR_NO_NODES;
   if (!f || (!fhat && p->M > 0)) return NFFT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
+  if (p->async_mode && p->M > 0 && !is_device_pointer(f) && !is_device_pointer(fhat))
+    return run_async(p, 0, f, (size_t)prod_N(p) * cplx_size(p), fhat, (size_t)p->M * cplx_size(p));
   const void* fd = nullptr;
   OutputBinding ob;
   if ((s = device_input(p, 0, f, (size_t)prod_N(p) * cplx_size(p), &fd)) != NFFT_OK) return s;
@@ -822,6 +882,8 @@ int nfft_adjoint(nfft_plan* p, const void* fhat, void* y) {
   if (!p->has_nodes) return NFFT_ERR_NO_NODES;
   if (!y || (!fhat && p->M > 0)) return NFFT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
+  if (p->async_mode && p->M > 0 && !is_device_pointer(fhat) && !is_device_pointer(y))
+    return run_async(p, 1, fhat, (size_t)p->M * cplx_size(p), y, (size_t)prod_N(p) * cplx_size(p));
   const void* fd = nullptr;
   OutputBinding ob;
   if ((s = device_input(p, 0, fhat, (size_t)p->M * cplx_size(p), &fd)) != NFFT_OK) return s;
@@ -852,6 +914,8 @@ int nfft_plan_sync(nfft_plan* p) {
   if (!p) return NFFT_ERR_INVALID_ARG;
   DeviceGuard guard(p->device);
   cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess && p->h2d) e = cudaStreamSynchronize(p->h2d);
+  if (e == cudaSuccess && p->d2h) e = cudaStreamSynchronize(p->d2h);
   if (e != cudaSuccess) return cuda_status(p, e);
   if (p->fast_gather && p->D == 3) {
     const int t = fast3d_take_wait_timeout();
@@ -1066,6 +1130,27 @@ int nfft_plan_set_graph(nfft_plan* p, int enable) {
   DeviceGuard guard(p->device);
   if (!enable) drop_graphs(p);
   p->graph_mode = enable != 0;
+  return NFFT_OK;
+}
+
+int nfft_plan_set_async(nfft_plan* p, int enable) {
+  int s;
+  if (!ready(p, &s)) return s;
+  DeviceGuard guard(p->device);
+  if (enable && !p->h2d) {
+    NFFT_CK(p, cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking));
+    NFFT_CK(p, cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      NFFT_CK(p, cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming));
+      NFFT_CK(p, cudaEventCreateWithFlags(&p->ev_comp[k], cudaEventDisableTiming));
+      NFFT_CK(p, cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming));
+    }
+  }
+  if (!enable && p->h2d) {
+    NFFT_CK(p, cudaStreamSynchronize(p->h2d));
+    NFFT_CK(p, cudaStreamSynchronize(p->d2h));
+  }
+  p->async_mode = enable != 0;
   return NFFT_OK;
 }
 

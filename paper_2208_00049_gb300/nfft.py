@@ -190,6 +190,12 @@ class Plan:
         """Replay nfft_forward / nfft_adjoint from captured CUDA graphs (device buffers)."""
         B.check(B.nfft_plan_set_graph(self.handle, enable), "nfft_plan_set_graph")
 
+    def set_async(self, enable=True):
+        """Host-buffer nfft_forward / nfft_adjoint return once enqueued, with
+        their copies overlapping the previous call's kernels; results are
+        ready after sync()."""
+        B.check(B.nfft_plan_set_async(self.handle, enable), "nfft_plan_set_async")
+
     def paths(self):
         """{'fast_gather', 'fast_scatter', 'pruned_fft', 'fft_form'}: which
         specialised kernels this plan's transforms run (fft_form: 'library',

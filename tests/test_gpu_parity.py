@@ -709,3 +709,42 @@ def test_graph_mode_full_matrix_takes_direct_path():
         plan.forward(f, out=fh)
         assert_close(fh.cpu().numpy(), onfft.forward(k, case["f"], 2.0, 3), TOL["c128"], "FULL, graph mode")
     plan.close()
+
+
+@pytest.mark.parametrize("N,M,dt", [((20, 18, 16), 3000, "c64"), ((48, 40), 2500, "c128"), ((128, 128, 128), 20000, "c64")])
+def test_async_host_transforms(N, M, dt):
+    """nfft_plan_set_async: several host-buffer forward / adjoint calls in
+    flight at once (alternating stage buffers, copies on their own streams)
+    give the synchronous path's results once nfft_plan_sync returns; a call
+    with a device buffer keeps the synchronous path."""
+    cases = [inputs.small_case(N, M, seed=131 + i, m=4) for i in range(3)]
+    plan = _plan(N, M, 2.0, 4, dt)
+    plan.set_nodes(to_dev(cases[0]["k"], torch.float64))
+    ct = cdtype(dt)
+    want = []
+    for c in cases:
+        fh = plan.forward(torch.from_numpy(c["f"]).to(ct)).numpy().copy()
+        y = plan.adjoint(torch.from_numpy(c["w"]).to(ct)).numpy().copy()
+        want.append((fh, y))
+    plan.set_async(True)
+    f_h = [torch.from_numpy(c["f"]).to(ct).pin_memory() for c in cases]
+    w_h = [torch.from_numpy(c["w"]).to(ct).pin_memory() for c in cases]
+    fh_h = [torch.empty(M, dtype=ct).pin_memory() for _ in cases]
+    y_h = [torch.empty(N, dtype=ct).pin_memory() for _ in cases]
+    for rep in range(2):
+        for i in range(3):
+            plan.forward(f_h[i], out=fh_h[i])
+            plan.adjoint(w_h[i], out=y_h[i])
+        plan.sync()
+        tol = 1e-6 if dt == "c64" else 1e-14
+        for i in range(3):
+            assert_close(fh_h[i].numpy(), want[i][0], tol, "async forward %d" % i)
+            assert_close(y_h[i].numpy(), want[i][1], tol, "async adjoint %d" % i)
+    # a device output keeps the synchronous path
+    fd = torch.empty(M, dtype=ct, device="cuda")
+    plan.forward(f_h[1], out=fd)
+    assert_close(fd.cpu().numpy(), want[1][0], 1e-6 if dt == "c64" else 1e-14, "async mode, device output")
+    plan.set_async(False)
+    plan.forward(f_h[2], out=fh_h[2])
+    assert_close(fh_h[2].numpy(), want[2][0], 1e-6 if dt == "c64" else 1e-14, "after async mode")
+    plan.close()
