@@ -230,24 +230,194 @@ __global__ void build_twiddles_kernel(float2* tw) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// The 2D form, N~_d = 2 N_d = 512 (N = 256^2, complex64): passes A (rows
+// i0 < N: correction, DFT along dim 1) and B (columns: DFT along dim 0) for
+// the forward, B' and A' for the adjoint.  A 512-point line DFT is 32 x 16:
+// thread r of the line's 16 holds x[16 n1 + r], n1 = 0..31, and takes the
+// 32-point DFT over n1 (two 16-point DFTs and a radix-2 step), multiplies by
+// the twiddle, and after a transpose in shared memory takes the 16-point
+// DFTs over r of k1 = r and k1 = r + 16, giving X[k1 + 32 k2].  The fftshift
+// phases fold into the twiddles as in 3D: i^l = i^k1 for l = k1 + 32 k2 and
+// (-i)^n = (-i)^r for n = 16 n1 + r, so
+//   forward  W512^(r k1) i^k1,   inverse  conj(W512^(r k1)) (-i)^r.
+constexpr int kLen2 = 512;
+constexpr int kHalf2 = 256;
+constexpr int kLines2 = 4;                 // lines per CTA
+constexpr int kThreads2 = 16 * kLines2;
+constexpr int kColPad2 = 4;                // complex of padding per k1 block (column passes)
+constexpr int kT2 = kLines2 * 32 * 17 > 32 * (16 * kLines2 + kColPad2) ? kLines2 * 32 * 17
+                                                                        : 32 * (16 * kLines2 + kColPad2);
+
+__device__ __forceinline__ int row_t2(int line, int k1, int r) { return line * (32 * 17) + k1 * 17 + r; }
+__device__ __forceinline__ int col_t2(int line, int k1, int r) {
+  return k1 * (16 * kLines2 + kColPad2) + r * kLines2 + line;
+}
+
+// exp(-2 pi i k/32) = (cos(pi k/16), -sin(pi k/16)), k = 0..15
+__constant__ float2 kW32[16] = {
+    {1.00000000000000000f, 0.00000000000000000f},  {0.98078528040323043f, 0.19509032201612825f},
+    {0.92387953251128674f, 0.38268343236508978f},  {0.83146961230254524f, 0.55557023301960218f},
+    {0.70710678118654757f, 0.70710678118654746f},  {0.55557023301960229f, 0.83146961230254524f},
+    {0.38268343236508984f, 0.92387953251128674f},  {0.19509032201612833f, 0.98078528040323043f},
+    {0.00000000000000006f, 1.00000000000000000f},  {-0.19509032201612819f, 0.98078528040323043f},
+    {-0.38268343236508973f, 0.92387953251128674f}, {-0.55557023301960196f, 0.83146961230254546f},
+    {-0.70710678118654746f, 0.70710678118654757f}, {-0.83146961230254535f, 0.55557023301960218f},
+    {-0.92387953251128674f, 0.38268343236508989f}, {-0.98078528040323043f, 0.19509032201612861f}};
+
+// 32-point DFT of x[n], n = 0..31 (W32 = exp(-+2 pi i/32)), natural order
+// out: y[k].  Even and odd halves by dft16, then y[k], y[k + 16] = E[k] +- W32^k O[k].
+template <bool INV>
+__device__ __forceinline__ void dft32(const float2* x, float2* y) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    e[j] = x[2 * j];
+    o[j] = x[2 * j + 1];
+  }
+  dft16<INV>(e);
+  dft16<INV>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float2 c = kW32[k];
+    const float2 w = INV ? c : make_float2(c.x, -c.y);
+    const float2 t = cmul(o[perm16(k)], w);
+    y[k] = cadd(e[perm16(k)], t);
+    y[k + 16] = csub(e[perm16(k)], t);
+  }
+}
+
+// The 512-point line DFT: on entry x[n1] = x_line[16 n1 + r], on return
+// x[perm16(k2)] = X_line[r + 32 k2] and x[16 + perm16(k2)] = X_line[r + 16 + 32 k2]
+// (phases included).  One barrier.
+template <bool INV, bool COL>
+__device__ __forceinline__ void line_dft512(float2* x, float2* T, const float2* __restrict__ tw, int line, int r) {
+  float2 y[32];
+  dft32<INV>(x, y);
+  const float2* twr = tw + (INV ? kLen2 : 0) + r;
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1) {
+    const float2 v = cmul(y[k1], __ldg(twr + 16 * k1));
+    T[COL ? col_t2(line, k1, r) : row_t2(line, k1, r)] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    x[q] = T[COL ? col_t2(line, r, q) : row_t2(line, r, q)];
+    x[16 + q] = T[COL ? col_t2(line, r + 16, q) : row_t2(line, r + 16, q)];
+  }
+  dft16<INV>(x);
+  dft16<INV>(x + 16);
+}
+
+// Pass A (forward): rows i0 < N of f times the correction, DFT along dim 1,
+// into grid rows i0.
+__global__ void __launch_bounds__(kThreads2)
+    fwd_rows2d_kernel(const float2* __restrict__ f, const float* __restrict__ beta0, const float* __restrict__ beta1,
+                      const float2* __restrict__ tw, float2* __restrict__ grid) {
+  __shared__ float2 T[kT2];
+  const int t = threadIdx.x, line = t >> 4, r = t & 15;
+  const int i0 = blockIdx.x * kLines2 + line;
+  const float2* src = f + (int64_t)i0 * kHalf2 + r;
+  const float b0 = beta0[i0];
+  float2 x[32];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) x[n1] = cscale(src[16 * n1], b0 * beta1[16 * n1 + r]);
+#pragma unroll
+  for (int n1 = 16; n1 < 32; ++n1) x[n1] = make_float2(0.f, 0.f);
+  line_dft512<false, false>(x, T, tw, line, r);
+  float2* dst = grid + (int64_t)i0 * kLen2 + r;
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    dst[32 * k2] = x[perm16(k2)];
+    dst[32 * k2 + 16] = x[16 + perm16(k2)];
+  }
+}
+
+// Pass B (forward: rows < N in, all N~ rows out) and B' (adjoint: all N~
+// rows in, rows < N out) over kLines2 adjacent columns, in place.
+template <bool INV>
+__global__ void __launch_bounds__(kThreads2)
+    cols2d_kernel(float2* __restrict__ grid, const float2* __restrict__ tw) {
+  __shared__ float2 T[kT2];
+  constexpr int NIN1 = INV ? 32 : 16;   // stage-1 inputs per thread
+  constexpr int NOUT2 = INV ? 8 : 16;   // stage-2 outputs per thread and k1 half
+  const int t = threadIdx.x, line = t % kLines2, r = t / kLines2;
+  float2* col = grid + blockIdx.x * kLines2 + line;
+  float2 x[32];
+#pragma unroll
+  for (int n1 = 0; n1 < 32; ++n1) x[n1] = n1 < NIN1 ? col[(int64_t)(16 * n1 + r) * kLen2] : make_float2(0.f, 0.f);
+  line_dft512<INV, true>(x, T, tw, line, r);
+#pragma unroll
+  for (int k2 = 0; k2 < NOUT2; ++k2) {
+    col[(int64_t)(r + 32 * k2) * kLen2] = x[perm16(k2)];
+    col[(int64_t)(r + 16 + 32 * k2) * kLen2] = x[16 + perm16(k2)];
+  }
+}
+
+// Pass A' (adjoint): rows i0 < N of the grid, inverse DFT along dim 1, the
+// N outputs times the correction into y.
+__global__ void __launch_bounds__(kThreads2)
+    adj_rows2d_kernel(const float2* __restrict__ grid, const float* __restrict__ beta0,
+                      const float* __restrict__ beta1, const float2* __restrict__ tw, float2* __restrict__ y) {
+  __shared__ float2 T[kT2];
+  const int t = threadIdx.x, line = t >> 4, r = t & 15;
+  const int i0 = blockIdx.x * kLines2 + line;
+  const float2* src = grid + (int64_t)i0 * kLen2 + r;
+  float2 x[32];
+#pragma unroll
+  for (int n1 = 0; n1 < 32; ++n1) x[n1] = src[16 * n1];
+  line_dft512<true, false>(x, T, tw, line, r);
+  const float b0 = beta0[i0];
+  float2* dst = y + (int64_t)i0 * kHalf2 + r;
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) {
+    dst[32 * k2] = cscale(x[perm16(k2)], b0 * beta1[r + 32 * k2]);
+    dst[32 * k2 + 16] = cscale(x[16 + perm16(k2)], b0 * beta1[r + 16 + 32 * k2]);
+  }
+}
+
+// tw[16 k1 + r]       = exp(-2 pi i r k1/512) i^k1      (forward)
+// tw[512 + 16 k1 + r] = exp(+2 pi i r k1/512) (-i)^r    (inverse)
+// in FP64, then rounded.
+__global__ void build_twiddles2d_kernel(float2* tw) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < 2 * kLen2) {
+    const int inv = j >= kLen2, e = j & (kLen2 - 1), k1 = e >> 4, r = e & 15;
+    const double turn = 2.0 * M_PI / (double)kLen2;
+    const double a = inv ? turn * (double)(r * k1) - 0.5 * M_PI * (double)r
+                         : -turn * (double)(r * k1) + 0.5 * M_PI * (double)k1;
+    tw[j] = make_float2((float)cos(a), (float)sin(a));
+  }
+}
+
 }  // namespace
 
 bool pruned_fft_supported(int D, const int* N, const int* Nt) {
+  if (D == 2) return N[0] == kHalf2 && N[1] == kHalf2 && Nt[0] == kLen2 && Nt[1] == kLen2;
   if (D != 3) return false;
   for (int d = 0; d < 3; ++d)
     if (N[d] != kHalf || Nt[d] != kLen) return false;
   return true;
 }
 
-cudaError_t build_fft_twiddles(float2* tw, cudaStream_t s) {
-  static_assert(kPrunedFftTwiddles == 2 * kLen, "twiddle table size");
-  build_twiddles_kernel<<<2, kLen, 0, s>>>(tw);
+cudaError_t build_fft_twiddles(int D, float2* tw, cudaStream_t s) {
+  static_assert(kPrunedFftTwiddles >= 2 * kLen && kPrunedFftTwiddles >= 2 * kLen2, "twiddle table size");
+  if (D == 2)
+    build_twiddles2d_kernel<<<4, kLen2 / 2, 0, s>>>(tw);
+  else
+    build_twiddles_kernel<<<2, kLen, 0, s>>>(tw);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pruned_forward(const void* f, const float* const* beta, const float2* tw, void* grid,
+cudaError_t launch_pruned_forward(int D, const void* f, const float* const* beta, const float2* tw, void* grid,
                                   cudaStream_t s) {
   float2* g = (float2*)grid;
+  if (D == 2) {
+    fwd_rows2d_kernel<<<kHalf2 / kLines2, kThreads2, 0, s>>>((const float2*)f, beta[0], beta[1], tw, g);
+    cols2d_kernel<false><<<kLen2 / kLines2, kThreads2, 0, s>>>(g, tw);
+    return cudaGetLastError();
+  }
   fwd_rows_kernel<<<kHalf * kHalf / kLines, kThreads, 0, s>>>((const float2*)f, beta[0], beta[1], beta[2], tw, g);
   // B: lines (i0 < N, l2), element stride N~ (dim 1)
   cols_kernel<false><<<kHalf * (kLen / kLines), kThreads, 0, s>>>(g, (int64_t)kLen * kLen, kLen, tw);
@@ -256,8 +426,14 @@ cudaError_t launch_pruned_forward(const void* f, const float* const* beta, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_pruned_adjoint(void* grid, const float* const* beta, const float2* tw, void* y, cudaStream_t s) {
+cudaError_t launch_pruned_adjoint(int D, void* grid, const float* const* beta, const float2* tw, void* y,
+                                  cudaStream_t s) {
   float2* g = (float2*)grid;
+  if (D == 2) {
+    cols2d_kernel<true><<<kLen2 / kLines2, kThreads2, 0, s>>>(g, tw);
+    adj_rows2d_kernel<<<kHalf2 / kLines2, kThreads2, 0, s>>>(g, beta[0], beta[1], tw, (float2*)y);
+    return cudaGetLastError();
+  }
   // C': lines (l1, l2) along dim 0, keep i0 < N
   cols_kernel<true><<<kLen * (kLen / kLines), kThreads, 0, s>>>(g, kLen, (int64_t)kLen * kLen, tw);
   // B': lines (i0 < N, l2) along dim 1, keep i1 < N

@@ -198,15 +198,17 @@ cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const Node
 cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArrays& na,
                                   const float* poly, const void* fhat, int compensated, int ctas, cudaStream_t s);
 
-// Pruned 3D FFT with the resampling correction fused in, N~_d = 2 N_d = 256,
-// complex64 (fft_pruned.cu).  `tw` holds kPrunedFftTwiddles inter-stage
-// twiddles (build_fft_twiddles); beta[d] are the FP32 correction vectors.
-constexpr int kPrunedFftTwiddles = 512;
+// Pruned FFT with the resampling correction fused in, complex64
+// (fft_pruned.cu): 3D with N~_d = 2 N_d = 256 and 2D with N~_d = 2 N_d = 512.
+// `tw` holds the inter-stage twiddles of that form (build_fft_twiddles,
+// at most kPrunedFftTwiddles); beta[d] are the FP32 correction vectors.
+constexpr int kPrunedFftTwiddles = 1024;
 bool pruned_fft_supported(int D, const int* N, const int* Nt);
-cudaError_t build_fft_twiddles(float2* tw, cudaStream_t s);
-cudaError_t launch_pruned_forward(const void* f, const float* const* beta, const float2* tw, void* grid,
+cudaError_t build_fft_twiddles(int D, float2* tw, cudaStream_t s);
+cudaError_t launch_pruned_forward(int D, const void* f, const float* const* beta, const float2* tw, void* grid,
                                   cudaStream_t s);
-cudaError_t launch_pruned_adjoint(void* grid, const float* const* beta, const float2* tw, void* y, cudaStream_t s);
+cudaError_t launch_pruned_adjoint(int D, void* grid, const float* const* beta, const float2* tw, void* y,
+                                  cudaStream_t s);
 
 // Small 1D complex128 plans (dft1d.cu): correction + pad + FFT and inverse
 // FFT + crop + correction as direct sums spread over every SM; `tw` holds

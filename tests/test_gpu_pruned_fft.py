@@ -43,6 +43,10 @@ def test_pruned_path_selection():
         ((128, 128, 64), "c64", 0, 2.0, False),
         ((128, 128, 128), "c64", 0, 1.5, False),
         ((128, 128), "c64", 0, 2.0, False),
+        ((256, 256), "c64", 0, 2.0, True),
+        ((256, 256), "c64", B.NFFT_FLAG_LIBRARY_FFT, 2.0, False),
+        ((256, 256), "c128", 0, 2.0, False),
+        ((256, 128), "c64", 0, 2.0, False),
     ]
     for N, dt, flags, sigma, want in cases:
         plan = _plan(N, 8, dt, flags, sigma)
@@ -168,4 +172,47 @@ def test_direct_sum_steps_match_oracle(N, sigma):
     ya = plan.adjoint(to_dev(case["w"], torch.complex128)).cpu().numpy()
     assert_close(fh, onfft.forward(case["k"], case["f"], sigma, 4), 1e-12, "forward")
     assert_close(ya, onfft.adjoint(case["k"], case["w"], N, sigma, 4), 1e-12, "adjoint")
+    plan.close()
+
+
+N2 = (256, 256)
+
+
+def test_pruned_2d_steps_match_oracle():
+    """The 2D pruned form (N~ = 2N = 512): correction + pad + FFT and inverse
+    FFT + crop + correction element by element on the full grid / output,
+    the whole transforms against the oracle, and agreement with the library
+    form."""
+    from paper_2208_00049_gb300 import binding as B
+    rng = np.random.default_rng(227)
+    p = onfft.Params(N2, 2.0, 4)
+    plan = _plan(N2, 8)
+    assert plan.paths()["pruned_fft"]
+    f = inputs.complex_normal(rng, N2)
+    plan.step_pad_fft(to_dev(f, torch.complex64))
+    got = plan.grid_tensor().cpu().numpy().astype(np.complex128) / _peak(p)
+    tol, tmax = tol_for(N2, 2.0, 4, "c64"), tol_max_for(N2, 2.0, 4, "c64")
+    assert_close(got, onfft.fft_forward(onfft.correction_pad(p, f)), tol, "2D pad_fft", tmax)
+    G = inputs.complex_normal(rng, p.Nt)
+    plan.grid_tensor().copy_(torch.from_numpy(G.astype(np.complex64)))
+    y = torch.empty(N2, dtype=torch.complex64, device="cuda")
+    plan.step_fft_crop(y)
+    got = y.cpu().numpy().astype(np.complex128) / _peak(p)
+    assert_close(got, onfft.crop_correction(p, onfft.fft_adjoint(G)), tol, "2D fft_crop", tmax)
+    plan.close()
+    grids = []
+    fd = to_dev(f, torch.complex64)
+    for flags in (0, B.NFFT_FLAG_LIBRARY_FFT):
+        pl = _plan(N2, 8, flags=flags)
+        pl.step_pad_fft(fd)
+        grids.append(pl.grid_tensor().cpu().numpy())
+        pl.close()
+    assert rel_l2(grids[0], grids[1]) <= 2e-6
+    case = inputs.small_case(N2, 20000, seed=229, m=4)
+    plan = _plan(N2, 20000)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    fh = plan.forward(to_dev(case["f"], torch.complex64)).cpu().numpy()
+    ya = plan.adjoint(to_dev(case["w"], torch.complex64)).cpu().numpy()
+    assert_close(fh, onfft.forward(case["k"], case["f"], 2.0, 4), tol, "2D forward")
+    assert_close(ya, onfft.adjoint(case["k"], case["w"], N2, 2.0, 4), tol, "2D adjoint")
     plan.close()
