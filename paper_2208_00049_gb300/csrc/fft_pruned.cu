@@ -391,31 +391,236 @@ __global__ void build_twiddles2d_kernel(float2* tw) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// The 3D form at sigma = 1.25: N~_d = 160, N_d = 128 (complex64).  The same
+// three passes per direction with 160-point line DFTs, 10 x 16: thread r of
+// the line's 16 holds x[16 n1 + r], n1 = 0..9, takes the 10-point DFT over
+// n1 (two 5-point DFTs and a radix-2 step), multiplies by W160^(r k1), and
+// after a transpose threads k1 < 10 take the 16-point DFT over r, giving
+// X[k1 + 10 k2].  N~ is not 2N here, so the fftshift of Sec. 3.5 is the
+// phase exp(2 pi i (N/2) l / N~) on output l (forward) and its conjugate on
+// input l (adjoint), applied per element from a table.
+constexpr int kLen3 = 160;
+constexpr int kHalf3 = 128;
+constexpr int kLines3 = 16;
+constexpr int kThreads3 = 16 * kLines3;
+constexpr int kT3 = kLines3 * 10 * 17 > 10 * 16 * kLines3 ? kLines3 * 10 * 17 : 10 * 16 * kLines3;
+static_assert(kT3 * 8 <= 48 * 1024, "static shared-memory launch");
+constexpr int kTw3Inv = kLen3;       // inverse twiddles at tw[160 + 16 k1 + r]
+constexpr int kTw3Phase = 2 * kLen3;  // phases at tw[320 + l]
+
+__device__ __forceinline__ int row_t3(int line, int k1, int r) { return line * (10 * 17) + k1 * 17 + r; }
+__device__ __forceinline__ int col_t3(int line, int k1, int r) { return k1 * (16 * kLines3) + r * kLines3 + line; }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// 5-point DFT (W5 = exp(-+2 pi i/5)) in place.
+template <bool INV>
+__device__ __forceinline__ void dft5(float2& x0, float2& x1, float2& x2, float2& x3, float2& x4) {
+  constexpr float c1 = 0.30901699437494745f, c2 = -0.80901699437494734f;
+  constexpr float s1 = 0.95105651629515353f, s2 = 0.58778525229247325f;
+  const float2 t1 = cadd(x1, x4), t2 = cadd(x2, x3), d1 = csub(x1, x4), d2 = csub(x2, x3);
+  const float2 a1 = make_float2(x0.x + c1 * t1.x + c2 * t2.x, x0.y + c1 * t1.y + c2 * t2.y);
+  const float2 a2 = make_float2(x0.x + c2 * t1.x + c1 * t2.x, x0.y + c2 * t1.y + c1 * t2.y);
+  const float2 e1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+  const float2 e2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+  // b = -+ i e
+  const float2 b1 = INV ? make_float2(-e1.y, e1.x) : make_float2(e1.y, -e1.x);
+  const float2 b2 = INV ? make_float2(-e2.y, e2.x) : make_float2(e2.y, -e2.x);
+  x0 = cadd(x0, cadd(t1, t2));
+  x1 = cadd(a1, b1);
+  x4 = csub(a1, b1);
+  x2 = cadd(a2, b2);
+  x3 = csub(a2, b2);
+}
+
+// 10-point DFT of x[n] (n = 0..9) into y[k], natural order: 5-point DFTs of
+// the even and odd elements, then y[k], y[k + 5] = E[k] +- W10^k O[k].
+template <bool INV>
+__device__ __forceinline__ void dft10(const float2* x, float2* y) {
+  constexpr float wc[5] = {1.0f, 0.80901699437494742f, 0.30901699437494745f, -0.30901699437494734f,
+                           -0.80901699437494734f};
+  constexpr float ws[5] = {0.0f, 0.58778525229247314f, 0.95105651629515353f, 0.95105651629515364f,
+                           0.58778525229247325f};
+  float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6], e4 = x[8];
+  float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7], o4 = x[9];
+  dft5<INV>(e0, e1, e2, e3, e4);
+  dft5<INV>(o0, o1, o2, o3, o4);
+  const float2 E[5] = {e0, e1, e2, e3, e4}, O[5] = {o0, o1, o2, o3, o4};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float2 w = make_float2(wc[k], INV ? ws[k] : -ws[k]);
+    const float2 t = cmul(O[k], w);
+    y[k] = cadd(E[k], t);
+    y[k + 5] = csub(E[k], t);
+  }
+}
+
+// The 160-point line DFT: on entry x[n1] = x_line[16 n1 + r] (n1 < 10, the
+// adjoint's input phase already applied), on return, for threads r < 10,
+// x[perm16(k2)] = X_line[r + 10 k2].  One barrier.
+template <bool INV, bool COL>
+__device__ __forceinline__ void line_dft160(float2* x, float2* T, const float2* __restrict__ tw, int line, int r) {
+  float2 y[10];
+  dft10<INV>(x, y);
+  const float2* twr = tw + (INV ? kTw3Inv : 0) + r;
+#pragma unroll
+  for (int k1 = 0; k1 < 10; ++k1) {
+    const float2 v = cmul(y[k1], __ldg(twr + 16 * k1));
+    T[COL ? col_t3(line, k1, r) : row_t3(line, k1, r)] = v;
+  }
+  __syncthreads();
+  if (r < 10) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = T[COL ? col_t3(line, r, q) : row_t3(line, r, q)];
+    dft16<INV>(x);
+  }
+}
+
+// Pass A (forward): rows (i0, i1) of f times the correction, DFT along dim 2,
+// with the output phase, into grid rows (i0, i1, :).
+__global__ void __launch_bounds__(kThreads3)
+    fwd_rows160_kernel(const float2* __restrict__ f, const float* __restrict__ beta0,
+                       const float* __restrict__ beta1, const float* __restrict__ beta2,
+                       const float2* __restrict__ tw, float2* __restrict__ grid) {
+  __shared__ float2 T[kT3];
+  const int t = threadIdx.x, line = t >> 4, r = t & 15;
+  const int row = blockIdx.x * kLines3 + line, i0 = row / kHalf3, i1 = row - i0 * kHalf3;
+  const float2* src = f + (int64_t)row * kHalf3 + r;
+  const float b01 = beta0[i0] * beta1[i1];
+  float2 x[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 8; ++n1) x[n1] = cscale(src[16 * n1], b01 * beta2[16 * n1 + r]);
+  x[8] = x[9] = make_float2(0.f, 0.f);
+  line_dft160<false, false>(x, T, tw, line, r);
+  if (r < 10) {
+    float2* dst = grid + ((int64_t)i0 * kLen3 + i1) * kLen3;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      const int l = r + 10 * k2;
+      dst[l] = cmul(x[perm16(k2)], __ldg(tw + kTw3Phase + l));
+    }
+  }
+}
+
+// Passes B, C (forward: N inputs, N~ outputs with the output phase) and C',
+// B' (adjoint: N~ inputs with the input phase, the N outputs kept) over
+// kLines3 adjacent columns, in place.
+template <bool INV>
+__global__ void __launch_bounds__(kThreads3)
+    cols160_kernel(float2* __restrict__ grid, int64_t outer_stride, int64_t S, const float2* __restrict__ tw) {
+  __shared__ float2 T[kT3];
+  constexpr int NIN1 = INV ? 10 : 8;
+  const int t = threadIdx.x, line = t % kLines3, r = t / kLines3;
+  constexpr int blocks_per_outer = kLen3 / kLines3;
+  const int outer = blockIdx.x / blocks_per_outer;
+  const int jb = (blockIdx.x - outer * blocks_per_outer) * kLines3;
+  float2* col = grid + outer * outer_stride + jb + line;
+  float2 x[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 10; ++n1) {
+    if (n1 < NIN1) {
+      const float2 v = col[(16 * n1 + r) * S];
+      x[n1] = INV ? cmul(v, cconj(__ldg(tw + kTw3Phase + 16 * n1 + r))) : v;
+    } else {
+      x[n1] = make_float2(0.f, 0.f);
+    }
+  }
+  line_dft160<INV, true>(x, T, tw, line, r);
+  if (r < 10) {
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      const int l = r + 10 * k2;
+      if (!INV)
+        col[l * S] = cmul(x[perm16(k2)], __ldg(tw + kTw3Phase + l));
+      else if (l < kHalf3)
+        col[l * S] = x[perm16(k2)];
+    }
+  }
+}
+
+// Pass A' (adjoint): rows (i0, i1) of the grid with the input phase, inverse
+// DFT along dim 2, the N outputs times the correction into y.
+__global__ void __launch_bounds__(kThreads3)
+    adj_rows160_kernel(const float2* __restrict__ grid, const float* __restrict__ beta0,
+                       const float* __restrict__ beta1, const float* __restrict__ beta2,
+                       const float2* __restrict__ tw, float2* __restrict__ y) {
+  __shared__ float2 T[kT3];
+  const int t = threadIdx.x, line = t >> 4, r = t & 15;
+  const int row = blockIdx.x * kLines3 + line, i0 = row / kHalf3, i1 = row - i0 * kHalf3;
+  const float2* src = grid + ((int64_t)i0 * kLen3 + i1) * kLen3 + r;
+  float2 x[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 10; ++n1) x[n1] = cmul(src[16 * n1], cconj(__ldg(tw + kTw3Phase + 16 * n1 + r)));
+  line_dft160<true, false>(x, T, tw, line, r);
+  if (r < 10) {
+    const float b01 = beta0[i0] * beta1[i1];
+    float2* dst = y + (int64_t)row * kHalf3;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      const int i = r + 10 * k2;
+      if (i < kHalf3) dst[i] = cscale(x[perm16(k2)], b01 * beta2[i]);
+    }
+  }
+}
+
+// tw[16 k1 + r]        = exp(-2 pi i r k1/160)   (forward, k1 < 10)
+// tw[160 + 16 k1 + r]  = exp(+2 pi i r k1/160)   (inverse)
+// tw[320 + l]          = exp(+2 pi i (N/2) l/160), N/2 = 64 (the fftshift phase)
+// in FP64, then rounded.
+__global__ void build_twiddles160_kernel(float2* tw) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < 3 * kLen3) {
+    const double turn = 2.0 * M_PI / (double)kLen3;
+    double a;
+    if (j < 2 * kLen3) {
+      const int e = j % kLen3, k1 = e >> 4, r = e & 15;
+      a = (j < kLen3 ? -turn : turn) * (double)(r * k1);
+    } else {
+      a = turn * (double)(kHalf3 / 2) * (double)(j - 2 * kLen3);
+    }
+    tw[j] = make_float2((float)cos(a), (float)sin(a));
+  }
+}
+
 }  // namespace
 
 bool pruned_fft_supported(int D, const int* N, const int* Nt) {
   if (D == 2) return N[0] == kHalf2 && N[1] == kHalf2 && Nt[0] == kLen2 && Nt[1] == kLen2;
   if (D != 3) return false;
-  for (int d = 0; d < 3; ++d)
-    if (N[d] != kHalf || Nt[d] != kLen) return false;
+  const bool is256 = N[0] == kHalf && Nt[0] == kLen, is160 = N[0] == kHalf3 && Nt[0] == kLen3;
+  if (!is256 && !is160) return false;
+  for (int d = 1; d < 3; ++d)
+    if (N[d] != N[0] || Nt[d] != Nt[0]) return false;
   return true;
 }
 
-cudaError_t build_fft_twiddles(int D, float2* tw, cudaStream_t s) {
-  static_assert(kPrunedFftTwiddles >= 2 * kLen && kPrunedFftTwiddles >= 2 * kLen2, "twiddle table size");
+cudaError_t build_fft_twiddles(int D, int len, float2* tw, cudaStream_t s) {
+  static_assert(kPrunedFftTwiddles >= 2 * kLen && kPrunedFftTwiddles >= 2 * kLen2 &&
+                    kPrunedFftTwiddles >= 3 * kLen3, "twiddle table size");
   if (D == 2)
     build_twiddles2d_kernel<<<4, kLen2 / 2, 0, s>>>(tw);
+  else if (len == kLen3)
+    build_twiddles160_kernel<<<3, kLen3, 0, s>>>(tw);
   else
     build_twiddles_kernel<<<2, kLen, 0, s>>>(tw);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pruned_forward(int D, const void* f, const float* const* beta, const float2* tw, void* grid,
-                                  cudaStream_t s) {
+cudaError_t launch_pruned_forward(int D, int len, const void* f, const float* const* beta, const float2* tw,
+                                  void* grid, cudaStream_t s) {
   float2* g = (float2*)grid;
   if (D == 2) {
     fwd_rows2d_kernel<<<kHalf2 / kLines2, kThreads2, 0, s>>>((const float2*)f, beta[0], beta[1], tw, g);
     cols2d_kernel<false><<<kLen2 / kLines2, kThreads2, 0, s>>>(g, tw);
+    return cudaGetLastError();
+  }
+  if (len == kLen3) {
+    fwd_rows160_kernel<<<kHalf3 * kHalf3 / kLines3, kThreads3, 0, s>>>((const float2*)f, beta[0], beta[1], beta[2],
+                                                                       tw, g);
+    // B: lines (i0 < N, l2), element stride N~ (dim 1)
+    cols160_kernel<false><<<kHalf3 * (kLen3 / kLines3), kThreads3, 0, s>>>(g, (int64_t)kLen3 * kLen3, kLen3, tw);
+    // C: lines (l1, l2), element stride N~^2 (dim 0)
+    cols160_kernel<false><<<kLen3 * (kLen3 / kLines3), kThreads3, 0, s>>>(g, kLen3, (int64_t)kLen3 * kLen3, tw);
     return cudaGetLastError();
   }
   fwd_rows_kernel<<<kHalf * kHalf / kLines, kThreads, 0, s>>>((const float2*)f, beta[0], beta[1], beta[2], tw, g);
@@ -426,12 +631,20 @@ cudaError_t launch_pruned_forward(int D, const void* f, const float* const* beta
   return cudaGetLastError();
 }
 
-cudaError_t launch_pruned_adjoint(int D, void* grid, const float* const* beta, const float2* tw, void* y,
+cudaError_t launch_pruned_adjoint(int D, int len, void* grid, const float* const* beta, const float2* tw, void* y,
                                   cudaStream_t s) {
   float2* g = (float2*)grid;
   if (D == 2) {
     cols2d_kernel<true><<<kLen2 / kLines2, kThreads2, 0, s>>>(g, tw);
     adj_rows2d_kernel<<<kHalf2 / kLines2, kThreads2, 0, s>>>(g, beta[0], beta[1], tw, (float2*)y);
+    return cudaGetLastError();
+  }
+  if (len == kLen3) {
+    // C': lines (l1, l2) along dim 0, keep i0 < N
+    cols160_kernel<true><<<kLen3 * (kLen3 / kLines3), kThreads3, 0, s>>>(g, kLen3, (int64_t)kLen3 * kLen3, tw);
+    // B': lines (i0 < N, l2) along dim 1, keep i1 < N
+    cols160_kernel<true><<<kHalf3 * (kLen3 / kLines3), kThreads3, 0, s>>>(g, (int64_t)kLen3 * kLen3, kLen3, tw);
+    adj_rows160_kernel<<<kHalf3 * kHalf3 / kLines3, kThreads3, 0, s>>>(g, beta[0], beta[1], beta[2], tw, (float2*)y);
     return cudaGetLastError();
   }
   // C': lines (l1, l2) along dim 0, keep i0 < N

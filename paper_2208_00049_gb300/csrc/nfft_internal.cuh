@@ -199,15 +199,16 @@ cudaError_t launch_scatter3d_fast(const Geometry& g, void* grid, const NodeArray
                                   const float* poly, const void* fhat, int compensated, int ctas, cudaStream_t s);
 
 // Pruned FFT with the resampling correction fused in, complex64
-// (fft_pruned.cu): 3D with N~_d = 2 N_d = 256 and 2D with N~_d = 2 N_d = 512.
-// `tw` holds the inter-stage twiddles of that form (build_fft_twiddles,
-// at most kPrunedFftTwiddles); beta[d] are the FP32 correction vectors.
+// (fft_pruned.cu): 3D with N~_d = 2 N_d = 256 or N~_d = 160, N_d = 128, and
+// 2D with N~_d = 2 N_d = 512 (len = N~_0).  `tw` holds the inter-stage
+// twiddles (and phases) of that form (build_fft_twiddles, at most
+// kPrunedFftTwiddles); beta[d] are the FP32 correction vectors.
 constexpr int kPrunedFftTwiddles = 1024;
 bool pruned_fft_supported(int D, const int* N, const int* Nt);
-cudaError_t build_fft_twiddles(int D, float2* tw, cudaStream_t s);
-cudaError_t launch_pruned_forward(int D, const void* f, const float* const* beta, const float2* tw, void* grid,
-                                  cudaStream_t s);
-cudaError_t launch_pruned_adjoint(int D, void* grid, const float* const* beta, const float2* tw, void* y,
+cudaError_t build_fft_twiddles(int D, int len, float2* tw, cudaStream_t s);
+cudaError_t launch_pruned_forward(int D, int len, const void* f, const float* const* beta, const float2* tw,
+                                  void* grid, cudaStream_t s);
+cudaError_t launch_pruned_adjoint(int D, int len, void* grid, const float* const* beta, const float2* tw, void* y,
                                   cudaStream_t s);
 
 // Small 1D complex128 plans (dft1d.cu): correction + pad + FFT and inverse

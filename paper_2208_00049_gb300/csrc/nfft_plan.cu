@@ -506,7 +506,8 @@ int run_pad_fft(nfft_plan* p, const void* f) {
                                                p->sms, p->stream));
   if (p->pruned) {
     const float* beta[kMaxD];
-    return cuda_status(p, launch_pruned_forward(p->D, f, beta32_dims(p, beta), p->fft_tw, p->grid, p->stream));
+    return cuda_status(p, launch_pruned_forward(p->D, (int)p->Nt[0], f, beta32_dims(p, beta), p->fft_tw, p->grid,
+                                                p->stream));
   }
   int s = run_deconv_pad(p, f);
   if (s != NFFT_OK) return s;
@@ -522,7 +523,8 @@ int run_fft_crop(nfft_plan* p, void* y) {
                                                p->sms, p->stream));
   if (p->pruned) {
     const float* beta[kMaxD];
-    return cuda_status(p, launch_pruned_adjoint(p->D, p->grid, beta32_dims(p, beta), p->fft_tw, y, p->stream));
+    return cuda_status(p, launch_pruned_adjoint(p->D, (int)p->Nt[0], p->grid, beta32_dims(p, beta), p->fft_tw, y,
+                                                p->stream));
   }
   int s = run_fft(p, +1);
   if (s != NFFT_OK) return s;
@@ -806,7 +808,7 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
     }
     if (pruned_fft_supported(D, Ni, Nti)) {
       s = dalloc(p, &p->fft_tw, sizeof(float2) * kPrunedFftTwiddles);
-      if (s == NFFT_OK) s = cuda_status(p, build_fft_twiddles(D, p->fft_tw, p->stream));
+      if (s == NFFT_OK) s = cuda_status(p, build_fft_twiddles(D, Nti[0], p->fft_tw, p->stream));
       p->pruned = s == NFFT_OK;
     }
   }
