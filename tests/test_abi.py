@@ -76,6 +76,9 @@ def test_status_strings_and_argument_validation(built_lib):
     # null plan handles are rejected, destroy(NULL) is a no-op
     assert B.nfft_forward(None, None, None) == B.NFFT_ERR_INVALID_ARG
     assert B.nfft_set_nodes(None, None, 1) == B.NFFT_ERR_INVALID_ARG
+    assert B.nfft_plan_set_graph(None, 1) == B.NFFT_ERR_INVALID_ARG
+    assert B.nfft_plan_set_async(None, 1) == B.NFFT_ERR_INVALID_ARG
+    assert B.nfft_plan_sync(None) == B.NFFT_ERR_INVALID_ARG
     assert B.nfft_plan_destroy(None) == B.NFFT_OK
     assert B.nfft_plan_grid(None) is None
 
