@@ -242,7 +242,11 @@ __global__ void __launch_bounds__(k2Threads, 5)
 }
 
 struct GTile2d {
-  float2 t[k2Lines][k2Cols];  // the region, row pitch 32 complex
+  // the region, row pitch 33 complex: with a pitch of 32 every row starts on
+  // the same bank, so a lane's tap (a0 + i0, a1 + i1) fell on bank pair
+  // (a1 + i1) mod 16 whatever its row, and lanes whose nodes share a1 mod 16
+  // conflicted; one extra complex per row shifts row r by r bank pairs
+  float2 t[k2Lines][k2Cols + 1];
   Poly2d pc;
 };
 
