@@ -596,17 +596,23 @@ __global__ void __launch_bounds__(32 * W)
 
 // ---------------------------------------------------------------------------
 // Gather for m = 6 (K = 12 taps per dimension), complex64: the tile + halo
-// (L_d = T_d + 11 <= 16 per dimension, row pitch L2) in shared memory, one
-// node per half-warp.  Lane i2 (< 12; lanes 12..15 repeat tap 11 with weight
-// 0) runs over the 12 x 12 (i0, i1) taps of its column: a half-warp load
-// reads 12 consecutive complex of one row, one shared wavefront per half.
-// The 36 window values of every node are evaluated once per work item
-// (POLYNOMIAL form, packed Horner, two taps per lane) into shared memory:
-// w0 and w1 once per tap (paired in registers: stored (w, w) pairs doubled
-// the shared wavefronts of their broadcast loads), w2 zero-padded to 16.
+// (L_d = T_d + 11 <= 16 per dimension) in shared memory, one node per
+// half-warp.  Per (i0) plane the node's 12 x 12 (i1, i2) taps are flattened,
+// f = 12 i1 + i2, and lane l of the half takes f = 16 k + l, k = 0..8: every
+// lane carries a tap (with one lane per i2 and a row of 12 taps, a quarter of
+// the lanes idled), each lane's w1[i1] w2[i2] products are formed once per
+// node, and the row pitch makes the 16 taps of one load conflict-free.  The
+// 36 window values of every node are evaluated once per work item
+// (POLYNOMIAL form, packed Horner, two taps per lane) into shared memory.
 constexpr int kG12Taps = 12;
 constexpr int kG12Warps = 8;
 constexpr int kG12Threads = 32 * kG12Warps;
+// Row pitch of the region copy: 28 complex = 12 bank pairs mod 16, so that
+// tap (i1, i2) of a plane lies on bank pair (base + 12 i1 + i2) mod 16 and
+// the 16 consecutive flattened taps f = 12 i1 + i2 a half-warp reads at once
+// fall on 16 distinct bank pairs.
+constexpr int kG12Pitch = 28;
+constexpr int kG12Steps = kG12Taps * kG12Taps / 16;  // flattened (i1, i2) taps per lane and plane
 
 struct G12Weights {
   float w0s[kItemCap][kG12Taps];
@@ -617,7 +623,7 @@ struct G12Weights {
 
 __device__ __forceinline__ size_t g12_tile_offset() { return sizeof(NodeStage) + sizeof(G12Weights); }
 
-__global__ void __launch_bounds__(kG12Threads, 3)
+__global__ void __launch_bounds__(kG12Threads, 2)
     gather3d_k12_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na,
                         const float* __restrict__ poly, float2* __restrict__ fhat) {
   constexpr int K = kG12Taps, P = K / 2, kPerIter = 32 / P;
@@ -626,9 +632,19 @@ __global__ void __launch_bounds__(kG12Threads, 3)
   G12Weights& wt = *reinterpret_cast<G12Weights*>(smem_raw + sizeof(NodeStage));
   float2* tile = reinterpret_cast<float2*>(smem_raw + g12_tile_offset());
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int half = lane >> 4, i2 = lane & 15, i2c = min(i2, K - 1);
+  const int half = lane >> 4, l16 = lane & 15;
   const int L1 = g.L[1], L2 = g.L[2];
-  const int pitch = L2, plane = L1 * pitch;
+  const int pitch = kG12Pitch, plane = L1 * pitch;
+  // lane l16 takes the flattened taps f = 16 k + l16 of every (i0) plane:
+  // (i1, i2) = (f / 12, f mod 12)
+  int toff[kG12Steps], ti1[kG12Steps], ti2[kG12Steps];
+#pragma unroll
+  for (int k = 0; k < kG12Steps; ++k) {
+    const int f = 16 * k + l16;
+    ti1[k] = f / K;
+    ti2[k] = f - K * ti1[k];
+    toff[k] = ti1[k] * pitch + ti2[k];
+  }
   // weight lanes: (wj, tp) = two taps of every dimension of node kPerIter (warp + it W) + wj
   const int wj = lane / P, tp = lane - P * (lane / P);
   for (int e = tid; e < 3 * P * (K + 1); e += kG12Threads) {
@@ -690,17 +706,12 @@ __global__ void __launch_bounds__(kG12Threads, 3)
       const int s = min(s0 + half, count - 1);  // a half without a node repeats the last one
       const int pk = __float_as_int(ns.w[s][3]);
       const int a0 = pk & 0xff, a1 = (pk >> 8) & 0xff, a2 = pk >> 16;
-      const float w2 = wt.w2[s][i2];
-      const f32x2* col = reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1) * pitch + a2 + i2c);
-      f32x2 w1[K];
-      const float4* w1q = reinterpret_cast<const float4*>(&wt.w1s[s][0]);
+      const f32x2* col = reinterpret_cast<const f32x2*>(tile + (a0 * L1 + a1) * pitch + a2);
+      f32x2 w12[kG12Steps];  // w1[i1] w2[i2] of this lane's flattened taps
 #pragma unroll
-      for (int q = 0; q < K / 4; ++q) {
-        const float4 x = w1q[q];
-        w1[4 * q] = pack2(x.x, x.x);
-        w1[4 * q + 1] = pack2(x.y, x.y);
-        w1[4 * q + 2] = pack2(x.z, x.z);
-        w1[4 * q + 3] = pack2(x.w, x.w);
+      for (int k = 0; k < kG12Steps; ++k) {
+        const float w = wt.w1s[s][ti1[k]] * wt.w2[s][ti2[k]];
+        w12[k] = pack2(w, w);
       }
       const float4* w0q = reinterpret_cast<const float4*>(&wt.w0s[s][0]);
       f32x2 acc = pack2(0.f, 0.f);
@@ -711,27 +722,25 @@ __global__ void __launch_bounds__(kG12Threads, 3)
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           const f32x2* pl = col + (4 * q + h) * plane;
-          f32x2 sum = mul2(pl[0], w1[0]);
+          f32x2 sum = mul2(pl[toff[0]], w12[0]);
 #pragma unroll
-          for (int i1 = 1; i1 < K; ++i1) sum = fma2(pl[i1 * pitch], w1[i1], sum);
+          for (int k = 1; k < kG12Steps; ++k) sum = fma2(pl[toff[k]], w12[k], sum);
           acc = fma2(sum, pack2(xs[h], xs[h]), acc);
         }
       }
       float2 r = unpack2(acc);
-      r.x *= w2;
-      r.y *= w2;
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
         r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
         r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
       }
-      if (i2 == 0 && s0 + half < count) fhat[__float_as_int(ns.w[s][4])] = r;
+      if (l16 == 0 && s0 + half < count) fhat[__float_as_int(ns.w[s][4])] = r;
     }
   }
 }
 
 size_t g12_smem_bytes(const Geometry& g) {
-  return sizeof(NodeStage) + sizeof(G12Weights) + (size_t)g.L[0] * g.L[1] * g.L[2] * sizeof(float2);
+  return sizeof(NodeStage) + sizeof(G12Weights) + (size_t)g.L[0] * g.L[1] * kG12Pitch * sizeof(float2);
 }
 
 bool g12_supported(const Geometry& g, int cmax) {
