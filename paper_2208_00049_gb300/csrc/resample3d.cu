@@ -1056,6 +1056,273 @@ __global__ void __launch_bounds__(kRegAccThreads, COMP ? 2 : 4)
   if (tma_cta && tid == 0) bulk_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident gather, K = 2m taps per dimension: the ownership of the
+// register-accumulating scatter turned around.  Thread (r1, cc) of a
+// 128-thread CTA loads the two region lines (., r1, cc) and (., r1, cc + 8)
+// of the tile + halo into registers (reg[h][r0], r0 < L0 <= 16) once per
+// work item, and for a node at offset (a0, a1, a2) forms
+//   p = w1[r1 - a1] (w2[cc - a2]     sum_i0 w0[i0] reg[0][a0 + i0]
+//                  + w2[cc + 8 - a2] sum_i0 w0[i0] reg[1][a0 + i0]),
+// 2K + 2 packed operations with static register indices (nodes
+// counting-sorted by (a0, a1), one loop per a0 bin, as in the scatter).  The
+// window values are stored once, as in the scatter: stored as (w, w) pairs
+// they took twice the shared wavefronts, and the gather measured slower
+// (0.95 against 0.90 ms at 160^3, m = 6).  The warp sums p over its lanes
+// four nodes at a time: one exchange hands nodes s, s + 1 to lanes 0..15
+// and s + 2, s + 3 to lanes 16..31, a second splits each half into 8-lane
+// groups of one node, three more levels sum the groups (3 shuffles of a
+// pair per node instead of 10 for a lone node).  Taps are read from
+// registers, so the shared-memory pipe carries only the broadcast window
+// loads and the shuffles, where the shared-tap gathers read every tap of
+// every node from shared memory.  A warp stores its sum for a node in its
+// own slot; after the node loop one thread per node adds the slots of the
+// warps whose rows meet the node's footprint, in warp order, so the result
+// does not depend on scheduling.
+template <int K>
+struct GatherRegStage {
+  static constexpr int kPairs = K / 2;
+  union {  // the records are done with once the window values are stored
+    float4 rec[kItemCap][2];                      // {t0, t1, t2, pk}, {perm, 0, key, rank}
+    f32x2 part[kRegAccWarps][kItemCap];           // per-warp sums, by slot
+  };
+  int count[kRegAccKeys];
+  int start[kRegAccKeys + 1];
+  f32x2 coef[3][kPairs][K + 1];                   // (tap 2 tp, tap 2 tp + 1) coefficient pairs
+  alignas(16) float w0s[kItemCap][K];             // w0, by slot
+  alignas(16) float w1r[kItemCap][kRegAccLines];  // w1[r - a1] by region row (zero outside), by slot
+  alignas(16) float2 w2s[kItemCap][8];            // cc -> (w2[cc - a2], w2[cc + 8 - a2]), by slot
+  int sperm[kItemCap];                            // caller index, by slot
+  int sa1[kItemCap];                              // a1, by slot
+};
+// four CTAs per SM: 4 x (stage + 1 KB reserved) within the SM's 228 KB
+static_assert(sizeof(GatherRegStage<12>) <= 56 * 1024, "four gather CTAs per SM");
+
+template <int A0, int K>
+__device__ __forceinline__ f32x2 gather_reg_node(const GatherRegStage<K>& st, int s, int r1, int cc,
+                                                 const f32x2 (&reg)[2][kRegAccLines]) {
+  const float u = st.w1r[s][r1];
+  const float2 w2 = st.w2s[s][cc];
+  const float4* wq = reinterpret_cast<const float4*>(&st.w0s[s][0]);
+  f32x2 t0 = 0, t1 = 0;
+#pragma unroll
+  for (int q = 0; q < K / 4; ++q) {
+    const float4 x = wq[q];
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const f32x2 wa = pack2(xs[j], xs[j]);
+      if (q == 0 && j == 0) {
+        t0 = mul2(reg[0][A0], wa);
+        t1 = mul2(reg[1][A0], wa);
+      } else {
+        t0 = fma2(reg[0][A0 + 4 * q + j], wa, t0);
+        t1 = fma2(reg[1][A0 + 4 * q + j], wa, t1);
+      }
+    }
+  }
+  const float u0 = u * w2.x, u1 = u * w2.y;
+  return fma2(t1, pack2(u1, u1), mul2(t0, pack2(u0, u0)));
+}
+
+__device__ __forceinline__ f32x2 shfl_xor2(f32x2 v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+
+// Sum of p[j] over the warp's lanes for the n <= 4 nodes s + j; lane 8 j
+// stores the sum of node s + j in the warp's slot.
+__device__ __forceinline__ void warp_sum4_store(f32x2 (&p)[4], f32x2* part, int s, int n, int lane) {
+  const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0;
+  f32x2 k0 = u16 ? p[2] : p[0], k1 = u16 ? p[3] : p[1];
+  k0 = add2(k0, shfl_xor2(u16 ? p[0] : p[2], 16));
+  k1 = add2(k1, shfl_xor2(u16 ? p[1] : p[3], 16));
+  f32x2 k = u8 ? k1 : k0;
+  k = add2(k, shfl_xor2(u8 ? k0 : k1, 8));
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) k = add2(k, shfl_xor2(k, o));
+  const int j = lane >> 3;
+  if ((lane & 7) == 0 && j < n) part[s + j] = k;
+}
+
+template <int A0, int K>
+__device__ __forceinline__ void gather_reg_bin(GatherRegStage<K>& st, int lo, int hi, int r1, int cc, int warp,
+                                               int lane, const f32x2 (&reg)[2][kRegAccLines]) {
+  if constexpr (A0 + K <= kRegAccLines) {  // a0 < T0 <= 17 - K
+    const int s0 = st.start[A0 * kRegAccA + lo], s1 = st.start[A0 * kRegAccA + hi + 1];
+    int s = s0;
+    for (; s + 3 < s1; s += 4) {
+      f32x2 p[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) p[j] = gather_reg_node<A0, K>(st, s + j, r1, cc, reg);
+      warp_sum4_store(p, st.part[warp], s, 4, lane);
+    }
+    if (s < s1) {  // 1 to 3 nodes left (s1 is uniform over the warp)
+      f32x2 p[4] = {0, 0, 0, 0};
+      p[0] = gather_reg_node<A0, K>(st, s, r1, cc, reg);
+      if (s + 1 < s1) p[1] = gather_reg_node<A0, K>(st, s + 1, r1, cc, reg);
+      if (s + 2 < s1) p[2] = gather_reg_node<A0, K>(st, s + 2, r1, cc, reg);
+      warp_sum4_store(p, st.part[warp], s, s1 - s, lane);
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kRegAccThreads, 4)
+    gather3d_reg_kernel(Geometry g, const float2* __restrict__ grid, NodeArrays na,
+                        const float* __restrict__ poly, float2* __restrict__ fhat) {
+  using Stage = GatherRegStage<K>;
+  constexpr int P = Stage::kPairs;
+  constexpr int kPerIter = 32 / P;  // nodes per warp and weight iteration
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Stage& st = *reinterpret_cast<Stage*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r1 = tid >> 3, cc = tid & 7;
+  // a1 run of this warp: one of rows 4w .. 4w + 3 lies in [a1, a1 + K)
+  const int lo = max(0, 4 * warp - (K - 1)), hi = min(kRegAccA - 1, 4 * warp + 3);
+  const int wj = lane / P, tp = lane - P * (lane / P);
+  for (int e = tid; e < 3 * P * (K + 1); e += kRegAccThreads) {
+    const int d = e / (P * (K + 1)), pp = (e / (K + 1)) % P, z = e % (K + 1);
+    st.coef[d][pp][z] = pack2(poly[(d * K + 2 * pp) * (K + 1) + z], poly[(d * K + 2 * pp + 1) * (K + 1) + z]);
+  }
+  const int nitems = *na.n_items;
+  const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+  const int64_t M = g.M;
+  const int64_t plane = (int64_t)g.Nt[1] * g.Nt[2];
+  const float* frac = reinterpret_cast<const float*>(na.frac);
+  const f32x2* gp = reinterpret_cast<const f32x2*>(grid);
+  for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;
+
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 item = na.items[it];
+    int tc[3], start[3];
+    tile_origin(g, item.x, tc);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) start[d] = tc[d] * g.T[d] + g.off;
+    const int count = item.z;
+
+    // the two region lines of this thread, issued first and consumed after
+    // the window values (zero outside the region)
+    f32x2 reg[2][kRegAccLines];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = cc + 8 * h;
+      const bool ok = r1 < L1 && c < L2;
+      const f32x2* src = gp;
+      if (ok) src = gp + (int64_t)wrap1(start[1] + r1, g.Nt[1]) * g.Nt[2] + wrap1(start[2] + c, g.Nt[2]);
+#pragma unroll
+      for (int r = 0; r < kRegAccLines; ++r)
+        reg[h][r] = (ok && r < L0) ? __ldg(src + wrap1(start[0] + r, g.Nt[0]) * plane) : 0ull;
+    }
+
+    __syncthreads();  // previous item's sums written out; counts cleared
+    for (int i = tid; i < count; i += kRegAccThreads) {
+      const int q = item.y + i;
+      int a[3];
+      float t[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        a[d] = na.cell[d * M + q] - tc[d] * g.T[d];
+        t[d] = frac[d * M + q];
+      }
+      const int key = a[0] * kRegAccA + a[1];
+      const int rank = atomicAdd(&st.count[key], 1);
+      st.rec[i][0] = make_float4(t[0], t[1], t[2], __int_as_float(a[0] | (a[1] << 8) | (a[2] << 16)));
+      st.rec[i][1] = make_float4(__int_as_float(na.perm[q]), 0.f, __int_as_float(key), __int_as_float(rank));
+    }
+    {
+      // clear the shifted rows of the slots in use (w1r, w2s: 4 float4 each per slot)
+      float4* z1 = reinterpret_cast<float4*>(&st.w1r[0][0]);
+      float4* z2 = reinterpret_cast<float4*>(&st.w2s[0][0]);
+      for (int e = tid; e < count * 4; e += kRegAccThreads) {
+        z1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        z2[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // exclusive scan of the 81 counts: lane owns keys 3 lane .. 3 lane + 2
+      int cv[3], sum = 0;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int key = 3 * lane + u;
+        cv[u] = key < kRegAccKeys ? st.count[key] : 0;
+        sum += cv[u];
+      }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int run = incl - sum;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int key = 3 * lane + u;
+        if (key <= kRegAccKeys) st.start[key] = run;
+        run += cv[u];
+      }
+    }
+    __syncthreads();
+    if (wj < kPerIter) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {  // one dimension's coefficients in registers at a time
+        f32x2 cpair[K + 1];
+#pragma unroll
+        for (int e = 0; e <= K; ++e) cpair[e] = st.coef[d][tp][e];
+        for (int s = kPerIter * warp + wj; s < count; s += kPerIter * kRegAccWarps) {
+          const float4 r0 = st.rec[s][0];
+          const float4 rv = st.rec[s][1];
+          const int pk = __float_as_int(r0.w);
+          const int q = st.start[__float_as_int(rv.z)] + __float_as_int(rv.w);
+          const float z = (d == 0 ? r0.x : (d == 1 ? r0.y : r0.z)) - 0.5f;
+          const f32x2 zz = pack2(z, z);
+          f32x2 pw = cpair[K];
+#pragma unroll
+          for (int e = K - 1; e >= 0; --e) pw = fma2(pw, zz, cpair[e]);
+          const float2 w = unpack2(pw);  // taps 2 tp, 2 tp + 1
+          if (d == 0) {
+            *reinterpret_cast<float2*>(&st.w0s[q][2 * tp]) = w;
+            if (tp == 0) {
+              st.sperm[q] = __float_as_int(rv.x);
+              st.sa1[q] = (pk >> 8) & 0xff;
+            }
+          } else if (d == 1) {
+            const int r = ((pk >> 8) & 0xff) + 2 * tp;
+            st.w1r[q][r] = w.x;
+            st.w1r[q][r + 1] = w.y;
+          } else {
+            // column c sits in pair cc = c & 7, half c >> 3
+            const int c0 = (pk >> 16) + 2 * tp, c1 = c0 + 1;
+            float* w2f = reinterpret_cast<float*>(&st.w2s[q][0]);
+            w2f[2 * (c0 & 7) + (c0 >> 3)] = w.x;
+            w2f[2 * (c1 & 7) + (c1 >> 3)] = w.y;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < kRegAccKeys; e += kRegAccThreads) st.count[e] = 0;  // for the next item
+
+    gather_reg_bin<0, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    gather_reg_bin<1, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    gather_reg_bin<2, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    gather_reg_bin<3, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    gather_reg_bin<4, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    gather_reg_bin<5, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    gather_reg_bin<6, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    gather_reg_bin<7, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    gather_reg_bin<8, K>(st, lo, hi, r1, cc, warp, lane, reg);
+    __syncthreads();
+    // sum the slots of the warps whose rows meet the node's footprint
+    for (int s = tid; s < count; s += kRegAccThreads) {
+      const int a1 = st.sa1[s];
+      f32x2 acc = 0;
+#pragma unroll
+      for (int w = 0; w < kRegAccWarps; ++w)
+        if (a1 >= max(0, 4 * w - (K - 1)) && a1 <= 4 * w + 3) acc = add2(acc, st.part[w][s]);
+      fhat[st.sperm[s]] = unpack2(acc);
+    }
+  }
+}
+
 bool regacc_supported(const Geometry& g) {
   if (g.D != 3 || g.closed || (g.K != 8 && g.K != 12) || g.m != 0.5 * g.K || g.off != 1 - g.K / 2) return false;
   for (int d = 0; d < 3; ++d)
@@ -1080,6 +1347,19 @@ bool use_regacc(const Geometry& g) {
 bool fast_scatter_supported(const Geometry& g, int cmax) { return cmax <= kItemCap && use_regacc(g); }
 
 namespace {
+
+// Gather form: NFFT_GB300_GATHER=smem keeps the shared-tap kernels, =regs
+// takes the register-resident one for K = 8 as well; by default it serves
+// K = 12 (read at each launch, so that the forms can be compared in one
+// process).
+bool use_gather_reg(const Geometry& g) {
+  if (!regacc_supported(g)) return false;
+  const char* e = getenv("NFFT_GB300_GATHER");
+  if (e && strcmp(e, "smem") == 0) return false;
+  return g.K == kG12Taps || (e && strcmp(e, "regs") == 0);
+}
+void* gather_reg_kernel(int K) { return K == 12 ? (void*)gather3d_reg_kernel<12> : (void*)gather3d_reg_kernel<8>; }
+size_t gather_reg_smem(int K) { return K == 12 ? sizeof(GatherRegStage<12>) : sizeof(GatherRegStage<8>); }
 
 void* regacc_kernel(int K, bool comp) {
   if (comp) return K == 12 ? (void*)scatter3d_regacc_kernel<12, true> : (void*)scatter3d_regacc_kernel<8, true>;
@@ -1265,6 +1545,14 @@ int fast3d_ctas_per_sm(const Geometry& g, int kind) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
     return n;
   }
+  if (kind == 0 && use_gather_reg(g)) {
+    const size_t smem = gather_reg_smem(g.K);
+    void* k = gather_reg_kernel(g.K);
+    if (set_smem(k, smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kRegAccThreads, smem) != cudaSuccess) return 0;
+    return n;
+  }
   if (kind == 0 && g.K == kG12Taps) {
     const size_t smem = g12_smem_bytes(g);
     if (set_smem(gather3d_k12_kernel, smem) != cudaSuccess) return 0;
@@ -1285,6 +1573,15 @@ int fast3d_ctas_per_sm(const Geometry& g, int kind) {
 
 cudaError_t launch_gather3d_fast(const Geometry& g, const void* grid, const NodeArrays& na,
                                  const float* poly, void* fhat, int ctas, cudaStream_t s) {
+  if (use_gather_reg(g)) {
+    const size_t smem = gather_reg_smem(g.K);
+    void* k = gather_reg_kernel(g.K);
+    cudaError_t e = set_smem(k, smem);
+    if (e != cudaSuccess) return e;
+    auto kern = reinterpret_cast<void (*)(Geometry, const float2*, NodeArrays, const float*, float2*)>(k);
+    kern<<<ctas, kRegAccThreads, smem, s>>>(g, (const float2*)grid, na, poly, (float2*)fhat);
+    return cudaGetLastError();
+  }
   if (g.K == kG12Taps) {
     const size_t smem = g12_smem_bytes(g);
     cudaError_t e = set_smem(gather3d_k12_kernel, smem);

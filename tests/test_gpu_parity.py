@@ -501,6 +501,43 @@ def test_fast_m6_tile_shapes(sigma, tile):
     assert_close(y, onfft.adjoint(case["k"], case["w"], N, sigma, 6), tol_a, "adjoint", tmax)
 
 
+@pytest.mark.parametrize("m,tile,hot", [(6, (5, 5, 5), False), (6, (5, 5, 5), True), (6, (2, 5, 3), False),
+                                        (4, (9, 9, 8), False), (4, (9, 9, 8), True), (4, (5, 7, 9), False),
+                                        (4, (8, 8, 1), False)])
+def test_gather_forms_match_oracle(m, tile, hot, monkeypatch):
+    """3D complex64 gather in its two forms: the register-resident kernel
+    (each thread holds two region lines in registers; the default at m = 6,
+    selected by NFFT_GB300_GATHER=regs at m = 4) and the shared-tap kernels
+    (NFFT_GB300_GATHER=smem).  Both against the oracle, on tiles that divide
+    the grid or not, with hot tiles (work items split at the per-item cap)
+    and nodes on the periodic boundary; the two forms differ only in the
+    order of the sums, and each repeats its result bit for bit."""
+    from paper_2208_00049_gb300.nfft import Plan
+    N = (16, 16, 16) if hot else (20, 18, 24)
+    case = inputs.small_case(N, 6000, seed=59 + m, m=m)
+    if hot:
+        case["k"][:4000] = 0.02 * case["k"][:4000]
+        case["k"][4000:4400, 1] = -0.5
+        case["k"][4400:4800, 2] = 0.5 - 1e-9
+    plan = Plan(N, case["M"], sigma=2.0, m=m, dtype=torch.complex64)
+    plan.set_tile(tile)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    assert plan.paths()["fast_gather"]
+    f = to_dev(case["f"], torch.complex64)
+    ref = onfft.forward(case["k"], case["f"], 2.0, m)
+    out = {}
+    for form in ("regs", "smem"):
+        monkeypatch.setenv("NFFT_GB300_GATHER", form)
+        a = plan.forward(f).clone()
+        b = plan.forward(f).clone()
+        plan.sync()
+        assert torch.equal(a, b), form + " gather is not deterministic"
+        out[form] = a.cpu().numpy()
+        assert_close(out[form], ref, 1e-5, form + " forward")
+    plan.close()
+    assert rel_l2(out["regs"], out["smem"]) <= 1e-6
+
+
 def test_fast_m6_hot_tile():
     """m = 6: work items split at the per-item cap, nodes on the boundary."""
     from paper_2208_00049_gb300.nfft import Plan
