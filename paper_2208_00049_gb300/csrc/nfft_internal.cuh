@@ -238,6 +238,15 @@ cudaError_t launch_scatter2d_fast(const Geometry& g, void* grid, const NodeArray
 cudaError_t launch_scatter2d_fast_batch(const BatchProblem* probs, void* grid, const BatchNodes& nb,
                                         const float* poly, const void* fhat, int ctas, cudaStream_t s);
 
+// 2D complex128 scatter without shared-memory atomics (resample2d_f64.cu):
+// even K = 2m <= 16 taps, half-open support, any window form; one work item
+// per CTA (scatter2d_f64_items_per_cta()).
+bool scatter2d_f64_supported(const Geometry& g);
+int scatter2d_f64_ctas_per_sm(const Geometry& g);
+int scatter2d_f64_items_per_cta();
+cudaError_t launch_scatter2d_f64(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat, int ctas,
+                                 cudaStream_t s);
+
 // FULL precomputation: B as a CSR matrix, applied with cuSPARSE (nfft_full.cu)
 struct FullMatrix;
 int full_build(FullMatrix** out, const Geometry& g, int dtype, const NodeArrays& na, cudaStream_t s);

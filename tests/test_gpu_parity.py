@@ -538,6 +538,53 @@ def test_gather_forms_match_oracle(m, tile, hot, monkeypatch):
     assert rel_l2(out["regs"], out["smem"]) <= 1e-6
 
 
+@pytest.mark.parametrize("N,M,sigma,m,tile,hot,flags", [
+    ((64, 64), 4096, 2.0, 8, None, False, 0),
+    ((64, 64), 4096, 2.0, 8, (7, 40), True, 0),
+    ((48, 40), 2500, 2.0, 4, (16, 16), False, 0),
+    ((33, 47), 1777, 1.5, 5, None, False, 0),
+    ((40, 36), 3000, 2.0, 6, (3, 33), True, 0),
+    ((40, 36), 3000, 2.0, 6, None, False, "linear"),
+    ((20, 24), 800, 2.0, 1, None, False, 0),
+])
+def test_f64_2d_scatter_matches_oracle(N, M, sigma, m, tile, hot, flags, monkeypatch):
+    """2D complex128 adjoint through the scatter without shared-memory atomics
+    (lanes own columns mod 16 and row parities; the default for even
+    K = 2m <= 16) and through the generic shared-atomic scatter
+    (NFFT_GB300_F64_SCATTER=generic): both against the oracle within the
+    complex128 tolerance, on tiles wider and narrower than 16 columns, with
+    hot tiles and boundary nodes, in the POLYNOMIAL (m >= 7), direct and
+    LINEAR window forms."""
+    from paper_2208_00049_gb300 import binding as B
+    from paper_2208_00049_gb300.nfft import Plan
+    case = inputs.small_case(N, M, seed=71 + m, sigma=sigma, m=m)
+    if hot:
+        case["k"][: M // 2] = 0.02 * case["k"][: M // 2]
+        case["k"][M // 2: M // 2 + 200, 0] = -0.5
+        case["k"][M // 2 + 200: M // 2 + 400, 1] = 0.5 - 1e-12
+    fl = B.NFFT_FLAG_WINDOW_LINEAR if flags == "linear" else 0
+    plan = Plan(N, M, sigma=sigma, m=m, dtype=torch.complex128, flags=fl)
+    if tile is not None:
+        plan.set_tile(tile)
+    plan.set_nodes(to_dev(case["k"], torch.float64))
+    w = to_dev(case["w"], torch.complex128)
+    out = {}
+    for form in ("lanes", "generic"):
+        if form == "generic":
+            monkeypatch.setenv("NFFT_GB300_F64_SCATTER", "generic")
+        out[form] = plan.adjoint(w).cpu().numpy()
+        plan.sync()
+    plan.close()
+    if flags == "linear":  # the oracle reads the same table with linear interpolation
+        want = onfft.adjoint(case["k"], case["w"], N, sigma, m, window="linear")
+    else:
+        want = onfft.adjoint(case["k"], case["w"], N, sigma, m)
+    tol = tol_for(N, sigma, m, "c128")
+    for form in out:
+        assert_close(out[form], want, tol, form + " adjoint", tol_max_for(N, sigma, m, "c128"))
+    assert rel_l2(out["lanes"], out["generic"]) <= 1e-13
+
+
 def test_fast_m6_hot_tile():
     """m = 6: work items split at the per-item cap, nodes on the boundary."""
     from paper_2208_00049_gb300.nfft import Plan
