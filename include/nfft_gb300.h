@@ -198,8 +198,9 @@ void *nfft_plan_grid(nfft_plan *p);
  * 9 cells per dimension (3D m = 4; the gather also accepts larger tiles in
  * dimensions 0 and 1), 5 (3D m = 6) or 9 x 25 (2D m = 4); other tiles run the
  * generic kernels.  Defaults: 9 x 9 x 8 (3D m = 4), 5 x 5 x 5 (3D m = 6),
- * 9 x 25 or 8 x 8 (2D m = 4, by grid size), else a power-of-two cube sized
- * for the node density. */
+ * 9 x 25 or 8 x 8 (2D m = 4, by grid size), 20 x 20 (2D complex128, m = 8)
+ * or 16 x 16 (2D complex128, m <= 6), else a power-of-two cube sized for the
+ * node density. */
 int nfft_plan_set_tile(nfft_plan *p, const int64_t *tile3);
 
 /* Algorithm 1, correction and zero-pad step: resampling correction and zero
