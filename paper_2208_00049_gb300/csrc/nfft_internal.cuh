@@ -246,6 +246,11 @@ int scatter2d_f64_ctas_per_sm(const Geometry& g);
 int scatter2d_f64_items_per_cta();
 cudaError_t launch_scatter2d_f64(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat, int ctas,
                                  cudaStream_t s);
+// 3D counterpart (resample3d_f64.cu): even K = 2m <= 8, one work item per CTA.
+bool scatter3d_f64_supported(const Geometry& g);
+int scatter3d_f64_ctas_per_sm(const Geometry& g);
+cudaError_t launch_scatter3d_f64(const Geometry& g, void* grid, const NodeArrays& na, const void* fhat, int ctas,
+                                 cudaStream_t s);
 
 // FULL precomputation: B as a CSR matrix, applied with cuSPARSE (nfft_full.cu)
 struct FullMatrix;

@@ -46,7 +46,7 @@ struct nfft_plan {
   FullMatrix* full = nullptr;  // NFFT_FLAG_FULL_MATRIX: B and B^T as CSR
   int fast_ctas[2] = {0, 0};
   int grad_ctas = 0;           // 3D m = 4 complex64 node-gradient kernel (0: generic)
-  int f64_scatter_ctas = 0;    // 2D complex128 scatter without shared atomics (0: generic)
+  int f64_scatter_ctas = 0;    // 2D / 3D complex128 scatter without shared atomics (0: generic)
   bool pruned = false;         // nfft_step_pad_fft / fft_crop use the pruned 3D FFT
   float2* fft_tw = nullptr;    // its 256 twiddles
   bool dft1d = false;          // ... or the direct sums of small 1D complex128 plans
@@ -413,6 +413,11 @@ int configure_tiles(nfft_plan* p, const int64_t* T) {
     if (ctas > need) ctas = (int)need;
     p->f64_scatter_ctas = ctas;
   }
+  if (p->dtype == NFFT_C128 && p->D == 3 && scatter3d_f64_supported(g)) {
+    int ctas = scatter3d_f64_ctas_per_sm(g) * p->sms;
+    if (ctas > p->max_items) ctas = (int)p->max_items;
+    p->f64_scatter_ctas = ctas;
+  }
   // generic kernels: gather and scatter are required; the compensated scatter
   // where the plan asks for it and no fast scatter serves it; the node
   // gradient is optional (m = 9, 10 have none: nfft_grad reports UNSUPPORTED)
@@ -501,8 +506,10 @@ int run_scatter(nfft_plan* p, const void* fhat) {
           ? (p->D == 2 ? launch_scatter2d_fast(g, p->grid, na, p->poly, fhat, comp, p->fast_ctas[1], p->stream)
                        : launch_scatter3d_fast(g, p->grid, na, p->poly, fhat, comp, p->fast_ctas[1], p->stream))
       : p->dtype == NFFT_C128
-          ? (p->f64_scatter_ctas > 0 && scatter2d_f64_supported(g)
+          ? (p->f64_scatter_ctas > 0 && p->D == 2 && scatter2d_f64_supported(g)
                  ? launch_scatter2d_f64(g, p->grid, na, fhat, p->f64_scatter_ctas, p->stream)
+             : p->f64_scatter_ctas > 0 && p->D == 3 && scatter3d_f64_supported(g)
+                 ? launch_scatter3d_f64(g, p->grid, na, fhat, p->f64_scatter_ctas, p->stream)
                  : launch_scatter<double>(g, p->grid, na, fhat, 0, p->ctas[1], p->stream))
           : launch_scatter<float>(g, p->grid, na, fhat, comp, p->ctas[comp ? 2 : 1], p->stream);
   return cuda_status(p, e);

@@ -546,22 +546,29 @@ def test_gather_forms_match_oracle(m, tile, hot, monkeypatch):
     ((40, 36), 3000, 2.0, 6, (3, 33), True, 0),
     ((40, 36), 3000, 2.0, 6, None, False, "linear"),
     ((20, 24), 800, 2.0, 1, None, False, 0),
+    ((20, 18, 16), 5000, 2.0, 4, None, False, 0),
+    ((20, 18, 16), 5000, 2.0, 4, (5, 7, 9), True, 0),
+    ((17, 23, 12), 3001, 2.0, 3, (3, 11, 2), False, 0),
+    ((16, 16, 16), 4096, 1.5, 2, None, True, 0),
+    ((12, 10, 14), 1500, 2.0, 4, None, False, "linear"),
+    ((10, 8, 12), 600, 2.0, 1, None, False, 0),
 ])
-def test_f64_2d_scatter_matches_oracle(N, M, sigma, m, tile, hot, flags, monkeypatch):
-    """2D complex128 adjoint through the scatter without shared-memory atomics
-    (lanes own columns mod 16 and row parities; the default for even
-    K = 2m <= 16) and through the generic shared-atomic scatter
+def test_f64_scatter_matches_oracle(N, M, sigma, m, tile, hot, flags, monkeypatch):
+    """2D and 3D complex128 adjoint through the scatter without shared-memory
+    atomics (threads own region points by residue class: in 2D columns mod 16
+    and rows mod 8, in 3D (mod 4, mod 4, mod 8); the default for even K = 2m
+    up to 16 in 2D and 8 in 3D) and through the generic shared-atomic scatter
     (NFFT_GB300_F64_SCATTER=generic): both against the oracle within the
-    complex128 tolerance, on tiles wider and narrower than 16 columns, with
-    hot tiles and boundary nodes, in the POLYNOMIAL (m >= 7), direct and
-    LINEAR window forms."""
+    complex128 tolerance, on tiles wider and narrower than the residue
+    classes, with hot tiles and boundary nodes, in the POLYNOMIAL (m >= 7),
+    direct and LINEAR window forms."""
     from paper_2208_00049_gb300 import binding as B
     from paper_2208_00049_gb300.nfft import Plan
     case = inputs.small_case(N, M, seed=71 + m, sigma=sigma, m=m)
     if hot:
         case["k"][: M // 2] = 0.02 * case["k"][: M // 2]
         case["k"][M // 2: M // 2 + 200, 0] = -0.5
-        case["k"][M // 2 + 200: M // 2 + 400, 1] = 0.5 - 1e-12
+        case["k"][M // 2 + 200: M // 2 + 400, len(N) - 1] = 0.5 - 1e-12
     fl = B.NFFT_FLAG_WINDOW_LINEAR if flags == "linear" else 0
     plan = Plan(N, M, sigma=sigma, m=m, dtype=torch.complex128, flags=fl)
     if tile is not None:
