@@ -578,8 +578,9 @@ def time_steps(step_fn, steps, warmup, stream, flush):
 
 
 def fp64_form(wl, fhat32, steps, warmup, flush):
-    """The plain FP64 form (complex128 plan, same kernels' FP64 instantiation)
-    on the same workload: throughput and the FP32 result's distance to it."""
+    """The FP64 form (complex128 plan: the generic gather in FP64 and the
+    FP64 scatter that owns region points by residue class) on the same
+    workload: throughput and the FP32 result's distance to it."""
     import numpy as np
     import torch
     from paper_2208_00049_gb300.nfft import Plan
