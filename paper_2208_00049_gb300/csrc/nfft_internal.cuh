@@ -46,11 +46,12 @@ struct Geometry {
   double norm[kMaxD];  // m / sinh(b m): scales the window to 1 at u = 0
   // window values of the generic kernels: kWinDirect (wtab unused),
   // kWinLinear (wtab = D tables of wS entries of the scaled window in the
-  // plan's real type, table d at d * wS), kWinPoly (wtab = [D][K][2m + 1]
-  // coefficients in the plan's real type)
+  // plan's real type, table d at d * wS), kWinPoly (wtab = [D][K][wZ]
+  // coefficients in the plan's real type, increasing powers of zeta)
   int wmode;
   int wS;
   const void* wtab;
+  int wZ;            // kWinPoly: coefficients per tap (degree + 1; 2m + 1, or more for complex128)
 };
 
 // Kaiser-Bessel window in grid units, scaled to 1 at u = 0:
@@ -279,7 +280,8 @@ struct PolyArgs {
   int m;
   double b[kMaxD];
 };
-// coef64 (may be null) receives the FP64 coefficients as well.
+// coef and coef64 (either may be null) receive the FP32 and FP64
+// coefficients [D][K][deg + 1].
 cudaError_t launch_build_poly(const PolyArgs& a, float* coef, cudaStream_t s, double* coef64 = nullptr);
 
 // LINEAR window tables (Sec. 3.7.4): for each dimension d, entries

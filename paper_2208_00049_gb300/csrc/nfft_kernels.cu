@@ -140,7 +140,7 @@ __global__ void build_poly_kernel(PolyArgs a, float* coef, double* coef64) {
     V[r][Z] = acc / V[r][r];
   }
   for (int z = 0; z < Z; ++z) {
-    coef[(d * a.K + i) * Z + z] = (float)V[z][Z];
+    if (coef) coef[(d * a.K + i) * Z + z] = (float)V[z][Z];
     if (coef64) coef64[(d * a.K + i) * Z + z] = V[z][Z];
   }
 }

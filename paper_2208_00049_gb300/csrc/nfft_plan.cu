@@ -56,7 +56,8 @@ struct nfft_plan {
   double* beta64 = nullptr;
   float* beta32 = nullptr;
   float* poly = nullptr;  // POLYNOMIAL window coefficients [D][K][2m + 1] (FP32)
-  double* poly64 = nullptr;  // the same in FP64 (complex128 plans with NFFT_FLAG_WINDOW_POLYNOMIAL)
+  double* poly64 = nullptr;  // FP64 coefficients [D][K][poly_Z] (complex128 plans in the POLYNOMIAL form)
+  int poly_Z = 0;            // coefficients per tap of the table the generic kernels read
   int wmode = kWinDirect;    // window values of the generic kernels
   void* lut = nullptr;       // LINEAR tables, D x lut_S entries of the plan's real type
   int64_t lut_S = 0;
@@ -235,6 +236,7 @@ Geometry make_geometry(const nfft_plan* p) {
   g.wtab = p->wmode == kWinLinear ? (const void*)p->lut
            : p->wmode == kWinPoly ? (p->dtype == NFFT_C128 ? (const void*)p->poly64 : (const void*)p->poly)
                                   : nullptr;
+  g.wZ = p->poly_Z;
   for (int d = 0; d < p->D; ++d) {
     g.Nt[d] = (int)p->Nt[d];
     g.T[d] = (int)p->T[d];
@@ -803,18 +805,24 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
       s = cuda_status(p, launch_build_lut(D, m, p->b, p->lut_S, dtype == NFFT_C128 ? nullptr : (float*)p->lut,
                                           dtype == NFFT_C128 ? (double*)p->lut : nullptr, p->stream));
   }
-  // complex128 plans with m >= 7 and no window flag take the POLYNOMIAL
-  // window as well: there its FP64 fit error is about 1e-14 of the window
-  // peak, the rounding level of the direct form, and 2m + 1 Horner steps per
-  // tap cost GB300's narrow FP64 units less than the direct form's sqrt,
-  // exponential and division.  Below m = 7 the fit error would show against
-  // the exact window (6e-9 at m = 4; at m = 6 and sigma = 1.25 it put a 3D
-  // adjoint at 4.4e-11 against a rounding bound of 4.2e-11), so those keep
-  // direct evaluation.
-  const bool poly_default = dtype == NFFT_C128 && !(flags & kWindowFlags) && !closed && !wide && m >= 7;
+  // complex128 plans with no window flag take the POLYNOMIAL window as well
+  // where its FP64 fit stays at the rounding level of the direct form: the
+  // direct form's sqrt, exponential and division cost GB300's narrow FP64
+  // units several times a Horner chain.  With m >= 7 the degree-2m fit is
+  // within about 1e-14 of the window peak; with oversampling of at least 1.5
+  // the table is fitted at degree max(2m, 16) instead (fit error <= 1e-14 of
+  // the peak for m = 1..8).  At sigma = 1.25 and m < 7 the correction
+  // amplifies even a 1e-14 fit error past the rounding bound (a 3D adjoint at
+  // m = 6 came to 4.4e-11 against 4.2e-11), so those keep direct evaluation.
+  double min_sigma = 1e300;
+  for (int d = 0; d < D; ++d) min_sigma = fmin(min_sigma, (double)p->Nt[d] / (double)N[d]);
+  const bool c128_poly_ok = dtype == NFFT_C128 && !(flags & kWindowFlags) && !closed && !wide;
+  const bool poly_default = c128_poly_ok && (m >= 7 || min_sigma >= 1.5);
   if (s == NFFT_OK && ((flags & NFFT_FLAG_WINDOW_POLYNOMIAL) || poly_default)) {
     p->wmode = kWinPoly;
-    if (dtype == NFFT_C128) s = dalloc(p, &p->poly64, sizeof(double) * D * p->K * (2 * m + 1));
+    p->poly_Z = 2 * m + 1;
+    if (poly_default && 2 * m < 16) p->poly_Z = 17;
+    if (dtype == NFFT_C128) s = dalloc(p, &p->poly64, sizeof(double) * D * p->K * p->poly_Z);
   }
   if (s == NFFT_OK && !closed && !wide) {
     PolyArgs pa{};
@@ -824,7 +832,13 @@ int nfft_plan_create(nfft_plan** out, int D, const int64_t* N, int64_t M, double
     pa.deg = 2 * m;
     pa.m = m;
     for (int d = 0; d < D; ++d) pa.b[d] = p->b[d];
-    s = cuda_status(p, launch_build_poly(pa, p->poly, p->stream, p->poly64));
+    // the FP32 table (degree 2m) and, at the same degree, the FP64 one
+    const bool same = p->poly64 && p->poly_Z == 2 * m + 1;
+    s = cuda_status(p, launch_build_poly(pa, p->poly, p->stream, same ? p->poly64 : nullptr));
+    if (s == NFFT_OK && p->poly64 && !same) {
+      pa.deg = p->poly_Z - 1;
+      s = cuda_status(p, launch_build_poly(pa, nullptr, p->stream, p->poly64));
+    }
   }
   if (s == NFFT_OK && dtype == NFFT_C64 && !(flags & NFFT_FLAG_LIBRARY_FFT)) {
     int Ni[kMaxD], Nti[kMaxD];

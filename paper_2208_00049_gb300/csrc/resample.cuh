@@ -111,7 +111,7 @@ __device__ __noinline__ void table_weights(const Geometry& g, int d, int mi, R t
       if (dw) dw[i] = dv;
     }
   } else {
-    const int Z = 2 * mi + 1;
+    const int Z = g.wZ;
     const R* pc = (const R*)g.wtab + (int64_t)d * K * Z;
     const R zeta = t - R(0.5);
     for (int i = 0; i < K; ++i) {
@@ -183,6 +183,14 @@ __device__ __forceinline__ void node_weight_derivs(const Geometry& g, int d, int
 // value node_weights gives for tap i.
 template <int K, typename R>
 __device__ __forceinline__ R node_weight_tap(const Geometry& g, int d, int mi, R t, int i) {
+  if (g.wmode == kWinPoly) {  // tap i's polynomial alone
+    const int Z = g.wZ;
+    const R* pc = (const R*)g.wtab + ((int64_t)d * K + i) * Z;
+    const R zeta = t - R(0.5);
+    R v = pc[Z - 1];
+    for (int z = Z - 2; z >= 0; --z) v = v * zeta + pc[z];
+    return v;
+  }
   if (g.wmode != kWinDirect) {
     R tmp[K];
     table_weights<K, R>(g, d, mi, t, tmp, nullptr);

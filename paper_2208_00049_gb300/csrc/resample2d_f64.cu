@@ -34,6 +34,7 @@ constexpr int kF64Warps = 4;                 // warps per CTA, one work item per
 constexpr int kF64Threads = 32 * kF64Warps;
 constexpr int kF64Rows = 2 * kF64Warps;      // row residues: (warp, lane >> 4)
 constexpr int kF64Batch = 32;                // nodes staged per batch
+constexpr int kF64Z = 17;                    // POLYNOMIAL coefficients per tap held (zero above the table's)
 
 struct F64Stage {
   double t[kF64Batch][2];      // fractional positions
@@ -48,15 +49,15 @@ size_t f64_cta_bytes(const Geometry& g) {
 }
 
 // Window value of tap i of dimension d (u = t - off - i), in the plan's
-// window form; coef: the tap's POLYNOMIAL coefficients (kWinPoly only).
-template <int K>
+// window form; coef: the tap's POLYNOMIAL coefficients, zero above the
+// table's degree (kWinPoly only).
 __device__ __forceinline__ double tap_value(const Geometry& g, int d, int mi, double t, int i,
-                                            const double (&coef)[K + 1]) {
+                                            const double (&coef)[kF64Z]) {
   if (g.wmode == kWinPoly) {
     const double zeta = t - 0.5;
-    double v = coef[K];
+    double v = coef[kF64Z - 1];
 #pragma unroll
-    for (int z = K - 1; z >= 0; --z) v = v * zeta + coef[z];
+    for (int z = kF64Z - 2; z >= 0; --z) v = v * zeta + coef[z];
     return v;
   }
   const double u = double(-g.off - i) + t;
@@ -84,10 +85,11 @@ __global__ void __launch_bounds__(kF64Threads)
   const int64_t M = g.M;
   const double* frac = reinterpret_cast<const double*>(na.frac);
   // this thread's window tap: tap c16 of dimension h; coefficients in registers
-  double coef[K + 1];
+  double coef[kF64Z];
 #pragma unroll
-  for (int z = 0; z <= K; ++z)
-    coef[z] = (g.wmode == kWinPoly && c16 < K) ? ((const double*)g.wtab)[((int64_t)h * K + c16) * (K + 1) + z] : 0.0;
+  for (int z = 0; z < kF64Z; ++z)
+    coef[z] = (g.wmode == kWinPoly && c16 < K && z < g.wZ) ? ((const double*)g.wtab)[((int64_t)h * K + c16) * g.wZ + z]
+                                                           : 0.0;
   const int nitems = *na.n_items;
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kF64Threads)
       // tap (h, c16) of nodes warp, warp + 4, ...
 #pragma unroll 2
       for (int n = warp; n < nb; n += kF64Warps)
-        st.w[n][lane] = c16 < K ? tap_value<K>(g, h, mi, st.t[n][h], c16, coef) : 0.0;
+        st.w[n][lane] = c16 < K ? tap_value(g, h, mi, st.t[n][h], c16, coef) : 0.0;
       __syncthreads();
       // v w1 per node and column residue
       for (int e = tid; e < nb * 16; e += kF64Threads) {
@@ -188,6 +190,7 @@ bool scatter2d_f64_supported(const Geometry& g) {
   const char* e = getenv("NFFT_GB300_F64_SCATTER");
   if (e && strcmp(e, "generic") == 0) return false;
   if (g.D != 2 || g.closed || g.K % 2 != 0 || g.K > 16 || g.K != 2 * (int)g.m || g.off != 1 - g.K / 2) return false;
+  if (g.wmode == kWinPoly && g.wZ > kF64Z) return false;
   return f64_cta_bytes(g) <= 200 * 1024;
 }
 

@@ -19,8 +19,9 @@
 //  * the region is added to the grid with FP64 global reductions (performed
 //    in L2), wrapped per dimension.
 //
-// FP64 work per node at m = 4: 24 Horner chains of 8 steps, 64 + 16 table
-// products and 1024 multiply-adds for the 512 complex terms, about 1300
+// FP64 work per node at m = 4: 24 Horner chains (of 16 steps in the complex128
+// POLYNOMIAL table, degree 16 at m <= 8; or the direct form), 64 + 16 table
+// products and 1024 multiply-adds for the 512 complex terms, about 1500
 // operations, where the generic kernel adds each of the 1024 real terms
 // with a shared-memory FP64 atomic.
 #include <stdlib.h>
@@ -34,10 +35,11 @@ namespace {
 constexpr int kS3Threads = 128;
 constexpr int kS3Batch = 16;  // nodes staged per batch
 constexpr int kS3MaxK = 8;
+constexpr int kS3Z = 17;      // POLYNOMIAL coefficients per tap held (zero above the table's)
 
 template <int K>
 struct S3Stage {
-  double coef[3][K][K + 1];        // POLYNOMIAL coefficients of every tap
+  double coef[3][K][kS3Z];         // POLYNOMIAL coefficients of every tap, zero above the table's
   double t[kS3Batch][3];           // fractional positions
   double2 v[kS3Batch];             // input values
   int a[kS3Batch][4];              // cell offsets in the tile
@@ -52,14 +54,13 @@ size_t s3_bytes(const Geometry& g) {
 }
 
 // Window value of tap i of dimension d (u = t - off - i), in the plan's
-// window form; pc: the tap's POLYNOMIAL coefficients (kWinPoly only).
-template <int K>
+// window form; pc: the tap's kS3Z POLYNOMIAL coefficients (kWinPoly only).
 __device__ __forceinline__ double tap_value3(const Geometry& g, int d, int mi, double t, int i, const double* pc) {
   if (g.wmode == kWinPoly) {
     const double zeta = t - 0.5;
-    double v = pc[K];
+    double v = pc[kS3Z - 1];
 #pragma unroll
-    for (int z = K - 1; z >= 0; --z) v = v * zeta + pc[z];
+    for (int z = kS3Z - 2; z >= 0; --z) v = v * zeta + pc[z];
     return v;
   }
   const double u = double(-g.off - i) + t;
@@ -86,7 +87,10 @@ __global__ void __launch_bounds__(kS3Threads)
   const int64_t M = g.M;
   const double* frac = reinterpret_cast<const double*>(na.frac);
   if (g.wmode == kWinPoly)
-    for (int e = tid; e < 3 * K * (K + 1); e += kS3Threads) (&st.coef[0][0][0])[e] = ((const double*)g.wtab)[e];
+    for (int e = tid; e < 3 * K * kS3Z; e += kS3Threads) {
+      const int tap = e / kS3Z, z = e - tap * kS3Z;  // tap = d K + i
+      (&st.coef[0][0][0])[e] = z < g.wZ ? ((const double*)g.wtab)[(int64_t)tap * g.wZ + z] : 0.0;
+    }
   const int nitems = *na.n_items;
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(kS3Threads)
       __syncthreads();
       for (int e = tid; e < nb * 3 * K; e += kS3Threads) {
         const int n = e / (3 * K), j = e - n * 3 * K, d = j / K, i = j - d * K;
-        st.w[n][d][i] = tap_value3<K>(g, d, mi, st.t[n][d], i, &st.coef[d][i][0]);
+        st.w[n][d][i] = tap_value3(g, d, mi, st.t[n][d], i, &st.coef[d][i][0]);
       }
       __syncthreads();
       for (int e = tid; e < nb * K * K; e += kS3Threads) {
@@ -200,6 +204,7 @@ bool scatter3d_f64_supported(const Geometry& g) {
   if (e && strcmp(e, "generic") == 0) return false;
   if (g.D != 3 || g.closed || g.K % 2 != 0 || g.K > kS3MaxK || g.K != 2 * (int)g.m || g.off != 1 - g.K / 2)
     return false;
+  if (g.wmode == kWinPoly && g.wZ > kS3Z) return false;
   return s3_smem(g) <= 200 * 1024;
 }
 

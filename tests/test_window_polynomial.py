@@ -63,3 +63,73 @@ def test_polynomial_taps_cover_the_footprint():
     peak = ow.psi(np.array([0.0]), m, b)[0]
     edge = np.polynomial.polynomial.polyval(-0.5, c) * peak
     assert abs(edge - b / np.pi) <= 1e-8 * peak
+
+
+def _fit_deg(m, b, i, deg):
+    """As _fit, at another degree (deg + 1 Chebyshev points)."""
+    Z = deg + 1
+    zeta = 0.5 * np.cos(np.pi * (np.arange(Z) + 0.5) / Z)
+    u = zeta + 0.5 + (m - 1) - i
+    val = ow.psi(u, m, b) / ow.psi(np.array([0.0]), m, b)[0]
+    return np.linalg.solve(np.vander(zeta, Z, increasing=True), val)
+
+
+@pytest.mark.parametrize("sigma", [1.5, 2.0])
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_complex128_default_polynomial_reaches_fp64_rounding(m, sigma):
+    """Complex128 plans without a window flag and with oversampling of at
+    least 1.5 (or m >= 7) read the window from a polynomial of degree
+    max(2m, 16) per tap interval, fitted in FP64 the same way: its error
+    against the direct window stays within 2e-14 of the peak, the level of
+    the direct form's own FP64 evaluation, for every m the complex128
+    kernels take."""
+    b = np.pi * (2.0 - 1.0 / sigma)
+    deg = max(2 * m, 16)
+    zeta = np.linspace(-0.5, 0.5, 2001)[:-1]
+    worst = 0.0
+    for i in range(2 * m):
+        c = _fit_deg(m, b, i, deg)
+        u = zeta + 0.5 + (m - 1) - i
+        ref = ow.psi(u, m, b) / ow.psi(np.array([0.0]), m, b)[0]
+        worst = max(worst, np.max(np.abs(np.polynomial.polynomial.polyval(zeta, c) - ref)))
+    assert worst <= 2e-14
+
+
+def test_complex128_default_polynomial_leaves_the_transform_at_rounding():
+    """The oracle's NFFT with the window replaced by the degree-16 table
+    reading (2D, 48 x 40, m = 4, sigma = 2; 1D, N = 257, m = 3) against the
+    oracle with the direct window: the transforms differ at the FP64
+    rounding level (<= 1e-13 relative L2), three orders below the
+    complex128 target of 1e-12."""
+    from oracle import nfft as onfft
+    from paper_2208_00049_gb300 import inputs
+
+    for N, M, sigma, m in (((48, 40), 600, 2.0, 4), ((257,), 513, 2.0, 3)):
+        case = inputs.small_case(N, M, seed=17, sigma=sigma, m=m)
+        p = onfft.Params(N, sigma, m)
+        deg = max(2 * m, 16)
+        tables = {bb: [_fit_deg(m, bb, i, deg) for i in range(2 * m)] for bb in set(p.b)}
+        peak = {bb: ow.psi(np.array([0.0]), m, bb)[0] for bb in set(p.b)}
+
+        def poly_window(self, u, bb):
+            u = np.asarray(u, dtype=float)
+            fl = np.floor(u)
+            tap = (m - 1 - fl).astype(int)
+            zeta = (u - fl) - 0.5
+            out = np.zeros_like(u)
+            for i, c in enumerate(tables[bb]):
+                sel = tap == i
+                out[sel] = np.polynomial.polynomial.polyval(zeta[sel], c) * peak[bb]
+            return out
+
+        ref_f = onfft.forward(case["k"], case["f"], sigma, m)
+        ref_a = onfft.adjoint(case["k"], case["w"], N, sigma, m)
+        orig = onfft.Params.window
+        onfft.Params.window = poly_window
+        try:
+            got_f = onfft.forward(case["k"], case["f"], sigma, m)
+            got_a = onfft.adjoint(case["k"], case["w"], N, sigma, m)
+        finally:
+            onfft.Params.window = orig
+        assert np.linalg.norm(got_f - ref_f) <= 1e-13 * np.linalg.norm(ref_f)
+        assert np.linalg.norm(got_a - ref_a) <= 1e-13 * np.linalg.norm(ref_a)
