@@ -85,10 +85,11 @@ extern "C" {
 
 /* Window values (Sec. 3.7.4).  Without these flags complex64 plans use the
    specialised 2D and 3D kernels where they apply (window from its
-   POLYNOMIAL representation), complex128 plans with m >= 7 the generic
-   kernels with the POLYNOMIAL window (its FP64 fit error is at the rounding
-   level there), and every other plan the generic kernels with the window
-   evaluated.  Each flag below selects the generic kernels (any D, m, dtype)
+   POLYNOMIAL representation), complex128 plans with m >= 7 or an
+   oversampling of at least 1.5 (and half-open support) a POLYNOMIAL window
+   fitted in FP64 at degree max(2m, 16), whose fit error is at the FP64
+   rounding level (about 1e-14 of the window peak), and every other plan the
+   window evaluated.  Each flag below selects the generic kernels (any D, m, dtype)
    with one way of obtaining the window values, so that the three can be
    compared on the same kernels; at most one may be given:
      DIRECT      the window evaluated per tap (sinh, sqrt);
